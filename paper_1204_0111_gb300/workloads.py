@@ -1,0 +1,145 @@
+"""Seeded synthetic workloads: velocity models, sources and frequencies.
+
+Inputs only: this module holds none of the method's arithmetic and is shared
+by the GPU binding's callers, the tests and the CPU oracle runs.  The paper
+measures on analytic models and on the SEG/EAGE Overthrust model (§3); the
+generators below stand in for that family (constant, lens-shaped, layered
+and faulted, smooth random, salt body), all seeded.
+
+Grid convention (§1.1): n interior points per axis, h = 1/(n+1), node
+(i1, i2, i3) at ((i1+1)h, (i2+1)h, (i3+1)h); arrays are (nz, ny, nx).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+def coords(nx, ny, nz, h):
+    z, y, x = np.meshgrid((np.arange(nz) + 1) * h, (np.arange(ny) + 1) * h, (np.arange(nx) + 1) * h,
+                          indexing="ij")
+    return x, y, z
+
+
+def omega_for_ppw(c_min: float, ppw: float, h: float) -> float:
+    """omega giving ``ppw`` points per minimum wavelength 2 pi c_min / omega (§1)."""
+    return 2.0 * math.pi * c_min / (ppw * h)
+
+
+def velocity_constant(nx, ny, nz, h, value=1.0):
+    return np.full((nz, ny, nx), float(value))
+
+
+def velocity_lens(nx, ny, nz, h):
+    """Converging lens c = 1 - 0.4 exp(-32 |x - 0.5|^2)."""
+    x, y, z = coords(nx, ny, nz, h)
+    return 1.0 - 0.4 * np.exp(-32.0 * ((x - 0.5) ** 2 + (y - 0.5) ** 2 + (z - 0.5) ** 2))
+
+
+def velocity_layered_faulted(nx, ny, nz, h, seed=3, n_interfaces=12, n_faults=2):
+    """Dipping piecewise-constant layers, c ~ U(1.5, 6), offset by planar faults."""
+    rng = np.random.default_rng(seed)
+    zbar = np.sort(rng.uniform(0.0, 1.0, n_interfaces))
+    dip_a = rng.uniform(-0.15, 0.15, n_interfaces)
+    dip_b = rng.uniform(-0.15, 0.15, n_interfaces)
+    layer_c = rng.uniform(1.5, 6.0, n_interfaces + 1)
+    faults = []
+    for _ in range(n_faults):
+        nrm = rng.normal(size=3)
+        nrm /= np.linalg.norm(nrm)
+        pt = rng.uniform(0.2, 0.8, 3)
+        shift = rng.uniform(1.0, 10.0) * h
+        faults.append((nrm, pt, shift))
+    x, y, z = coords(nx, ny, nz, h)
+    zz = z.copy()
+    for nrm, pt, shift in faults:
+        side = (x - pt[0]) * nrm[0] + (y - pt[1]) * nrm[1] + (z - pt[2]) * nrm[2] > 0
+        zz = np.where(side, zz - shift, zz)
+    layer = np.zeros(x.shape, dtype=np.int64)
+    for k in range(n_interfaces):
+        layer += (zz > zbar[k] + dip_a[k] * (x - 0.5) + dip_b[k] * (y - 0.5)).astype(np.int64)
+    return layer_c[layer]
+
+
+def velocity_smooth_random(nx, ny, nz, h, seed, corr_len=0.1):
+    """c = 2 + 0.5 tanh(g), g an N(0,1) field Gaussian-filtered to ``corr_len``, unit variance."""
+    from scipy.ndimage import gaussian_filter
+    rng = np.random.default_rng(seed)
+    g = gaussian_filter(rng.normal(size=(nz, ny, nx)), sigma=corr_len / h, mode="reflect")
+    g = (g - g.mean()) / g.std()
+    return 2.0 + 0.5 * np.tanh(g)
+
+
+def velocity_salt(nx, ny, nz, h):
+    """Linear gradient 1.5 -> 4.5 with depth plus a smooth ellipsoidal body at 4.5."""
+    x, y, z = coords(nx, ny, nz, h)
+    bg = 1.5 + 3.0 * z
+    r = np.sqrt(((x - 0.5) / 0.3) ** 2 + ((y - 0.5) / 0.3) ** 2 + ((z - 0.55) / 0.2125) ** 2)
+    w = 2.0 * h / 0.2125
+    blend = 0.5 * (1.0 + np.tanh(-(r - 1.0) / w))
+    return bg + (4.5 - bg) * blend
+
+
+def gaussian_source(nx, ny, nz, h, center, sigma=None):
+    """f = exp(-|x - x0|^2 / (2 sigma^2)), sigma = 2h by default; flat (N,) complex."""
+    sigma = 2.0 * h if sigma is None else sigma
+    x, y, z = coords(nx, ny, nz, h)
+    r2 = (x - center[0]) ** 2 + (y - center[1]) ** 2 + (z - center[2]) ** 2
+    return np.exp(-r2 / (2.0 * sigma * sigma)).ravel().astype(np.complex128)
+
+
+def random_vector(N, nrhs=1, seed=0):
+    """Seeded complex Gaussian test vectors, shape (nrhs, N)."""
+    rng = np.random.default_rng(seed)
+    return (rng.normal(size=(nrhs, N)) + 1j * rng.normal(size=(nrhs, N))).astype(np.complex128)
+
+
+@dataclass
+class Workload:
+    name: str
+    n: int
+    c: np.ndarray
+    h: float
+    omega: float
+    gamma: int
+    panel_depth: int
+    pad: int
+    leaf: int = 64
+    pml_C: float = 4.0
+    alpha: float = 2.0 * math.pi
+    sources: list = field(default_factory=list)
+    k: int = 20
+    tol: float = 1e-5
+
+    @property
+    def N(self):
+        return self.n ** 3
+
+    def rhs(self) -> np.ndarray:
+        """(nrhs, N) Gaussian shots."""
+        return np.stack([gaussian_source(self.n, self.n, self.n, self.h, s) for s in self.sources])
+
+
+def cube_constant(n=20, gamma=5, panel_depth=4, pad=None, ppw=10.0, leaf=64):
+    """Constant c = 1 on n^3, Gaussian shot at the centre (the CPU-seconds case at n = 20)."""
+    h = 1.0 / (n + 1)
+    c = velocity_constant(n, n, n, h)
+    return Workload(f"constant{n}", n, c, h, omega_for_ppw(1.0, ppw, h), gamma, panel_depth,
+                    gamma if pad is None else pad, leaf, sources=[(0.5, 0.5, 0.5)])
+
+
+def cube_lens(n=100, gamma=8, panel_depth=4, pad=None, ppw=10.0, leaf=64):
+    """Converging lens on n^3, shot at (0.5, 0.5, 0.1) (the plain-complex128 GPU case at n = 100)."""
+    h = 1.0 / (n + 1)
+    c = velocity_lens(n, n, n, h)
+    return Workload(f"lens{n}", n, c, h, omega_for_ppw(float(c.min()), ppw, h), gamma, panel_depth,
+                    gamma if pad is None else pad, leaf, sources=[(0.5, 0.5, 0.1)])
+
+
+def cube_layered(n=200, gamma=10, panel_depth=4, pad=None, ppw=10.0, leaf=64, seed=3):
+    h = 1.0 / (n + 1)
+    c = velocity_layered_faulted(n, n, n, h, seed=seed)
+    return Workload(f"layered{n}", n, c, h, omega_for_ppw(float(c.min()), ppw, h), gamma, panel_depth,
+                    gamma if pad is None else pad, leaf, sources=[(0.5, 0.5, 0.1)])
