@@ -1,0 +1,171 @@
+/*
+ * psp.h - C ABI of the GB300 (sm_103a) moving-PML sweeping preconditioner.
+ *
+ * Poulson, Engquist, Li, Ying, "A parallel sweeping preconditioner for
+ * heterogeneous 3D Helmholtz equations" (arXiv:1204.0111).
+ *
+ * Problem (§1, Eq. (1.1)): the Helmholtz operator A = -Laplacian - omega^2/c(x)^2
+ * on the interior grid nx x ny x nz (spacing h, node (i1,i2,i3) at
+ * ((i1+1)h, (i2+1)h, (i3+1)h), unknown index i1 + i2 nx + i3 nx ny), second
+ * order 7-point differences, PML of pml_gamma points on the faces selected by
+ * psp_options.pml_faces, homogeneous Dirichlet beyond.  The library works with
+ * the symmetric form multiplied through by s1 s2 s3 (s_j = 1 + i sigma_j/omega):
+ *     A_s u = s1 s2 s3 f,
+ * which is complex symmetric (§1.1).  The preconditioner is built from the
+ * damped operator J of Eq. (1.5) (omega -> omega + i alpha in the mass term).
+ *
+ * Conventions for every entry point:
+ *  - Complex vectors are interleaved (re, im) doubles.  A block of nrhs vectors
+ *    of length N = nx ny nz is column-major: vector r starts at element r*N.
+ *  - Pointers may be DEVICE pointers (cudaMalloc'd / torch CUDA tensors) or
+ *    HOST pointers; the library inspects each pointer and stages host data
+ *    through device memory itself (on the given stream, synchronising it
+ *    before returning host results).  The caller keeps ownership of all
+ *    buffers it passes; the library owns everything behind a psp_handle.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Device work is
+ *    ordered on it.  Calls returning host data synchronise the stream.
+ *  - No exception or abort crosses the ABI: every call returns a psp_status.
+ *    psp_last_error() returns a thread-local message for the last failure.
+ *    A handle stays destroyable after any error.
+ *  - A handle must not be used from two host threads at once.
+ */
+#ifndef PSP_H
+#define PSP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct psp_ctx_s* psp_handle;
+
+typedef enum {
+  PSP_OK = 0,
+  PSP_ERR_ARG = 1,            /* invalid argument (size, NULL pointer, option out of range) */
+  PSP_ERR_OOM = 2,            /* device or host allocation failed */
+  PSP_ERR_CUDA = 3,           /* a CUDA runtime call failed; see psp_last_error() */
+  PSP_ERR_ZERO_PIVOT = 4,     /* an unpivoted LDL^T pivot fell below the threshold */
+  PSP_ERR_NOT_CONVERGED = 5,  /* GMRES hit maxit before reaching tol */
+  PSP_ERR_TIMEOUT = 6,        /* a bounded device wait gave up */
+  PSP_ERR_STATE = 7           /* handle not in a state that allows the call */
+} psp_status;
+
+typedef struct {
+  int nx, ny, nz; /* interior points per axis, >= 1 */
+  double h;       /* grid spacing, > 0 */
+} psp_grid;
+
+typedef enum {
+  PSP_PREC_C128 = 0,  /* fronts and sweeps in complex128 (FP64 CUDA cores) */
+  PSP_PREC_C64 = 1    /* fronts and sweeps in complex64; GMRES and matvec stay complex128 */
+} psp_precision;
+
+typedef enum {
+  PSP_AUX_MOVING_PML = 0, /* H_i = PML pad + panel (Alg. 1.4): the preconditioner */
+  PSP_AUX_EXACT = 1       /* H_i = all planes below the panel's top (Fig. 2 middle): M = J exactly */
+} psp_aux_mode;
+
+/* Options; psp_default_options() fills the defaults shown. */
+typedef struct {
+  double pml_C;       /* PML amplitude "C" (§3), default 4.0 */
+  double alpha;       /* damping of Eq. (1.5), default 2*pi */
+  int pad_depth;      /* artificial PML planes prefixed to each panel (Alg. 1.4); -1 = pml_gamma */
+  int leaf_size;      /* nested-dissection leaf: boxes with nx*ny*depth <= leaf are leaves; default 64 */
+  int precision;      /* psp_precision, default PSP_PREC_C128 */
+  int pml_faces;      /* bit mask x-lo 1, x-hi 2, y-lo 4, y-hi 8, z-lo 16, z-hi 32; default 63 */
+  int aux_mode;       /* psp_aux_mode, default PSP_AUX_MOVING_PML */
+  int reserved[9];
+} psp_options;
+
+/* Per-solve report filled by psp_solve (host struct). */
+typedef struct {
+  int iterations;      /* total inner GMRES iterations, max over right-hand sides */
+  int restarts;        /* restart cycles, max over right-hand sides */
+  int converged;       /* 1 if every right-hand side reached tol */
+  int applies;         /* preconditioner applications issued */
+  double relres_max;   /* max over rhs of the true ||b - A_s u|| / ||b||, b = s1 s2 s3 f */
+  double solve_ms;     /* wall time of the solve (host clock, stream synchronised) */
+  int status_front;    /* front id of a zero pivot, -1 if none */
+  int reserved[7];
+} psp_solve_info;
+
+void psp_default_options(psp_options* opt);
+
+/*
+ * psp_setup - Alg. 1.4 (§1.1): plan the m panels (panel 0 = planes [0, gamma+d),
+ * then d planes each, the last one taking the remainder), form every PML-padded
+ * auxiliary problem H_i, and factor all of them with the supernodal
+ * nested-dissection multifrontal LDL^T of §2.1-§2.2 (unpivoted, complex symmetric),
+ * followed by selective inversion of every front (§2.2).
+ *
+ *   g            grid (host struct)
+ *   c            wave speed c(x) > 0, N doubles, x fastest (host or device)
+ *   omega        angular frequency > 0
+ *   pml_gamma    PML points gamma >= 0 on each selected face
+ *   panel_depth  planes per panel d >= 1
+ *   opt          options or NULL for defaults
+ *   out          receives the new handle (owned by the library until psp_destroy)
+ * Errors: PSP_ERR_ARG, PSP_ERR_OOM, PSP_ERR_CUDA, PSP_ERR_ZERO_PIVOT (|d| < 1e-300
+ * for complex128, < 1e-30 for complex64; *out is still set and must be destroyed).
+ * The c array is copied; the caller may free it after the call returns.
+ */
+psp_status psp_setup(const psp_grid* g, const double* c, double omega, int pml_gamma, int panel_depth,
+                     const psp_options* opt, void* stream, psp_handle* out);
+
+/*
+ * psp_apply - Alg. 1.5: out = M^{-1} rhs, a forward sweep u_i := T_i u_i,
+ * u_{i+1} -= J_{i+1,i} u_i and a backward sweep u_i -= T_i(J_{i+1,i}^T u_{i+1}),
+ * with T_i the Alg. 1.3 application of the factored H_i (extend by zero over the
+ * pad, multifrontal solve, keep the panel's planes).  rhs and out are nrhs
+ * complex vectors of length N (host or device); out may alias rhs.
+ */
+psp_status psp_apply(psp_handle h, const double* rhs, double* out, int nrhs, void* stream);
+
+/*
+ * psp_matvec - y = A_s x (which = 0) or y = J_s x (which = 1), the 7-point
+ * operators of Eq. (1.1) / Eq. (1.5) in the symmetric s1 s2 s3-scaled form.
+ */
+psp_status psp_matvec(psp_handle h, int which, const double* x, double* y, int nrhs, void* stream);
+
+/*
+ * psp_solve - right-preconditioned restarted GMRES(k) (§2.4) for A_s u = s1 s2 s3 f
+ * with x0 = 0 (§3), in complex128, preconditioned by psp_apply.  Stops when every
+ * right-hand side has a true relative residual < tol or after maxit inner
+ * iterations.  f: nrhs unscaled sources; u: nrhs solutions (host or device).
+ * info (host, may be NULL) receives the report.
+ * Returns PSP_ERR_NOT_CONVERGED (u holds the last iterate) if maxit is reached.
+ */
+psp_status psp_solve(psp_handle h, const double* f, double* u, int nrhs, double tol, int k, int maxit,
+                     psp_solve_info* info, void* stream);
+
+/*
+ * psp_symbolic_export - the nested-dissection tree of panel `panel`'s auxiliary
+ * problem (§2.1 separator tree, postorder), for bit-exact comparison.
+ * Layout of the int32 stream: [nx, ny, depth, lead, nsn, then for each supernode:
+ * s, u, parent, then s node ids, then u struct node ids] with node id
+ * x + nx*y + nx*ny*k in the box (k = 0 is the bottom pad plane).
+ * Call with buf = NULL to get the length in *len (int32 count).
+ */
+psp_status psp_symbolic_export(psp_handle h, int panel, int32_t* buf, size_t* len);
+
+/* Number of panels m, total fronts, and bytes of factor storage (any pointer may be NULL). */
+psp_status psp_info(psp_handle h, int* panels, int64_t* fronts, int64_t* factor_bytes);
+
+/*
+ * psp_export_front - copy the factor of one front (panel, supernode) to host memory:
+ * the (s+u) x s column-major block G = [inv(L_TL) with D on its diagonal; L_BL inv(L_TL)]
+ * after selective inversion, as complex128 (converted if the handle is complex64).
+ * Call with buf = NULL to get s and u.
+ */
+psp_status psp_export_front(psp_handle h, int panel, int supernode, double* buf, int* s, int* u);
+
+psp_status psp_destroy(psp_handle h);
+const char* psp_status_string(psp_status s);
+const char* psp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSP_H */

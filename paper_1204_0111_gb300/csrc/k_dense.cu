@@ -1,0 +1,259 @@
+// Dense front kernels of the partial factorisation (§2.2), CUDA-core path for complex128
+// and complex64:  blocked unpivoted LDL^T of F_TL, the blocked inverse of L_TL for selective
+// inversion, and a batched complex GEMM C (+)= alpha A diag(d)^{+-1} B^T with triangle masks
+// that carries the trailing updates, the Schur update F_BR -= Z F_BL^T and the two
+// triangular multiplies.
+#include "cplx.cuh"
+#include "psp_internal.h"
+
+namespace psp {
+
+constexpr int kNB = 32;  // diagonal block size of the blocked LDL^T and inverse
+
+// ---------------------------------------------------------------------------
+// LDL^T of the kb-th diagonal block of F_TL (unblocked, right-looking, in shared memory).
+// The block is overwritten by its unit lower factor (strict part) and D (diagonal).
+// A pivot with |d| < tiny records 1 + (front's global id) in status[0].
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_diag_ldlt(const FrontTask<T>* __restrict__ fronts, const int* __restrict__ list,
+                                                   int kb, double tiny, int* status) {
+  __shared__ T S[kNB][kNB + 1];  // S[col][row]
+  __shared__ T colv[kNB];
+  const FrontTask<T> ft = fronts[list[blockIdx.x]];
+  const int ld = ft.s + ft.u;
+  const int o = kb * kNB;
+  const int bs = min(kNB, ft.s - o);
+  T* B = ft.G + (int64_t)o * ld + o;
+  for (int e = threadIdx.x; e < bs * bs; e += blockDim.x) {
+    const int r = e % bs, c = e / bs;
+    if (r >= c) S[c][r] = B[(int64_t)c * ld + r];
+  }
+  __syncthreads();
+  for (int j = 0; j < bs; ++j) {
+    const T d = S[j][j];
+    if (threadIdx.x == 0 && (double)cabs2(d) < tiny * tiny) atomicCAS(status, 0, (int)(1 + ft.gfid));
+    const T dinv = cdiv(CplxTraits<T>::one(), d);
+    for (int i = j + 1 + threadIdx.x; i < bs; i += blockDim.x) {
+      const T a = S[j][i];
+      colv[i] = a;
+      S[j][i] = cmul(a, dinv);
+    }
+    __syncthreads();
+    // S(i,k) -= a_i * l_k for j < k <= i
+    const int m = bs - j - 1;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      const int i = j + 1 + e % m, k = j + 1 + e / m;
+      if (i >= k) cfms(S[k][i], colv[i], S[j][k]);
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < bs * bs; e += blockDim.x) {
+    const int r = e % bs, c = e / bs;
+    if (r >= c) B[(int64_t)c * ld + r] = S[c][r];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Rows of F_TL below diagonal block kb:  X L_kk^T = F(r, block)  ->  F(r, block) := X D^{-1}.
+// One thread per row; L_kk and D in shared memory.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(64) k_panel_right(const FrontTask<T>* __restrict__ fronts,
+                                                    const ColTask* __restrict__ tasks, int kb) {
+  __shared__ T L[kNB][kNB + 1];  // L[col][row]
+  __shared__ T dinv[kNB];
+  const ColTask tk = tasks[blockIdx.x];
+  const FrontTask<T> ft = fronts[tk.front];
+  const int ld = ft.s + ft.u;
+  const int o = kb * kNB;
+  const int bs = min(kNB, ft.s - o);
+  const T* Bd = ft.G + (int64_t)o * ld + o;
+  for (int e = threadIdx.x; e < bs * bs; e += blockDim.x) {
+    const int r = e % bs, c = e / bs;
+    L[c][r] = (r > c) ? Bd[(int64_t)c * ld + r] : CplxTraits<T>::zero();
+  }
+  for (int c = threadIdx.x; c < bs; c += blockDim.x) dinv[c] = cdiv(CplxTraits<T>::one(), Bd[(int64_t)c * ld + c]);
+  __syncthreads();
+  const int r = tk.c0 + threadIdx.x;
+  if (r >= tk.c1) return;
+  T* row = ft.G + (int64_t)o * ld + r;
+  T x[kNB];
+#pragma unroll
+  for (int c = 0; c < kNB; ++c) {
+    if (c < bs) {
+      T v = row[(int64_t)c * ld];
+      for (int k = 0; k < c; ++k) cfms(v, x[k], L[k][c]);
+      x[c] = v;
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < kNB; ++c)
+    if (c < bs) row[(int64_t)c * ld] = cmul(x[c], dinv[c]);
+}
+
+// ---------------------------------------------------------------------------
+// Block row kb of W (the inverse of L_TL under construction): W(kb, cols) := L_kk^{-1} W(kb, cols).
+// A 32 x 64 tile is staged through shared memory; one thread per column.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(64) k_panel_left(const FrontTask<T>* __restrict__ fronts,
+                                                   const ColTask* __restrict__ tasks, int kb) {
+  __shared__ T L[kNB][kNB + 1];   // L[col][row]
+  __shared__ T Wt[64][kNB + 1];   // Wt[col][row]
+  const ColTask tk = tasks[blockIdx.x];
+  const FrontTask<T> ft = fronts[tk.front];
+  const int ld = ft.s + ft.u;
+  const int o = kb * kNB;
+  const int bs = min(kNB, ft.s - o);
+  const int ncol = tk.c1 - tk.c0;
+  const T* Bd = ft.G + (int64_t)o * ld + o;
+  for (int e = threadIdx.x; e < bs * bs; e += blockDim.x) {
+    const int r = e % bs, c = e / bs;
+    L[c][r] = (r > c) ? Bd[(int64_t)c * ld + r] : CplxTraits<T>::zero();
+  }
+  T* W0 = ft.W + (int64_t)tk.c0 * ft.s + o;
+  for (int e = threadIdx.x; e < bs * ncol; e += blockDim.x) {
+    const int r = e % bs, c = e / bs;
+    Wt[c][r] = W0[(int64_t)c * ft.s + r];
+  }
+  __syncthreads();
+  const int c = threadIdx.x;
+  if (c < ncol) {
+    for (int r = 1; r < bs; ++r) {
+      T v = Wt[c][r];
+      for (int k = 0; k < r; ++k) cfms(v, L[k][r], Wt[c][k]);
+      Wt[c][r] = v;
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < bs * ncol; e += blockDim.x) {
+    const int r = e % bs, cc = e / bs;
+    W0[(int64_t)cc * ft.s + r] = Wt[cc][r];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Batched complex GEMM, one 64 x 64 output tile per CTA (16 x 16 threads, 4 x 4 each).
+// ---------------------------------------------------------------------------
+constexpr int GT = 64, GK = 16;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm(const GemmTask<T>* __restrict__ tasks) {
+  __shared__ T As[GK][GT + 1];
+  __shared__ T Bs[GK][GT + 1];
+  const GemmTask<T> tk = tasks[blockIdx.x];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const T zero = CplxTraits<T>::zero();
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = zero;
+
+  const bool bnn = tk.flags & GF_B_NN;
+  for (int k0 = 0; k0 < tk.k; k0 += GK) {
+    // A chunk: 64 rows x 16 k
+    for (int e = threadIdx.x; e < GT * GK; e += 256) {
+      const int i = e % GT, kk = e / GT;
+      T v = zero;
+      if (i < tk.m && k0 + kk < tk.k) {
+        v = tk.A[(int64_t)(k0 + kk) * tk.lda + i];
+        if (tk.flags & (GF_D_MUL | GF_D_DIV)) {
+          const T dd = tk.d[(int64_t)(k0 + kk) * tk.ldd];
+          v = (tk.flags & GF_D_MUL) ? cmul(v, dd) : cdiv(v, dd);
+        }
+      }
+      As[kk][i] = v;
+    }
+    // B chunk: 64 n x 16 k
+    for (int e = threadIdx.x; e < GT * GK; e += 256) {
+      int j, kk;
+      if (bnn) { kk = e % GK; j = e / GK; } else { j = e % GT; kk = e / GT; }
+      T v = zero;
+      if (j < tk.n && k0 + kk < tk.k) {
+        v = bnn ? tk.B[(int64_t)j * tk.ldb + (k0 + kk)] : tk.B[(int64_t)(k0 + kk) * tk.ldb + j];
+        if (tk.flags & (GF_B_UNIT_LOWER_NT | GF_B_UNIT_LOWER_NN)) {
+          const int kg = tk.kg0 + k0 + kk, ng = tk.ng0 + j;
+          if (kg == ng) v = CplxTraits<T>::one();
+          else if ((tk.flags & GF_B_UNIT_LOWER_NT) ? (kg > ng) : (kg < ng)) v = zero;
+        }
+      }
+      Bs[kk][j] = v;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < GK; ++kk) {
+      T av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = As[kk][ty + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) cfma(acc[a][b], av[a], bv[b]);
+    }
+    __syncthreads();
+  }
+  const bool neg = tk.flags & GF_NEG, beta0 = tk.flags & GF_BETA0, lower = tk.flags & GF_C_LOWER;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int i = ty + 16 * a;
+    if (i >= tk.m) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int j = tx + 16 * b;
+      if (j >= tk.n || (lower && i < j)) continue;
+      T* c = tk.C + (int64_t)j * tk.ldc + i;
+      T v = neg ? cneg(acc[a][b]) : acc[a][b];
+      *c = beta0 ? v : cadd(*c, v);
+    }
+  }
+}
+
+// strict lower part of W -> strict lower part of F_TL (D stays on the diagonal)
+template <typename T>
+__global__ void __launch_bounds__(256) k_copy_linv(const FrontTask<T>* __restrict__ fronts,
+                                                   const ColTask* __restrict__ tasks) {
+  const ColTask tk = tasks[blockIdx.x];
+  const FrontTask<T> ft = fronts[tk.front];
+  const int ld = ft.s + ft.u;
+  for (int c = tk.c0; c < tk.c1; ++c)
+    for (int r = c + 1 + threadIdx.x; r < ft.s; r += blockDim.x)
+      ft.G[(int64_t)c * ld + r] = ft.W[(int64_t)c * ft.s + r];
+}
+
+template <typename T>
+void launch_diag_ldlt(const FrontTask<T>* fronts, const int* list, int nlist, int kb, double tiny, int* status,
+                      cudaStream_t st) {
+  if (nlist > 0) k_diag_ldlt<T><<<nlist, 256, 0, st>>>(fronts, list, kb, tiny, status);
+}
+template <typename T>
+void launch_panel_right(const FrontTask<T>* fronts, const ColTask* tasks, int ntasks, int kb, cudaStream_t st) {
+  if (ntasks > 0) k_panel_right<T><<<ntasks, 64, 0, st>>>(fronts, tasks, kb);
+}
+template <typename T>
+void launch_panel_left(const FrontTask<T>* fronts, const ColTask* tasks, int ntasks, int kb, cudaStream_t st) {
+  if (ntasks > 0) k_panel_left<T><<<ntasks, 64, 0, st>>>(fronts, tasks, kb);
+}
+template <typename T>
+void launch_gemm(const GemmTask<T>* tasks, int ntasks, cudaStream_t st) {
+  if (ntasks > 0) k_gemm<T><<<ntasks, 256, 0, st>>>(tasks);
+}
+template <typename T>
+void launch_copy_linv(const FrontTask<T>* fronts, const ColTask* tasks, int ntasks, cudaStream_t st) {
+  if (ntasks > 0) k_copy_linv<T><<<ntasks, 256, 0, st>>>(fronts, tasks);
+}
+
+#define PSP_INST(T)                                                                                           \
+  template void launch_diag_ldlt<T>(const FrontTask<T>*, const int*, int, int, double, int*, cudaStream_t);    \
+  template void launch_panel_right<T>(const FrontTask<T>*, const ColTask*, int, int, cudaStream_t);            \
+  template void launch_panel_left<T>(const FrontTask<T>*, const ColTask*, int, int, cudaStream_t);             \
+  template void launch_gemm<T>(const GemmTask<T>*, int, cudaStream_t);                                         \
+  template void launch_copy_linv<T>(const FrontTask<T>*, const ColTask*, int, cudaStream_t);
+PSP_INST(double2)
+PSP_INST(float2)
+#undef PSP_INST
+
+}  // namespace psp

@@ -1,0 +1,247 @@
+// Multifrontal solve with selectively inverted fronts (§2.2), one tree level per launch, as the
+// T_i of Alg. 1.3 inside the sweep of Alg. 1.5.
+//
+// Each front stores G = [inv(L_TL) (unit lower, D on the diagonal); M_BL = L_BL inv(L_TL)], so
+//   up the tree:   v_S = inv(L_TL) w_S,  x_S = D^{-1} v_S,  update_U = w_U - M_BL w_S
+//   down the tree: x_S = inv(L_TL)^T x_S - M_BL^T x_U
+// which are matrix-vector products (the point of selective inversion): every task reads its
+// block of G once, column segments contiguous, and no task depends on another task of the same
+// level.  Children's update vectors are pulled (at most two per row), never scattered, so the
+// summation order is fixed.  Extension by zero over the pad, the plane coupling J_{i+1,i} of
+// the previous / next panel and the extraction of the panel's planes are fused into the
+// gathers and the final write.
+#include "cplx.cuh"
+#include "psp_internal.h"
+
+namespace psp {
+
+template <typename T>
+__device__ __forceinline__ T input_value(const SolveCtx<T>& cx, int node, int q) {
+  const int nx = cx.sh.nx, ny = cx.sh.ny;
+  const int k = node / (nx * ny);
+  if (k < cx.lead) return CplxTraits<T>::zero();          // extension by zero over the pad (Alg. 1.3)
+  const int x = node % nx, y = (node / nx) % ny;
+  const int zg = cx.z0 + k - cx.lead;
+  const int64_t plane = (int64_t)nx * ny;
+  const int64_t g = x + (int64_t)nx * y + plane * zg;
+  const double2* uq = cx.u + (int64_t)q * cx.N;
+  double2 v;
+  if (cx.mode == 0) {
+    // u_i - J_{i,i-1} u_{i-1}: J's coupling entry is -s1 s2 / s3(z0 - 1/2) / h^2
+    v = uq[g];
+    if (cx.has_prev && zg == cx.z0) {
+      const double2 a = cscale(cmul(cmul(cx.s1n[x], cx.s2n[y]), cx.s3h[cx.z0]), cx.inv_h2);
+      cfma(v, a, uq[g - plane]);
+    }
+  } else {
+    // J_{i+1,i}^T u_{i+1}: supported on the panel's last plane
+    v = make_double2(0.0, 0.0);
+    if (cx.has_next && zg == cx.z1 - 1) {
+      const double2 a = cscale(cmul(cmul(cx.s1n[x], cx.s2n[y]), cx.s3h[cx.z1]), -cx.inv_h2);
+      v = cmul(a, uq[g + plane]);
+    }
+  }
+  return CplxTraits<T>::from(v);
+}
+
+template <typename T, int RG>
+__device__ __forceinline__ void pull_add(const SolveCtx<T>& cx, const int32_t* pl, int rhs0, T* out) {
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    const int32_t o = pl[t];
+    if (o < 0) break;
+#pragma unroll
+    for (int q = 0; q < RG; ++q)
+      if (rhs0 + q < cx.nrhs) out[q] = cadd(out[q], cx.upd[(int64_t)(rhs0 + q) * cx.upd_ld + o]);
+  }
+}
+
+template <typename T, int RG>
+__global__ void __launch_bounds__(256) k_solve_fwd(const SolveTask* __restrict__ tasks, SolveCtx<T> cx, int R) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const SolveTask tk = tasks[blockIdx.x];
+  const int rhs0 = blockIdx.y * RG;
+  const int sn = tk.sn;
+  const int s = cx.sh.s[sn], u = cx.sh.u[sn], ld = s + u;
+  const int first = cx.sh.first[sn];
+  const T* G = cx.G + cx.sh.g_off[sn];
+  const int32_t* pull = cx.sh.pull + 2 * cx.sh.pull_ptr[sn];
+  T* w = reinterpret_cast<T*>(smem_raw);        // s x RG
+  T* red = w + (int64_t)s * RG;                  // blockDim x RG
+
+  // w_S = (zero-extended input) + children's updates
+  for (int p = threadIdx.x; p < s; p += blockDim.x) {
+    const int node = cx.sh.order[first + p];
+    T v[RG];
+#pragma unroll
+    for (int q = 0; q < RG; ++q) v[q] = (rhs0 + q < cx.nrhs) ? input_value(cx, node, rhs0 + q) : CplxTraits<T>::zero();
+    pull_add<T, RG>(cx, pull + 2 * p, rhs0, v);
+#pragma unroll
+    for (int q = 0; q < RG; ++q) w[p * RG + q] = v[q];
+  }
+  __syncthreads();
+
+  const int i = threadIdx.x % R, grp = threadIdx.x / R, ngrp = blockDim.x / R;
+  const int r = tk.r0 + i;
+  T acc[RG];
+#pragma unroll
+  for (int q = 0; q < RG; ++q) acc[q] = CplxTraits<T>::zero();
+  if (r < tk.r1) {
+    const int jmax = r < s ? r : s;   // strictly lower part of inv(L_TL), all of M_BL
+    const T* Gr = G + r;
+    for (int j = grp; j < jmax; j += ngrp) {
+      const T gv = Gr[(int64_t)j * ld];
+#pragma unroll
+      for (int q = 0; q < RG; ++q) cfma(acc[q], gv, w[j * RG + q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < RG; ++q) red[threadIdx.x * RG + q] = acc[q];
+  __syncthreads();
+  if (grp == 0 && r < tk.r1) {
+    for (int g2 = 1; g2 < ngrp; ++g2)
+#pragma unroll
+      for (int q = 0; q < RG; ++q) acc[q] = cadd(acc[q], red[(g2 * R + i) * RG + q]);
+    if (r < s) {
+      const T dinv = cdiv(CplxTraits<T>::one(), G[(int64_t)r * ld + r]);
+#pragma unroll
+      for (int q = 0; q < RG; ++q)
+        if (rhs0 + q < cx.nrhs)
+          cx.xf[(int64_t)(rhs0 + q) * cx.n_loc + first + r] = cmul(cadd(acc[q], w[r * RG + q]), dinv);
+    } else {
+      T wu[RG];
+#pragma unroll
+      for (int q = 0; q < RG; ++q) wu[q] = CplxTraits<T>::zero();
+      pull_add<T, RG>(cx, pull + 2 * r, rhs0, wu);
+      const int64_t o = cx.sh.upd_off[sn] + (r - s);
+#pragma unroll
+      for (int q = 0; q < RG; ++q)
+        if (rhs0 + q < cx.nrhs) cx.upd[(int64_t)(rhs0 + q) * cx.upd_ld + o] = csub(wu[q], acc[q]);
+    }
+  }
+}
+
+template <typename T, int RG>
+__global__ void __launch_bounds__(256) k_solve_bwd(const SolveTask* __restrict__ tasks, SolveCtx<T> cx) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const SolveTask tk = tasks[blockIdx.x];
+  const int rhs0 = blockIdx.y * RG;
+  const int sn = tk.sn;
+  const int s = cx.sh.s[sn], u = cx.sh.u[sn], ld = s + u;
+  const int first = cx.sh.first[sn];
+  const T* G = cx.G + cx.sh.g_off[sn];
+  const int32_t* sel = cx.sh.struct_elim + cx.sh.struct_ptr[sn];
+  const int c0 = tk.r0;
+  T* y = reinterpret_cast<T*>(smem_raw);   // rows [c0, s+u) x RG
+  for (int r = c0 + threadIdx.x; r < ld; r += blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < RG; ++q) {
+      T v = CplxTraits<T>::zero();
+      if (rhs0 + q < cx.nrhs) {
+        const int64_t base = (int64_t)(rhs0 + q) * cx.n_loc;
+        v = (r < s) ? cx.xf[base + first + r] : cneg(cx.xb[base + sel[r - s]]);
+      }
+      y[(r - c0) * RG + q] = v;
+    }
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c = c0 + warp; c < tk.r1; c += nw) {
+    T acc[RG];
+#pragma unroll
+    for (int q = 0; q < RG; ++q) acc[q] = CplxTraits<T>::zero();
+    const T* Gc = G + (int64_t)c * ld;
+    for (int r = c + 1 + lane; r < ld; r += 32) {
+      const T gv = Gc[r];
+#pragma unroll
+      for (int q = 0; q < RG; ++q) cfma(acc[q], gv, y[(r - c0) * RG + q]);
+    }
+#pragma unroll
+    for (int q = 0; q < RG; ++q) {
+      for (int off = 16; off > 0; off >>= 1) {
+        acc[q].x += __shfl_xor_sync(0xffffffffu, acc[q].x, off);
+        acc[q].y += __shfl_xor_sync(0xffffffffu, acc[q].y, off);
+      }
+    }
+    if (lane == 0) {
+      const int node = cx.sh.order[first + c];
+      const int nx = cx.sh.nx, ny = cx.sh.ny;
+      const int k = node / (nx * ny);
+      const int64_t g = (node % (nx * ny)) + (int64_t)nx * ny * (cx.z0 + k - cx.lead);
+#pragma unroll
+      for (int q = 0; q < RG; ++q) {
+        if (rhs0 + q >= cx.nrhs) continue;
+        const T out = cadd(acc[q], y[(c - c0) * RG + q]);
+        cx.xb[(int64_t)(rhs0 + q) * cx.n_loc + first + c] = out;
+        if (k >= cx.lead) {   // the panel's own planes (Alg. 1.3 extraction)
+          double2* uq = cx.u + (int64_t)(rhs0 + q) * cx.N + g;
+          const double2 o = to_c128(out);
+          *uq = (cx.mode == 0) ? o : csub(*uq, o);
+        }
+      }
+    }
+  }
+}
+
+template <typename T, int RG>
+static void fwd_rg(const SolveTask* tasks, int ntasks, const SolveCtx<T>& cx, int R, int smax, cudaStream_t st) {
+  const size_t smem = ((size_t)smax + 256) * RG * sizeof(T);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_solve_fwd<T, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    attr_set = true;
+  }
+  dim3 grid(ntasks, (cx.nrhs + RG - 1) / RG);
+  k_solve_fwd<T, RG><<<grid, 256, smem, st>>>(tasks, cx, R);
+}
+
+template <typename T, int RG>
+static void bwd_rg(const SolveTask* tasks, int ntasks, const SolveCtx<T>& cx, int ldmax, cudaStream_t st) {
+  const size_t smem = (size_t)ldmax * RG * sizeof(T);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_solve_bwd<T, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    attr_set = true;
+  }
+  dim3 grid(ntasks, (cx.nrhs + RG - 1) / RG);
+  k_solve_bwd<T, RG><<<grid, 256, smem, st>>>(tasks, cx);
+}
+
+// rhs group size so that the shared-memory footprint stays below ~200 KB
+template <typename T>
+static int pick_rg(int nrhs, size_t per_rhs_bytes) {
+  int rg = 8;
+  while (rg > 1 && (rg >= 2 * nrhs || per_rhs_bytes * rg > 200 * 1024)) rg >>= 1;
+  return rg;
+}
+
+template <typename T>
+void launch_solve_fwd(const SolveTask* tasks, int ntasks, const SolveCtx<T>& cx, int R, int smax, cudaStream_t st) {
+  if (ntasks <= 0) return;
+  const int rg = pick_rg<T>(cx.nrhs, ((size_t)smax + 256) * sizeof(T));
+  switch (rg) {
+    case 8: fwd_rg<T, 8>(tasks, ntasks, cx, R, smax, st); break;
+    case 4: fwd_rg<T, 4>(tasks, ntasks, cx, R, smax, st); break;
+    case 2: fwd_rg<T, 2>(tasks, ntasks, cx, R, smax, st); break;
+    default: fwd_rg<T, 1>(tasks, ntasks, cx, R, smax, st); break;
+  }
+}
+
+template <typename T>
+void launch_solve_bwd(const SolveTask* tasks, int ntasks, const SolveCtx<T>& cx, int ldmax, cudaStream_t st) {
+  if (ntasks <= 0) return;
+  const int rg = pick_rg<T>(cx.nrhs, (size_t)ldmax * sizeof(T));
+  switch (rg) {
+    case 8: bwd_rg<T, 8>(tasks, ntasks, cx, ldmax, st); break;
+    case 4: bwd_rg<T, 4>(tasks, ntasks, cx, ldmax, st); break;
+    case 2: bwd_rg<T, 2>(tasks, ntasks, cx, ldmax, st); break;
+    default: bwd_rg<T, 1>(tasks, ntasks, cx, ldmax, st); break;
+  }
+}
+
+template void launch_solve_fwd<double2>(const SolveTask*, int, const SolveCtx<double2>&, int, int, cudaStream_t);
+template void launch_solve_fwd<float2>(const SolveTask*, int, const SolveCtx<float2>&, int, int, cudaStream_t);
+template void launch_solve_bwd<double2>(const SolveTask*, int, const SolveCtx<double2>&, int, cudaStream_t);
+template void launch_solve_bwd<float2>(const SolveTask*, int, const SolveCtx<float2>&, int, cudaStream_t);
+
+}  // namespace psp

@@ -1,0 +1,1115 @@
+// C ABI and host orchestration of the sweeping preconditioner: panel plan and PML tables
+// (§1.1), batched multifrontal setup of every panel (Alg. 1.4, §2.1-§2.2), the sweep (Alg. 1.5)
+// and GMRES(k) (§2.4).  All arithmetic of the path runs in the kernels of this library; the host
+// only plans (symbolic analysis, memory layout, task lists) and sequences launches.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <stdexcept>
+#include <tuple>
+#include <string>
+#include <vector>
+
+#include "cplx.cuh"
+#include "psp_internal.h"
+
+namespace psp {
+
+static thread_local std::string g_last_error;
+
+struct Error {
+  psp_status st;
+  std::string msg;
+};
+
+#define PSP_CK(call)                                                                                       \
+  do {                                                                                                     \
+    cudaError_t e_ = (call);                                                                               \
+    if (e_ != cudaSuccess)                                                                                 \
+      throw Error{e_ == cudaErrorMemoryAllocation ? PSP_ERR_OOM : PSP_ERR_CUDA,                          \
+                  std::string(#call) + ": " + cudaGetErrorString(e_) + " (line " + std::to_string(__LINE__) + ")"}; \
+  } while (0)
+
+// Owning device allocation.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  void alloc(size_t b) {
+    release();
+    if (b == 0) b = 16;
+    PSP_CK(cudaMalloc(&p, b));
+    bytes = b;
+  }
+  void ensure(size_t b) {
+    if (b > bytes) alloc(b);
+  }
+  template <typename U> U* as() const { return static_cast<U*>(p); }
+};
+
+template <typename U>
+static void upload(DevBuf& d, const std::vector<U>& h) {
+  d.alloc(std::max<size_t>(h.size() * sizeof(U), 16));
+  if (!h.empty()) PSP_CK(cudaMemcpy(d.p, h.data(), h.size() * sizeof(U), cudaMemcpyHostToDevice));
+}
+
+static bool is_device_pointer(const void* p) {
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// ---------------------------------------------------------------------------
+// PML tables.  sigma(xi) = C/(g h) * t^2 with t = max(0, ((g+1) h - dist)/(g h)) measured to each
+// PML-carrying wall; stretch s = 1 + i sigma/omega (real omega).  Half-point k sits at xi = k - 1/2;
+// the tables keep 1/s there.
+// ---------------------------------------------------------------------------
+static double sigma_side(double dist, int gam, double C, double h) {
+  if (gam <= 0) return 0.0;
+  double t = ((gam + 1) * h - dist) / (gam * h);
+  if (t <= 0.0) return 0.0;
+  return C / (gam * h) * t * t;
+}
+static double sigma_axis(double xi, int n, int gam, double C, double h, bool lo, bool hi) {
+  double s = 0.0;
+  if (lo) s += sigma_side((xi + 1.0) * h, gam, C, h);
+  if (hi) s += sigma_side((n - xi) * h, gam, C, h);
+  return s;
+}
+static double2 stretch(double sig, double omega) { return make_double2(1.0, sig / omega); }
+static double2 inv_stretch(double sig, double omega) { return cinv(stretch(sig, omega)); }
+
+}  // namespace psp
+
+using namespace psp;
+
+struct psp_ctx_s {
+  // problem
+  int nx = 0, ny = 0, nz = 0;
+  int64_t N = 0;
+  double h = 0, omega = 0, alpha = 0, C = 0;
+  int gamma = 0, depth = 0, pad = 0, leaf = 64, prec = 0, faces = 63, aux_mode = 0;
+  // panels
+  int m = 0;
+  std::vector<int> z0, z1, lead, shape_of;
+  std::vector<int64_t> sn_base;
+  int64_t nfronts = 0;
+  std::vector<Shape> shapes;
+  std::vector<ShapeDev> shdev;
+  std::vector<DevBuf> shape_bufs;
+  DevBuf d_shapes, d_panel_shape;
+  // operators
+  DevBuf d_c, d_gtab, d_ptab, d_boxops;
+  BoxOp opA{}, opJ{};
+  const double2 *s1n = nullptr, *s2n = nullptr, *s3hi = nullptr;
+  // factors
+  DevBuf d_factor;
+  int64_t factor_elems = 0;
+  size_t elem_bytes = 16;
+  std::vector<int64_t> panel_fbase;
+  // solve plan
+  struct LevelPlan {
+    int64_t fwd_off = 0;
+    int nfwd = 0, R = 64, smax = 0;
+    int64_t bwd_off = 0;
+    int nbwd = 0, ldmax = 0;
+  };
+  std::vector<std::vector<LevelPlan>> splan;
+  DevBuf d_stasks;
+  int64_t max_nloc = 0, max_upd = 0;
+  // apply workspaces
+  DevBuf ws_xf, ws_xb, ws_upd;
+  int ws_nrhs = 0;
+  DevBuf stage_in, stage_out;
+  DevBuf d_status;
+  // gmres workspace
+  DevBuf gm;
+  int gm_nrhs = 0, gm_k = 0;
+  int zero_pivot_front = -1;
+};
+
+namespace psp {
+
+// ---------------------------------------------------------------------------
+// first-fit interval allocator used to plan the update-matrix arena
+// ---------------------------------------------------------------------------
+struct ArenaPlanner {
+  std::map<int64_t, int64_t> free_;  // offset -> size
+  int64_t top = 0, peak = 0;
+  int64_t alloc(int64_t n) {
+    n = (n + 15) / 16 * 16;
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= n) {
+        int64_t off = it->first;
+        int64_t rem = it->second - n;
+        free_.erase(it);
+        if (rem > 0) free_[off + n] = rem;
+        return off;
+      }
+    }
+    int64_t off = top;
+    top += n;
+    peak = std::max(peak, top);
+    return off;
+  }
+  void release(int64_t off, int64_t n) {
+    n = (n + 15) / 16 * 16;
+    auto it = free_.emplace(off, n).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+        it = pv;
+      }
+    }
+    if (it->first + it->second == top) {
+      top = it->first;
+      free_.erase(it);
+    }
+  }
+};
+
+static int64_t pad16(int64_t n) { return (n + 15) / 16 * 16; }
+
+// ---------------------------------------------------------------------------
+// Plan and run the factorisation of all panels, level by level (all panels' fronts of one
+// tree level in each launch: the panels are independent, §2).
+// ---------------------------------------------------------------------------
+template <typename T>
+static void factor_all(psp_ctx_s* X, cudaStream_t st) {
+  const int nb = 32;
+  const double tiny = sizeof(T) == 16 ? 1e-300 : 1e-30;
+  int L = 0;
+  for (auto& sh : X->shapes) L = std::max(L, sh.nlevels);
+
+  // --- memory plan ---
+  std::vector<int64_t> uoff(X->nfronts, -1);
+  ArenaPlanner ua;
+  std::vector<std::vector<std::pair<int, int>>> lev_fronts(L);  // (panel, sn)
+  for (int lv = 0; lv < L; ++lv)
+    for (int p = 0; p < X->m; ++p) {
+      const Shape& sh = X->shapes[X->shape_of[p]];
+      if (lv < sh.nlevels)
+        for (int sn : sh.level_sns[lv]) lev_fronts[lv].push_back({p, sn});
+    }
+  int64_t temp_max = 0;
+  for (int lv = 0; lv < L; ++lv) {
+    int64_t tsum = 0;
+    for (auto [p, sn] : lev_fronts[lv]) {
+      const Shape& sh = X->shapes[X->shape_of[p]];
+      const int64_t s = sh.s[sn], u = sh.u[sn];
+      if (u > 0) uoff[X->sn_base[p] + sn] = ua.alloc(u * u);
+      tsum += pad16(s * s) + pad16(u * s);
+    }
+    temp_max = std::max(temp_max, tsum);
+    for (auto [p, sn] : lev_fronts[lv]) {
+      const Shape& sh = X->shapes[X->shape_of[p]];
+      for (int c = sh.child_ptr[sn]; c < sh.child_ptr[sn + 1]; ++c) {
+        const int ch = sh.child_idx[c];
+        ua.release(uoff[X->sn_base[p] + ch], (int64_t)sh.u[ch] * sh.u[ch]);
+      }
+    }
+  }
+  DevBuf d_upd, d_temp;
+  d_upd.alloc((size_t)std::max<int64_t>(ua.peak, 16) * sizeof(T));
+  d_temp.alloc((size_t)std::max<int64_t>(temp_max, 16) * sizeof(T));
+  T* ubase = d_upd.as<T>();
+  T* tbase = d_temp.as<T>();
+  T* fbase = X->d_factor.as<T>();
+  std::vector<T*> upd_ptr(X->nfronts, nullptr);
+  for (int64_t i = 0; i < X->nfronts; ++i)
+    if (uoff[i] >= 0) upd_ptr[i] = ubase + uoff[i];
+  DevBuf d_upd_ptr;
+  upload(d_upd_ptr, upd_ptr);
+
+  // --- task lists ---
+  std::vector<FrontTask<T>> fronts;
+  std::vector<ColTask> ctasks;
+  std::vector<int> dlist;
+  std::vector<GemmTask<T>> gtasks;
+  enum Kind { ASSEMBLE, DIAG, PRIGHT, PLEFT, GEMM, COPY };
+  struct Launch {
+    Kind kind;
+    int64_t front_off;
+    int64_t off;
+    int count;
+    int kb;
+  };
+  std::vector<Launch> launches;
+
+  auto tiles_lower = [&](T* C, int ldc, int M, auto&& emit) {
+    for (int tj = 0; tj < M; tj += 64)
+      for (int ti = tj; ti < M; ti += 64) emit(C, ldc, ti, tj, std::min(64, M - ti), std::min(64, M - tj));
+  };
+
+  for (int lv = 0; lv < L; ++lv) {
+    const int64_t f0 = (int64_t)fronts.size();
+    int smax = 0;
+    int64_t toff = 0;
+    for (auto [p, sn] : lev_fronts[lv]) {
+      const Shape& sh = X->shapes[X->shape_of[p]];
+      FrontTask<T> ft{};
+      ft.s = sh.s[sn];
+      ft.u = sh.u[sn];
+      ft.panel = p;
+      ft.sn = sn;
+      ft.gfid = X->sn_base[p] + sn;
+      ft.G = fbase + X->panel_fbase[p] + sh.g_off[sn];
+      ft.U = upd_ptr[ft.gfid];
+      ft.W = tbase + toff;
+      toff += pad16((int64_t)ft.s * ft.s);
+      ft.Z = tbase + toff;
+      toff += pad16((int64_t)ft.u * ft.s);
+      fronts.push_back(ft);
+      smax = std::max(smax, ft.s);
+    }
+    const int nf = (int)(fronts.size() - f0);
+    // assembly: column chunks of 32 over the full front width
+    {
+      const int64_t c0 = (int64_t)ctasks.size();
+      for (int f = 0; f < nf; ++f) {
+        const auto& ft = fronts[f0 + f];
+        for (int c = 0; c < ft.s + ft.u; c += 32) ctasks.push_back({f, c, std::min(c + 32, ft.s + ft.u)});
+      }
+      launches.push_back({ASSEMBLE, f0, c0, (int)(ctasks.size() - c0), 0});
+    }
+    // blocked LDL^T of F_TL with the inverse of L_TL built alongside in W
+    const int nblk = (smax + nb - 1) / nb;
+    for (int kb = 0; kb < nblk; ++kb) {
+      const int o = kb * nb;
+      const int64_t d0 = (int64_t)dlist.size();
+      for (int f = 0; f < nf; ++f)
+        if (fronts[f0 + f].s > o) dlist.push_back(f);
+      launches.push_back({DIAG, f0, d0, (int)(dlist.size() - d0), kb});
+      const int64_t pr0 = (int64_t)ctasks.size();
+      for (int f = 0; f < nf; ++f) {
+        const auto& ft = fronts[f0 + f];
+        for (int r = o + nb; r < ft.s; r += 64) ctasks.push_back({f, r, std::min(r + 64, ft.s)});
+      }
+      launches.push_back({PRIGHT, f0, pr0, (int)(ctasks.size() - pr0), kb});
+      const int64_t pl0 = (int64_t)ctasks.size();
+      for (int f = 0; f < nf; ++f) {
+        const auto& ft = fronts[f0 + f];
+        if (ft.s <= o) continue;
+        const int cend = std::min(ft.s, o + nb);
+        for (int c = 0; c < cend; c += 64) ctasks.push_back({f, c, std::min(c + 64, cend)});
+      }
+      launches.push_back({PLEFT, f0, pl0, (int)(ctasks.size() - pl0), kb});
+      const int64_t g0 = (int64_t)gtasks.size();
+      for (int f = 0; f < nf; ++f) {
+        const auto& ft = fronts[f0 + f];
+        if (ft.s <= o + nb) continue;
+        const int ld = ft.s + ft.u;
+        const int bs = std::min(nb, ft.s - o);
+        const int t0 = o + nb;  // first row/col of the trailing block
+        // F_TL trailing update: F(r, c) -= L(r, kb) D_kb L(c, kb)^T, lower
+        tiles_lower(ft.G, ld, ft.s - t0, [&](T*, int, int ti, int tj, int mm, int nn) {
+          GemmTask<T> g{};
+          g.C = ft.G + (int64_t)(t0 + tj) * ld + (t0 + ti);
+          g.ldc = ld;
+          g.A = ft.G + (int64_t)o * ld + (t0 + ti);
+          g.lda = ld;
+          g.B = ft.G + (int64_t)o * ld + (t0 + tj);
+          g.ldb = ld;
+          g.d = ft.G + (int64_t)o * ld + o;
+          g.ldd = ld + 1;
+          g.m = mm; g.n = nn; g.k = bs;
+          g.flags = GF_D_MUL | GF_NEG | (ti == tj ? GF_C_LOWER : 0);
+          gtasks.push_back(g);
+        });
+        // W(r, c) -= L(r, kb) W(kb, c) for rows below the block, columns up to its end
+        const int cend = o + bs;
+        for (int tj = 0; tj < cend; tj += 64)
+          for (int ti = t0; ti < ft.s; ti += 64) {
+            GemmTask<T> g{};
+            g.C = ft.W + (int64_t)tj * ft.s + ti;
+            g.ldc = ft.s;
+            g.A = ft.G + (int64_t)o * ld + ti;
+            g.lda = ld;
+            g.B = ft.W + (int64_t)tj * ft.s + o;  // B(n, k) = W[o + k, tj + n]
+            g.ldb = ft.s;
+            g.m = std::min(64, ft.s - ti);
+            g.n = std::min(64, cend - tj);
+            g.k = bs;
+            g.flags = GF_NEG | GF_B_NN;
+            gtasks.push_back(g);
+          }
+      }
+      launches.push_back({GEMM, f0, g0, (int)(gtasks.size() - g0), kb});
+    }
+    // inv(L_TL) into F_TL's strict lower part
+    {
+      const int64_t c0 = (int64_t)ctasks.size();
+      for (int f = 0; f < nf; ++f) {
+        const auto& ft = fronts[f0 + f];
+        for (int c = 0; c < ft.s; c += 16) ctasks.push_back({f, c, std::min(c + 16, ft.s)});
+      }
+      launches.push_back({COPY, f0, c0, (int)(ctasks.size() - c0), 0});
+    }
+    // Z = F_BL inv(L_TL)^T  (= F_BL L^{-T})
+    {
+      const int64_t g0 = (int64_t)gtasks.size();
+      for (int f = 0; f < nf; ++f) {
+        const auto& ft = fronts[f0 + f];
+        if (ft.u == 0) continue;
+        const int ld = ft.s + ft.u;
+        for (int tj = 0; tj < ft.s; tj += 64)
+          for (int ti = 0; ti < ft.u; ti += 64) {
+            GemmTask<T> g{};
+            const int j1 = std::min(tj + 64, ft.s);
+            g.C = ft.Z + (int64_t)tj * ft.u + ti;
+            g.ldc = ft.u;
+            g.A = ft.G + ft.s + ti;  // F_BL rows, k from 0
+            g.lda = ld;
+            g.B = ft.G + tj;         // B(n, k) = Linv[tj + n, k]
+            g.ldb = ld;
+            g.m = std::min(64, ft.u - ti);
+            g.n = j1 - tj;
+            g.k = j1;
+            g.kg0 = 0;
+            g.ng0 = tj;
+            g.flags = GF_BETA0 | GF_B_UNIT_LOWER_NT;
+            gtasks.push_back(g);
+          }
+      }
+      launches.push_back({GEMM, f0, g0, (int)(gtasks.size() - g0), -1});
+    }
+    // F_BR -= Z D^{-1} Z^T (lower) and M_BL = Z D^{-1} inv(L_TL)
+    {
+      const int64_t g0 = (int64_t)gtasks.size();
+      for (int f = 0; f < nf; ++f) {
+        const auto& ft = fronts[f0 + f];
+        if (ft.u == 0) continue;
+        const int ld = ft.s + ft.u;
+        tiles_lower(ft.U, ft.u, ft.u, [&](T*, int, int ti, int tj, int mm, int nn) {
+          GemmTask<T> g{};
+          g.C = ft.U + (int64_t)tj * ft.u + ti;
+          g.ldc = ft.u;
+          g.A = ft.Z + ti;
+          g.lda = ft.u;
+          g.B = ft.Z + tj;
+          g.ldb = ft.u;
+          g.d = ft.G;
+          g.ldd = ld + 1;
+          g.m = mm; g.n = nn; g.k = ft.s;
+          g.flags = GF_D_DIV | GF_NEG | (ti == tj ? GF_C_LOWER : 0);
+          gtasks.push_back(g);
+        });
+        for (int tj = 0; tj < ft.s; tj += 64)
+          for (int ti = 0; ti < ft.u; ti += 64) {
+            GemmTask<T> g{};
+            g.C = ft.G + (int64_t)tj * ld + ft.s + ti;
+            g.ldc = ld;
+            g.A = ft.Z + (int64_t)tj * ft.u + ti;   // A(i, k) = Z[ti + i, tj + k]
+            g.lda = ft.u;
+            g.d = ft.G + (int64_t)tj * (ld + 1);
+            g.ldd = ld + 1;
+            g.B = ft.G + (int64_t)tj * ld + tj;     // B(n, k) = Linv[tj + k, tj + n]
+            g.ldb = ld;
+            g.m = std::min(64, ft.u - ti);
+            g.n = std::min(64, ft.s - tj);
+            g.k = ft.s - tj;
+            g.kg0 = tj;
+            g.ng0 = tj;
+            g.flags = GF_BETA0 | GF_D_DIV | GF_B_NN | GF_B_UNIT_LOWER_NN;
+            gtasks.push_back(g);
+          }
+      }
+      launches.push_back({GEMM, f0, g0, (int)(gtasks.size() - g0), -1});
+    }
+  }
+
+  DevBuf d_fronts, d_ctasks, d_dlist, d_gtasks;
+  upload(d_fronts, fronts);
+  upload(d_ctasks, ctasks);
+  upload(d_dlist, dlist);
+  upload(d_gtasks, gtasks);
+  const FrontTask<T>* F = d_fronts.as<FrontTask<T>>();
+  const ColTask* CT = d_ctasks.as<ColTask>();
+  const int* DL = d_dlist.as<int>();
+  const GemmTask<T>* GT = d_gtasks.as<GemmTask<T>>();
+  int* status = X->d_status.as<int>();
+  PSP_CK(cudaMemsetAsync(status, 0, 4 * sizeof(int), st));
+  for (const auto& l : launches) {
+    switch (l.kind) {
+      case ASSEMBLE:
+        launch_assemble_impl<T>(F + l.front_off, CT + l.off, l.count, X->d_shapes.as<ShapeDev>(),
+                                X->d_boxops.as<BoxOp>(), d_upd_ptr.as<T*>(), X->d_panel_shape.as<int32_t>(), st);
+        break;
+      case DIAG: launch_diag_ldlt<T>(F + l.front_off, DL + l.off, l.count, l.kb, tiny, status, st); break;
+      case PRIGHT: launch_panel_right<T>(F + l.front_off, CT + l.off, l.count, l.kb, st); break;
+      case PLEFT: launch_panel_left<T>(F + l.front_off, CT + l.off, l.count, l.kb, st); break;
+      case GEMM: launch_gemm<T>(GT + l.off, l.count, st); break;
+      case COPY: launch_copy_linv<T>(F + l.front_off, CT + l.off, l.count, st); break;
+    }
+  }
+  PSP_CK(cudaGetLastError());
+  PSP_CK(cudaStreamSynchronize(st));
+  int hs[4];
+  PSP_CK(cudaMemcpy(hs, status, sizeof(hs), cudaMemcpyDeviceToHost));
+  if (hs[0] != 0) {
+    X->zero_pivot_front = hs[0] - 1;
+    throw Error{PSP_ERR_ZERO_PIVOT, "zero pivot in front " + std::to_string(hs[0] - 1)};
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Solve plan: per shape and level, forward row tasks and backward column tasks.
+// ---------------------------------------------------------------------------
+static void plan_solve(psp_ctx_s* X) {
+  std::vector<SolveTask> tasks;
+  X->splan.assign(X->shapes.size(), {});
+  for (size_t si = 0; si < X->shapes.size(); ++si) {
+    const Shape& sh = X->shapes[si];
+    X->splan[si].resize(sh.nlevels);
+    for (int lv = 0; lv < sh.nlevels; ++lv) {
+      auto& P = X->splan[si][lv];
+      int64_t rows = 0, cols = 0;
+      for (int sn : sh.level_sns[lv]) {
+        rows += sh.s[sn] + sh.u[sn];
+        cols += sh.s[sn];
+        P.smax = std::max(P.smax, (int)sh.s[sn]);
+        P.ldmax = std::max(P.ldmax, (int)(sh.s[sn] + sh.u[sn]));
+      }
+      int R = 64;
+      while (R > 8 && rows / R < 608) R >>= 1;
+      P.R = R;
+      int Cc = 64;
+      while (Cc > 8 && cols / Cc < 608) Cc >>= 1;
+      P.fwd_off = (int64_t)tasks.size();
+      for (int sn : sh.level_sns[lv])
+        for (int r = 0; r < sh.s[sn] + sh.u[sn]; r += R) tasks.push_back({sn, r, std::min(r + R, sh.s[sn] + sh.u[sn])});
+      P.nfwd = (int)(tasks.size() - P.fwd_off);
+      P.bwd_off = (int64_t)tasks.size();
+      for (int sn : sh.level_sns[lv])
+        for (int c = 0; c < sh.s[sn]; c += Cc) tasks.push_back({sn, c, std::min(c + Cc, (int)sh.s[sn])});
+      P.nbwd = (int)(tasks.size() - P.bwd_off);
+    }
+  }
+  upload(X->d_stasks, tasks);
+}
+
+template <typename T>
+static void ensure_apply_ws(psp_ctx_s* X, int nrhs) {
+  if (X->ws_nrhs >= nrhs) return;
+  X->ws_xf.alloc((size_t)X->max_nloc * nrhs * sizeof(T));
+  X->ws_xb.alloc((size_t)X->max_nloc * nrhs * sizeof(T));
+  X->ws_upd.alloc((size_t)X->max_upd * nrhs * sizeof(T));
+  X->ws_nrhs = nrhs;
+}
+
+// Alg. 1.5 on a device block u (N x nrhs, in place)
+template <typename T>
+static void apply_impl(psp_ctx_s* X, double2* u, int nrhs, cudaStream_t st) {
+  ensure_apply_ws<T>(X, nrhs);
+  SolveCtx<T> cx{};
+  cx.xf = X->ws_xf.as<T>();
+  cx.xb = X->ws_xb.as<T>();
+  cx.upd = X->ws_upd.as<T>();
+  cx.u = u;
+  cx.N = X->N;
+  cx.nrhs = nrhs;
+  cx.nz = X->nz;
+  cx.s1n = X->s1n;
+  cx.s2n = X->s2n;
+  cx.s3h = X->s3hi;
+  cx.inv_h2 = 1.0 / (X->h * X->h);
+  cx.upd_ld = X->max_upd;
+  cx.n_loc = X->max_nloc;
+  const SolveTask* tasks = X->d_stasks.as<SolveTask>();
+  auto runT = [&](int i, int mode) {
+    const int si = X->shape_of[i];
+    cx.sh = X->shdev[si];
+    cx.G = X->d_factor.as<T>() + X->panel_fbase[i];
+    cx.z0 = X->z0[i];
+    cx.z1 = X->z1[i];
+    cx.lead = X->lead[i];
+    cx.mode = mode;
+    cx.has_prev = i > 0;
+    cx.has_next = i < X->m - 1;
+    const auto& plan = X->splan[si];
+    const int nl = (int)plan.size();
+    for (int lv = 0; lv < nl; ++lv)
+      launch_solve_fwd<T>(tasks + plan[lv].fwd_off, plan[lv].nfwd, cx, plan[lv].R, plan[lv].smax, st);
+    for (int lv = nl - 1; lv >= 0; --lv)
+      launch_solve_bwd<T>(tasks + plan[lv].bwd_off, plan[lv].nbwd, cx, plan[lv].ldmax, st);
+  };
+  for (int i = 0; i < X->m; ++i) runT(i, 0);          // u_i := T_i (u_i - J_{i,i-1} u_{i-1})
+  for (int i = X->m - 2; i >= 0; --i) runT(i, 1);     // u_i -= T_i J_{i+1,i}^T u_{i+1}
+  PSP_CK(cudaGetLastError());
+}
+
+static void apply_dispatch(psp_ctx_s* X, double2* u, int nrhs, cudaStream_t st) {
+  if (X->prec == PSP_PREC_C64) apply_impl<float2>(X, u, nrhs, st);
+  else apply_impl<double2>(X, u, nrhs, st);
+}
+
+// ---------------------------------------------------------------------------
+// setup
+// ---------------------------------------------------------------------------
+static void setup_impl(psp_ctx_s* X, const double* c, cudaStream_t st) {
+  const int nx = X->nx, ny = X->ny, nz = X->nz;
+  X->N = (int64_t)nx * ny * nz;
+  // wave speed (host or device input)
+  X->d_c.alloc(X->N * sizeof(double));
+  PSP_CK(cudaMemcpyAsync(X->d_c.p, c, X->N * sizeof(double), cudaMemcpyDefault, st));
+
+  // global stretch tables: s1n, 1/s1h, s2n, 1/s2h, s3n, 1/s3h
+  const bool f[6] = {bool(X->faces & 1), bool(X->faces & 2), bool(X->faces & 4),
+                     bool(X->faces & 8), bool(X->faces & 16), bool(X->faces & 32)};
+  const int dims[3] = {nx, ny, nz};
+  std::vector<double2> gt;
+  int64_t goff[6];
+  for (int a = 0; a < 3; ++a) {
+    const int n = dims[a];
+    goff[2 * a] = (int64_t)gt.size();
+    for (int i = 0; i < n; ++i)
+      gt.push_back(stretch(sigma_axis(i, n, X->gamma, X->C, X->h, f[2 * a], f[2 * a + 1]), X->omega));
+    goff[2 * a + 1] = (int64_t)gt.size();
+    for (int k = 0; k <= n; ++k)
+      gt.push_back(inv_stretch(sigma_axis(k - 0.5, n, X->gamma, X->C, X->h, f[2 * a], f[2 * a + 1]), X->omega));
+  }
+  // panel plan (§1.1, Alg. 1.4): panel 0 = [0, gamma + d), then d planes each
+  X->z0.clear(); X->z1.clear(); X->lead.clear();
+  {
+    int first = std::min(X->gamma + X->depth, nz);
+    X->z0.push_back(0);
+    X->z1.push_back(first);
+    for (int z = first; z < nz; z += X->depth) {
+      X->z0.push_back(z);
+      X->z1.push_back(std::min(z + X->depth, nz));
+    }
+  }
+  X->m = (int)X->z0.size();
+  // per-panel tables: s3 nodes, 1/s3 half-points, c plane map (device-global layout appended to gt)
+  std::vector<int32_t> cplane_all;
+  std::vector<int64_t> p_s3n(X->m), p_s3h(X->m), p_cpl(X->m);
+  std::map<std::tuple<int, int, int>, int> shape_idx;
+  X->shape_of.assign(X->m, 0);
+  for (int i = 0; i < X->m; ++i) {
+    const int z0 = X->z0[i], z1 = X->z1[i];
+    int lead;
+    if (z0 == 0) lead = 0;
+    else if (X->aux_mode == PSP_AUX_EXACT) lead = z0;
+    else lead = X->pad;
+    X->lead.push_back(lead);
+    const int D = lead + (z1 - z0);
+    p_s3n[i] = (int64_t)gt.size();
+    for (int k = 0; k < D; ++k) {
+      double sig;
+      if (z0 == 0 || X->aux_mode == PSP_AUX_EXACT) {
+        sig = sigma_axis(k + (z0 - lead), nz, X->gamma, X->C, X->h, f[4], f[5]);
+      } else {
+        sig = sigma_side((k + 1.0) * X->h, X->pad, X->C, X->h);
+        if (k >= lead) sig += sigma_axis(z0 + k - lead, nz, X->gamma, X->C, X->h, f[4], f[5]);
+      }
+      gt.push_back(stretch(sig, X->omega));
+    }
+    p_s3h[i] = (int64_t)gt.size();
+    for (int k = 0; k <= D; ++k) {
+      const double xi = k - 0.5;
+      double sig;
+      if (z0 == 0 || X->aux_mode == PSP_AUX_EXACT) {
+        sig = sigma_axis(xi + (z0 - lead), nz, X->gamma, X->C, X->h, f[4], f[5]);
+      } else {
+        sig = sigma_side((xi + 1.0) * X->h, X->pad, X->C, X->h);
+        if (xi >= lead - 0.5) sig += sigma_axis(z0 + xi - lead, nz, X->gamma, X->C, X->h, f[4], f[5]);
+      }
+      gt.push_back(inv_stretch(sig, X->omega));
+    }
+    p_cpl[i] = (int64_t)cplane_all.size();
+    for (int k = 0; k < D; ++k) cplane_all.push_back(k < lead && X->aux_mode != PSP_AUX_EXACT ? z0 : z0 - lead + k);
+    auto key = std::make_tuple(nx, ny, D);
+    auto it = shape_idx.find(key);
+    if (it == shape_idx.end()) {
+      const int idx = (int)X->shapes.size();
+      shape_idx[key] = idx;
+      X->shapes.emplace_back();
+      build_shape(X->shapes.back(), nx, ny, D, X->leaf);
+      X->shape_of[i] = idx;
+    } else {
+      X->shape_of[i] = it->second;
+    }
+  }
+  // global plane map (identity) for the full-domain operators
+  const int64_t gcpl = (int64_t)cplane_all.size();
+  for (int k = 0; k < nz; ++k) cplane_all.push_back(k);
+
+  upload(X->d_gtab, gt);
+  upload(X->d_ptab, cplane_all);
+  const double2* G = X->d_gtab.as<double2>();
+  const int32_t* CP = X->d_ptab.as<int32_t>();
+  X->s1n = G + goff[0];
+  X->s2n = G + goff[2];
+  X->s3hi = G + goff[5];
+  auto make_op = [&](int bz, double2 k2num, const int32_t* cpl, const double2* s3n, const double2* s3h) {
+    BoxOp op{};
+    op.nx = nx; op.ny = ny; op.nz = bz;
+    op.inv_h2 = 1.0 / (X->h * X->h);
+    op.k2num = k2num;
+    op.c = X->d_c.as<double>();
+    op.cplane = cpl;
+    op.s1n = G + goff[0]; op.s1h = G + goff[1];
+    op.s2n = G + goff[2]; op.s2h = G + goff[3];
+    op.s3n = s3n; op.s3h = s3h;
+    return op;
+  };
+  const double2 k2A = make_double2(X->omega * X->omega, 0.0);
+  const double2 k2J = make_double2(X->omega * X->omega - X->alpha * X->alpha, 2.0 * X->omega * X->alpha);
+  X->opA = make_op(nz, k2A, CP + gcpl, G + goff[4], G + goff[5]);
+  X->opJ = make_op(nz, k2J, CP + gcpl, G + goff[4], G + goff[5]);
+  std::vector<BoxOp> bops(X->m);
+  for (int i = 0; i < X->m; ++i)
+    bops[i] = make_op(X->lead[i] + X->z1[i] - X->z0[i], k2J, CP + p_cpl[i], G + p_s3n[i], G + p_s3h[i]);
+  upload(X->d_boxops, bops);
+
+  // shapes to the device
+  X->shape_bufs.clear();
+  X->shdev.clear();
+  X->max_nloc = 0;
+  X->max_upd = 0;
+  for (auto& sh : X->shapes) {
+    X->max_nloc = std::max<int64_t>(X->max_nloc, (int64_t)sh.nx * sh.ny * sh.nz);
+    X->max_upd = std::max<int64_t>(X->max_upd, sh.upd_total);
+    // pack all arrays of the shape into one buffer
+    std::vector<char> blob;
+    auto put = [&](const void* src, size_t bytes) {
+      size_t off = (blob.size() + 15) / 16 * 16;
+      blob.resize(off + bytes);
+      if (bytes) std::memcpy(blob.data() + off, src, bytes);
+      return off;
+    };
+    size_t o_order = put(sh.order.data(), sh.order.size() * 4);
+    size_t o_elim = put(sh.elim.data(), sh.elim.size() * 4);
+    size_t o_first = put(sh.first.data(), sh.first.size() * 4);
+    size_t o_s = put(sh.s.data(), sh.s.size() * 4);
+    size_t o_u = put(sh.u.data(), sh.u.size() * 4);
+    size_t o_cp = put(sh.child_ptr.data(), sh.child_ptr.size() * 4);
+    size_t o_ci = put(sh.child_idx.data(), sh.child_idx.size() * 4);
+    size_t o_sp = put(sh.struct_ptr.data(), sh.struct_ptr.size() * 8);
+    size_t o_se = put(sh.struct_elim.data(), sh.struct_elim.size() * 4);
+    size_t o_rel = put(sh.rel.data(), sh.rel.size() * 4);
+    size_t o_pp = put(sh.pull_ptr.data(), sh.pull_ptr.size() * 8);
+    size_t o_pl = put(sh.pull.data(), sh.pull.size() * 4);
+    size_t o_go = put(sh.g_off.data(), sh.g_off.size() * 8);
+    size_t o_uo = put(sh.upd_off.data(), sh.upd_off.size() * 8);
+    DevBuf b;
+    b.alloc(blob.size());
+    PSP_CK(cudaMemcpy(b.p, blob.data(), blob.size(), cudaMemcpyHostToDevice));
+    char* base = b.as<char>();
+    ShapeDev d{};
+    d.nx = sh.nx; d.ny = sh.ny; d.nz = sh.nz; d.nsn = sh.nsn;
+    d.order = (const int32_t*)(base + o_order);
+    d.elim = (const int32_t*)(base + o_elim);
+    d.first = (const int32_t*)(base + o_first);
+    d.s = (const int32_t*)(base + o_s);
+    d.u = (const int32_t*)(base + o_u);
+    d.child_ptr = (const int32_t*)(base + o_cp);
+    d.child_idx = (const int32_t*)(base + o_ci);
+    d.struct_ptr = (const int64_t*)(base + o_sp);
+    d.struct_elim = (const int32_t*)(base + o_se);
+    d.rel = (const int32_t*)(base + o_rel);
+    d.pull_ptr = (const int64_t*)(base + o_pp);
+    d.pull = (const int32_t*)(base + o_pl);
+    d.g_off = (const int64_t*)(base + o_go);
+    d.upd_off = (const int64_t*)(base + o_uo);
+    X->shdev.push_back(d);
+    X->shape_bufs.push_back(std::move(b));
+  }
+  upload(X->d_shapes, X->shdev);
+  std::vector<int32_t> ps(X->shape_of.begin(), X->shape_of.end());
+  upload(X->d_panel_shape, ps);
+
+  // front ids and factor slabs
+  X->sn_base.assign(X->m, 0);
+  X->panel_fbase.assign(X->m, 0);
+  int64_t nf = 0, fe = 0;
+  for (int i = 0; i < X->m; ++i) {
+    const Shape& sh = X->shapes[X->shape_of[i]];
+    X->sn_base[i] = nf;
+    nf += sh.nsn;
+    X->panel_fbase[i] = fe;
+    fe += sh.g_total;
+  }
+  X->nfronts = nf;
+  X->factor_elems = fe;
+  X->elem_bytes = X->prec == PSP_PREC_C64 ? 8 : 16;
+  X->d_factor.alloc((size_t)fe * X->elem_bytes);
+  X->d_status.alloc(4 * sizeof(int));
+  plan_solve(X);
+  if (X->prec == PSP_PREC_C64) factor_all<float2>(X, st);
+  else factor_all<double2>(X, st);
+}
+
+// ---------------------------------------------------------------------------
+// GMRES(k), right preconditioned, x0 = 0, complex128 (§2.4, §3)
+// ---------------------------------------------------------------------------
+static void solve_impl(psp_ctx_s* X, const double2* f, double2* x, int nrhs, double tol, int k, int maxit,
+                       psp_solve_info* info, cudaStream_t st) {
+  const int64_t N = X->N;
+  const int K = k;
+  // workspace layout (double2 elements)
+  const int64_t nV = (int64_t)(K + 1) * nrhs * N, nZ = (int64_t)K * nrhs * N, nW = (int64_t)nrhs * N;
+  const int64_t nB = nW;
+  const int64_t nH = (int64_t)(K + 1) * K * nrhs, nSn = (int64_t)K * nrhs, nG = (int64_t)(K + 1) * nrhs;
+  const int64_t nPart = (int64_t)304 * (K + 1) * nrhs, nDot = (int64_t)(K + 1) * nrhs;
+  const int64_t total = nV + nZ + nW + nB + nH + nSn + nG + nPart + 3 * nDot + 3 * nrhs + (int64_t)K * nrhs + 64;
+  X->gm.ensure((size_t)total * sizeof(double2) + (size_t)(K + 8) * nrhs * sizeof(double) + 4 * nrhs * sizeof(int));
+  double2* base = X->gm.as<double2>();
+  double2* V = base;
+  double2* Z = V + nV;
+  double2* w = Z + nZ;
+  double2* b = w + nW;
+  double2* Hm = b + nB;
+  double2* sn = Hm + nH;
+  double2* g = sn + nSn;
+  double2* part = g + nG;
+  double2* h1 = part + nPart;
+  double2* h2 = h1 + nDot;
+  double2* nrm = h2 + nDot;
+  double2* scl = nrm + nDot;
+  double2* ybuf = scl + 3 * nrhs;
+  double* cs = reinterpret_cast<double*>(ybuf + (int64_t)K * nrhs + 64);
+  double* resid = cs + (int64_t)K * nrhs;
+  int* active = reinterpret_cast<int*>(resid + 8 * nrhs);
+  int* jr = active + nrhs;
+
+  LsqState Ls{};
+  Ls.H = Hm; Ls.cs = cs; Ls.sn = sn; Ls.g = g; Ls.resid = resid; Ls.scl = scl; Ls.active = active;
+  Ls.k = K; Ls.nrhs = nrhs;
+  const int64_t ldv_vec = (int64_t)nrhs * N;
+
+  auto t0 = std::chrono::steady_clock::now();
+  launch_scale_rhs(X->opA, f, b, nrhs, N, st);
+  // ||b||
+  std::vector<double> bnorm(nrhs), rel(nrhs, 1.0), hres(nrhs);
+  std::vector<int> act(nrhs, 1), its(nrhs, 0), restarts(nrhs, 0), jrh(nrhs, 0);
+  launch_multidot(b, 0, N, 1, b, N, nrhs, N, part, nrm, st);
+  std::vector<double2> hn(nrhs);
+  PSP_CK(cudaMemcpyAsync(hn.data(), nrm, nrhs * sizeof(double2), cudaMemcpyDeviceToHost, st));
+  PSP_CK(cudaStreamSynchronize(st));
+  for (int r = 0; r < nrhs; ++r) {
+    bnorm[r] = std::sqrt(std::max(hn[r].x, 0.0));
+    if (bnorm[r] == 0.0) { act[r] = 0; rel[r] = 0.0; }
+  }
+  PSP_CK(cudaMemsetAsync(x, 0, nW * sizeof(double2), st));
+  PSP_CK(cudaMemcpyAsync(w, b, nW * sizeof(double2), cudaMemcpyDeviceToDevice, st));  // r = b - A*0
+  int applies = 0, total_it = 0;
+  bool any = std::any_of(act.begin(), act.end(), [](int a) { return a != 0; });
+  while (any && total_it < maxit) {
+    PSP_CK(cudaMemcpyAsync(active, act.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
+    // V_0 = r / ||r||
+    launch_multidot(w, 0, N, 1, w, N, nrhs, N, part, nrm, st);
+    launch_cycle_start(Ls, nrm, st);
+    launch_axpby_batch(w, V, N, nrhs, scl, 0, st);
+    for (int r = 0; r < nrhs; ++r) jrh[r] = 0;
+    int j = 0;
+    for (; j < K && total_it < maxit; ++j) {
+      double2* Vj = V + (int64_t)j * ldv_vec;
+      double2* Zj = Z + (int64_t)j * ldv_vec;
+      PSP_CK(cudaMemcpyAsync(Zj, Vj, nW * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+      apply_dispatch(X, Zj, nrhs, st);   // z_j = M^{-1} v_j
+      ++applies;
+      launch_matvec(X->opA, Zj, w, nrhs, N, st);  // w = A z_j
+      // classical Gram-Schmidt, twice
+      launch_multidot(V, ldv_vec, N, j + 1, w, N, nrhs, N, part, h1, st);
+      launch_multiaxpy(V, ldv_vec, N, j + 1, h1, w, N, nrhs, N, -1.0, st);
+      launch_multidot(V, ldv_vec, N, j + 1, w, N, nrhs, N, part, h2, st);
+      launch_multiaxpy(V, ldv_vec, N, j + 1, h2, w, N, nrhs, N, -1.0, st);
+      launch_multidot(w, 0, N, 1, w, N, nrhs, N, part, nrm, st);
+      launch_arnoldi_step(Ls, j, h1, h2, nrm, st);
+      launch_axpby_batch(w, V + (int64_t)(j + 1) * ldv_vec, N, nrhs, scl, 0, st);
+      PSP_CK(cudaMemcpyAsync(hres.data(), resid, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+      PSP_CK(cudaStreamSynchronize(st));
+      ++total_it;
+      bool all_done = true;
+      for (int r = 0; r < nrhs; ++r) {
+        if (!act[r]) continue;
+        its[r]++;
+        jrh[r] = j + 1;
+        if (hres[r] / bnorm[r] < tol) act[r] = 0;   // converged within the cycle (estimate)
+        else all_done = false;
+      }
+      PSP_CK(cudaMemcpyAsync(active, act.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
+      if (all_done) { ++j; break; }
+    }
+    // x += Z y for every rhs that iterated in this cycle
+    PSP_CK(cudaMemcpyAsync(jr, jrh.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
+    launch_backsolve(Ls, jr, ybuf, st);
+    launch_multiaxpy(Z, ldv_vec, N, K, ybuf, x, N, nrhs, N, 1.0, st);
+    // true residual r = b - A x
+    launch_matvec(X->opA, x, w, nrhs, N, st);
+    launch_axpby_batch(b, w, N, nrhs, nullptr, 1, st);
+    launch_multidot(w, 0, N, 1, w, N, nrhs, N, part, nrm, st);
+    PSP_CK(cudaMemcpyAsync(hn.data(), nrm, nrhs * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    PSP_CK(cudaStreamSynchronize(st));
+    any = false;
+    for (int r = 0; r < nrhs; ++r) {
+      if (bnorm[r] == 0.0) continue;
+      if (jrh[r] > 0) restarts[r]++;
+      rel[r] = std::sqrt(std::max(hn[r].x, 0.0)) / bnorm[r];
+      act[r] = rel[r] >= tol ? 1 : 0;
+      if (act[r]) any = true;
+    }
+  }
+  auto t1 = std::chrono::steady_clock::now();
+  const double relmax = *std::max_element(rel.begin(), rel.end());
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->iterations = *std::max_element(its.begin(), its.end());
+    info->restarts = *std::max_element(restarts.begin(), restarts.end());
+    info->converged = relmax < tol;
+    info->applies = applies;
+    info->relres_max = relmax;
+    info->solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    info->status_front = -1;
+  }
+  if (!(relmax < tol)) throw Error{PSP_ERR_NOT_CONVERGED, "GMRES reached maxit with relative residual " + std::to_string(relmax)};
+}
+
+}  // namespace psp
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void psp_default_options(psp_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->pml_C = 4.0;
+  o->alpha = 2.0 * M_PI;
+  o->pad_depth = -1;
+  o->leaf_size = 64;
+  o->precision = PSP_PREC_C128;
+  o->pml_faces = 63;
+  o->aux_mode = PSP_AUX_MOVING_PML;
+}
+
+const char* psp_status_string(psp_status s) {
+  switch (s) {
+    case PSP_OK: return "ok";
+    case PSP_ERR_ARG: return "invalid argument";
+    case PSP_ERR_OOM: return "out of memory";
+    case PSP_ERR_CUDA: return "CUDA error";
+    case PSP_ERR_ZERO_PIVOT: return "zero pivot";
+    case PSP_ERR_NOT_CONVERGED: return "not converged";
+    case PSP_ERR_TIMEOUT: return "device wait timed out";
+    case PSP_ERR_STATE: return "invalid handle state";
+  }
+  return "unknown status";
+}
+
+const char* psp_last_error(void) { return g_last_error.c_str(); }
+
+static psp_status fail(psp_status s, const std::string& m) {
+  g_last_error = m;
+  return s;
+}
+
+#define PSP_TRY try {
+#define PSP_CATCH                                                          \
+  }                                                                        \
+  catch (const Error& e) { return fail(e.st, e.msg); }                     \
+  catch (const std::bad_alloc&) { return fail(PSP_ERR_OOM, "host allocation failed"); } \
+  catch (const std::exception& e) { return fail(PSP_ERR_STATE, e.what()); }
+
+psp_status psp_setup(const psp_grid* g, const double* c, double omega, int pml_gamma, int panel_depth,
+                     const psp_options* opt, void* stream, psp_handle* out) {
+  if (!out) return fail(PSP_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!g || !c) return fail(PSP_ERR_ARG, "grid or c is NULL");
+  if (g->nx < 1 || g->ny < 1 || g->nz < 1 || !(g->h > 0)) return fail(PSP_ERR_ARG, "bad grid");
+  if ((int64_t)g->nx * g->ny * g->nz > (int64_t)1 << 31) return fail(PSP_ERR_ARG, "grid too large");
+  if (!(omega > 0) || pml_gamma < 0 || panel_depth < 1) return fail(PSP_ERR_ARG, "bad omega, gamma or panel depth");
+  psp_options o;
+  psp_default_options(&o);
+  if (opt) o = *opt;
+  if (o.leaf_size < 1 || o.pml_faces < 0 || o.pml_faces > 63 || (o.precision != PSP_PREC_C128 && o.precision != PSP_PREC_C64) ||
+      (o.aux_mode != PSP_AUX_MOVING_PML && o.aux_mode != PSP_AUX_EXACT) || !(o.alpha >= 0) || !(o.pml_C >= 0))
+    return fail(PSP_ERR_ARG, "bad options");
+  psp_ctx_s* X = nullptr;
+  try {
+    X = new psp_ctx_s();
+  } catch (...) {
+    return fail(PSP_ERR_OOM, "host allocation failed");
+  }
+  X->nx = g->nx; X->ny = g->ny; X->nz = g->nz; X->h = g->h;
+  X->omega = omega; X->alpha = o.alpha; X->C = o.pml_C;
+  X->gamma = pml_gamma; X->depth = panel_depth;
+  X->pad = o.pad_depth < 0 ? pml_gamma : o.pad_depth;
+  X->leaf = o.leaf_size; X->prec = o.precision; X->faces = o.pml_faces; X->aux_mode = o.aux_mode;
+  *out = X;
+  PSP_TRY
+  setup_impl(X, c, (cudaStream_t)stream);
+  return PSP_OK;
+  PSP_CATCH
+}
+
+psp_status psp_apply(psp_handle X, const double* rhs, double* out, int nrhs, void* stream) {
+  if (!X || !rhs || !out || nrhs < 1) return fail(PSP_ERR_ARG, "bad apply arguments");
+  if (!X->d_factor.p) return fail(PSP_ERR_STATE, "handle has no factorisation");
+  PSP_TRY
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = (size_t)X->N * nrhs * sizeof(double2);
+  const bool dev_out = is_device_pointer(out);
+  double2* u;
+  if (dev_out) {
+    u = reinterpret_cast<double2*>(out);
+  } else {
+    X->stage_out.ensure(bytes);
+    u = X->stage_out.as<double2>();
+  }
+  if ((const void*)rhs != (const void*)u) PSP_CK(cudaMemcpyAsync(u, rhs, bytes, cudaMemcpyDefault, st));
+  apply_dispatch(X, u, nrhs, st);
+  if (!dev_out) {
+    PSP_CK(cudaMemcpyAsync(out, u, bytes, cudaMemcpyDeviceToHost, st));
+    PSP_CK(cudaStreamSynchronize(st));
+  }
+  return PSP_OK;
+  PSP_CATCH
+}
+
+psp_status psp_matvec(psp_handle X, int which, const double* x, double* y, int nrhs, void* stream) {
+  if (!X || !x || !y || nrhs < 1 || (which != 0 && which != 1)) return fail(PSP_ERR_ARG, "bad matvec arguments");
+  PSP_TRY
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = (size_t)X->N * nrhs * sizeof(double2);
+  const double2* xd = reinterpret_cast<const double2*>(x);
+  if (!is_device_pointer(x)) {
+    X->stage_in.ensure(bytes);
+    PSP_CK(cudaMemcpyAsync(X->stage_in.p, x, bytes, cudaMemcpyHostToDevice, st));
+    xd = X->stage_in.as<double2>();
+  }
+  const bool dev_out = is_device_pointer(y);
+  double2* yd = reinterpret_cast<double2*>(y);
+  if (!dev_out) {
+    X->stage_out.ensure(bytes);
+    yd = X->stage_out.as<double2>();
+  }
+  if ((const void*)xd == (const void*)yd) return fail(PSP_ERR_ARG, "matvec cannot run in place");
+  launch_matvec(which == 0 ? X->opA : X->opJ, xd, yd, nrhs, X->N, st);
+  PSP_CK(cudaGetLastError());
+  if (!dev_out) {
+    PSP_CK(cudaMemcpyAsync(y, yd, bytes, cudaMemcpyDeviceToHost, st));
+    PSP_CK(cudaStreamSynchronize(st));
+  }
+  return PSP_OK;
+  PSP_CATCH
+}
+
+psp_status psp_solve(psp_handle X, const double* f, double* u, int nrhs, double tol, int k, int maxit,
+                     psp_solve_info* info, void* stream) {
+  if (!X || !f || !u || nrhs < 1 || !(tol > 0) || k < 1 || maxit < 1) return fail(PSP_ERR_ARG, "bad solve arguments");
+  if (!X->d_factor.p) return fail(PSP_ERR_STATE, "handle has no factorisation");
+  PSP_TRY
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = (size_t)X->N * nrhs * sizeof(double2);
+  const double2* fd = reinterpret_cast<const double2*>(f);
+  if (!is_device_pointer(f)) {
+    X->stage_in.ensure(bytes);
+    PSP_CK(cudaMemcpyAsync(X->stage_in.p, f, bytes, cudaMemcpyHostToDevice, st));
+    fd = X->stage_in.as<double2>();
+  }
+  const bool dev_out = is_device_pointer(u);
+  double2* ud = reinterpret_cast<double2*>(u);
+  if (!dev_out) {
+    X->stage_out.ensure(bytes);
+    ud = X->stage_out.as<double2>();
+  }
+  psp_status rs = PSP_OK;
+  try {
+    solve_impl(X, fd, ud, nrhs, tol, k, maxit, info, st);
+  } catch (const Error& e) {
+    if (e.st != PSP_ERR_NOT_CONVERGED) throw;
+    rs = fail(e.st, e.msg);
+  }
+  if (!dev_out) {
+    PSP_CK(cudaMemcpyAsync(u, ud, bytes, cudaMemcpyDeviceToHost, st));
+    PSP_CK(cudaStreamSynchronize(st));
+  }
+  return rs;
+  PSP_CATCH
+}
+
+psp_status psp_symbolic_export(psp_handle X, int panel, int32_t* buf, size_t* len) {
+  if (!X || !len || panel < 0 || panel >= X->m) return fail(PSP_ERR_ARG, "bad panel");
+  const Shape& sh = X->shapes[X->shape_of[panel]];
+  size_t n = 5;
+  for (int f = 0; f < sh.nsn; ++f) n += 3 + sh.s[f] + sh.u[f];
+  if (!buf) {
+    *len = n;
+    return PSP_OK;
+  }
+  if (*len < n) return fail(PSP_ERR_ARG, "buffer too small");
+  size_t p = 0;
+  buf[p++] = sh.nx; buf[p++] = sh.ny; buf[p++] = sh.nz; buf[p++] = X->lead[panel]; buf[p++] = sh.nsn;
+  for (int f = 0; f < sh.nsn; ++f) {
+    buf[p++] = sh.s[f];
+    buf[p++] = sh.u[f];
+    buf[p++] = sh.parent[f];
+    for (int e = sh.first[f]; e < sh.first[f] + sh.s[f]; ++e) buf[p++] = sh.order[e];
+    for (int64_t a = sh.struct_ptr[f]; a < sh.struct_ptr[f + 1]; ++a) buf[p++] = sh.order[sh.struct_elim[a]];
+  }
+  *len = n;
+  return PSP_OK;
+}
+
+psp_status psp_info(psp_handle X, int* panels, int64_t* fronts, int64_t* factor_bytes) {
+  if (!X) return fail(PSP_ERR_ARG, "NULL handle");
+  if (panels) *panels = X->m;
+  if (fronts) *fronts = X->nfronts;
+  if (factor_bytes) *factor_bytes = X->factor_elems * (int64_t)X->elem_bytes;
+  return PSP_OK;
+}
+
+psp_status psp_export_front(psp_handle X, int panel, int sn, double* buf, int* s, int* u) {
+  if (!X || panel < 0 || panel >= X->m) return fail(PSP_ERR_ARG, "bad panel");
+  const Shape& sh = X->shapes[X->shape_of[panel]];
+  if (sn < 0 || sn >= sh.nsn) return fail(PSP_ERR_ARG, "bad supernode");
+  if (s) *s = sh.s[sn];
+  if (u) *u = sh.u[sn];
+  if (!buf) return PSP_OK;
+  PSP_TRY
+  const int64_t n = (int64_t)(sh.s[sn] + sh.u[sn]) * sh.s[sn];
+  const char* src = X->d_factor.as<char>() + (X->panel_fbase[panel] + sh.g_off[sn]) * (int64_t)X->elem_bytes;
+  if (X->elem_bytes == 16) {
+    PSP_CK(cudaMemcpy(buf, src, n * 16, cudaMemcpyDeviceToHost));
+  } else {
+    std::vector<float> tmp(2 * n);
+    PSP_CK(cudaMemcpy(tmp.data(), src, n * 8, cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < 2 * n; ++i) buf[i] = tmp[i];
+  }
+  return PSP_OK;
+  PSP_CATCH
+}
+
+psp_status psp_destroy(psp_handle X) {
+  if (!X) return PSP_OK;
+  delete X;
+  return PSP_OK;
+}
+
+}  // extern "C"

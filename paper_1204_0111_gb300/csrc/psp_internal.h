@@ -1,0 +1,208 @@
+// Internal declarations shared by the translation units of libpsp.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "psp.h"
+
+namespace psp {
+
+// ---------------------------------------------------------------------------
+// Symbolic analysis of one auxiliary-problem box (nx x ny x depth): the
+// supernodal nested-dissection tree of §2.1 (separator-tree figure), postorder.
+// ---------------------------------------------------------------------------
+struct Shape {
+  int nx = 0, ny = 0, nz = 0;  // box extents (nz = depth of the auxiliary problem)
+  int leaf = 0;
+  int nsn = 0;
+  std::vector<int32_t> order;       // elimination index -> box node id
+  std::vector<int32_t> elim;        // box node id -> elimination index
+  std::vector<int32_t> first;       // nsn + 1: elimination index of each supernode's first node
+  std::vector<int32_t> s, u;        // supernode size, |struct(S)|
+  std::vector<int32_t> parent;      // -1 for the root
+  std::vector<int32_t> child_ptr, child_idx;
+  std::vector<int64_t> struct_ptr;  // nsn + 1 offsets into struct_elim / rel
+  std::vector<int32_t> struct_elim; // struct(S) as sorted elimination indices
+  std::vector<int32_t> rel;         // position of each struct entry in the parent's front rows
+  std::vector<int32_t> height;      // leaves 0, parent = 1 + max(children)
+  int nlevels = 0;
+  std::vector<std::vector<int32_t>> level_sns;
+  // solve-side pull map: for each front row position p of S u struct(S), up to two
+  // offsets (within the per-panel update-vector slab) of children's update entries
+  std::vector<int64_t> pull_ptr;    // nsn + 1, = sum (s + u)
+  std::vector<int32_t> pull;        // 2 per position, -1 = none
+  // per-panel layouts
+  std::vector<int64_t> g_off;       // G block offset within a panel's factor slab (elements)
+  int64_t g_total = 0;
+  std::vector<int64_t> upd_off;     // update-vector offset within the panel's update slab
+  int64_t upd_total = 0;
+};
+
+void build_shape(Shape& sh, int nx, int ny, int nz, int leaf);
+
+// ---------------------------------------------------------------------------
+// Device views
+// ---------------------------------------------------------------------------
+struct ShapeDev {
+  int nx, ny, nz, nsn;
+  const int32_t* order;
+  const int32_t* elim;
+  const int32_t* first;
+  const int32_t* s;
+  const int32_t* u;
+  const int32_t* child_ptr;
+  const int32_t* child_idx;
+  const int64_t* struct_ptr;
+  const int32_t* struct_elim;
+  const int32_t* rel;
+  const int64_t* pull_ptr;
+  const int32_t* pull;
+  const int64_t* g_off;
+  const int64_t* upd_off;
+};
+
+// 7-point operator on a box: -sum_j d_j(a_j d_j u) - k2num / c^2 * s1 s2 s3 u (Eq. (1.1)/(1.5),
+// s1 s2 s3-scaled).  Stretch tables are complex; half[k] sits between node k-1 and node k.
+struct BoxOp {
+  int nx, ny, nz;
+  double inv_h2;
+  double2 k2num;            // omega^2 (A) or (omega + i alpha)^2 (J)
+  const double* c;          // global wave speed, nx*ny*nz_global
+  const int32_t* cplane;    // box plane -> global plane whose c is used
+  const double2* s1n;
+  const double2* s1h;
+  const double2* s2n;
+  const double2* s2h;
+  const double2* s3n;
+  const double2* s3h;
+};
+
+// One panel's auxiliary problem (Alg. 1.4) as seen by the apply kernels.
+struct PanelDev {
+  int z0, z1, lead;         // global planes [z0, z1); lead pad (or exact-mode) planes before them
+  int shape;
+  int64_t sn_base;          // global front id of supernode 0
+};
+
+enum GemmFlags : int {
+  GF_BETA0 = 1,           // C = alpha * A B^T (do not read C)
+  GF_C_LOWER = 2,         // write only local row >= local col (diagonal tiles)
+  GF_B_NN = 4,            // B(n,k) = B[k + n ldb]   (default NT: B[n + k ldb])
+  GF_B_UNIT_LOWER_NT = 8, // B(n,k) is T[n,k] of a unit lower T stored with D on its diagonal
+  GF_B_UNIT_LOWER_NN = 16,// B(n,k) is T[k,n] of a unit lower T stored with D on its diagonal
+  GF_D_MUL = 32,          // scale A(:,k) by d(k)
+  GF_D_DIV = 64,          // scale A(:,k) by 1/d(k)
+  GF_NEG = 128            // alpha = -1 (else +1)
+};
+
+// C(m x n) (+)= alpha * A(m x k) * diag(d)^{+-1} * B(n x k)^T ; pointers already offset.
+template <typename T>
+struct GemmTask {
+  T* C;
+  const T* A;
+  const T* B;
+  const T* d;
+  int ldc, lda, ldb, ldd;
+  int m, n, k;
+  int kg0, ng0;   // global k / n index of the first element (for the unit-lower masks)
+  int flags;
+  int pad_;
+};
+
+// A front in a level batch.
+template <typename T>
+struct FrontTask {
+  T* G;        // (s+u) x s, ld = s+u
+  T* U;        // u x u update (F_BR), ld = u; nullptr for the root
+  T* W;        // s x s work: inv(L_TL) under construction
+  T* Z;        // u x s work: F_BL L^{-T}
+  int s, u;
+  int panel, sn;
+  int64_t gfid;
+};
+
+struct ColTask {   // a chunk of columns / rows of one front
+  int front;       // index into the level's FrontTask array
+  int c0, c1;
+};
+
+// ---------------------------------------------------------------------------
+// Launchers (defined in the .cu files)
+// ---------------------------------------------------------------------------
+void launch_matvec(const BoxOp& op, const double2* x, double2* y, int nrhs, int64_t N, cudaStream_t st);
+void launch_scale_rhs(const BoxOp& op, const double2* f, double2* b, int nrhs, int64_t N, cudaStream_t st);
+
+template <typename T>
+void launch_assemble_impl(const FrontTask<T>* fronts, const ColTask* tasks, int ntasks, const ShapeDev* shapes,
+                          const BoxOp* boxops, T* const* upd_ptr, const int32_t* panel_shape, cudaStream_t st);
+template <typename T>
+void launch_diag_ldlt(const FrontTask<T>* fronts, const int* list, int nlist, int kb, double tiny, int* status,
+                      cudaStream_t st);
+template <typename T>
+void launch_panel_right(const FrontTask<T>* fronts, const ColTask* tasks, int ntasks, int kb, cudaStream_t st);
+template <typename T>
+void launch_panel_left(const FrontTask<T>* fronts, const ColTask* tasks, int ntasks, int kb, cudaStream_t st);
+template <typename T>
+void launch_gemm(const GemmTask<T>* tasks, int ntasks, cudaStream_t st);
+template <typename T>
+void launch_copy_linv(const FrontTask<T>* fronts, const ColTask* tasks, int ntasks, cudaStream_t st);
+
+// ---- multifrontal solve of one panel (Alg. 1.3 inside Alg. 1.5) ----
+struct SolveTask {  // rows [r0, r1) of front sn (forward) or columns [r0, r1) of S (backward)
+  int sn, r0, r1;
+};
+
+template <typename T>
+struct SolveCtx {
+  ShapeDev sh;
+  const T* G;              // this panel's factor slab
+  T* xf;                   // box vector after L^{-1} and D^{-1} (elimination order), ld = n_loc
+  T* xb;                   // box vector after L^{-T}
+  T* upd;                  // children's update vectors, ld = upd_ld
+  double2* u;              // global vector block, ld = N
+  int64_t N, n_loc, upd_ld;
+  int nrhs;
+  int z0, z1, lead, nz;    // panel planes, pad planes, global plane count
+  int mode;                // 0: forward sweep (u_i := T_i(u_i - J_{i,i-1} u_{i-1})); 1: backward (u_i -= T_i J^T u_{i+1})
+  int has_prev, has_next;
+  const double2* s1n;      // global stretch tables for the plane coupling J_{i+1,i}
+  const double2* s2n;
+  const double2* s3h;
+  double inv_h2;
+};
+
+template <typename T>
+void launch_solve_fwd(const SolveTask* tasks, int ntasks, const SolveCtx<T>& cx, int R, int smax, cudaStream_t st);
+template <typename T>
+void launch_solve_bwd(const SolveTask* tasks, int ntasks, const SolveCtx<T>& cx, int ldmax, cudaStream_t st);
+
+// ---- GMRES helpers (complex128) ----
+// partial[b * (nvec * nrhs) + i * nrhs + r] = sum over block b's slice of conj(V_i[r]) w[r]
+void launch_multidot(const double2* V, int64_t ldv_vec, int64_t ldv_rhs, int nvec, const double2* w, int64_t ldw,
+                     int nrhs, int64_t N, double2* partial, double2* out, cudaStream_t st);
+// w[r] -= sum_i h[i, r] V_i[r]
+void launch_multiaxpy(const double2* V, int64_t ldv_vec, int64_t ldv_rhs, int nvec, const double2* h, double2* w,
+                      int64_t ldw, int nrhs, int64_t N, double sign, cudaStream_t st);
+void launch_axpby_batch(const double2* x, double2* y, int64_t N, int nrhs, const double2* alpha, int alpha_mode,
+                        cudaStream_t st);
+
+// Hessenberg least-squares state, one column block per right-hand side
+struct LsqState {
+  double2* H;        // (k+1) x k per rhs, column-major, ld = k+1
+  double* cs;        // k per rhs
+  double2* sn;       // k per rhs
+  double2* g;        // k+1 per rhs
+  double* resid;     // |g_{j+1}| per rhs
+  double2* scl;      // scale of the next basis vector per rhs (0 when inactive)
+  const int* active; // 1 while the rhs iterates
+  int k, nrhs;
+};
+void launch_arnoldi_step(const LsqState& L, int j, const double2* h1, const double2* h2, const double2* nrm2,
+                         cudaStream_t st);
+void launch_backsolve(const LsqState& L, const int* jr, double2* y, cudaStream_t st);
+void launch_cycle_start(const LsqState& L, const double2* nrm2, cudaStream_t st);
+
+}  // namespace psp

@@ -1,0 +1,232 @@
+"""ctypes binding of libpsp (include/psp.h): argument marshalling only.
+
+Every step of the method runs inside the library's CUDA kernels; this module
+checks shapes and dtypes, passes raw pointers (torch CUDA tensors or host
+numpy arrays) and the current CUDA stream, and turns status codes into
+exceptions.  It fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libpsp.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "psp.h")
+
+PREC_C128, PREC_C64 = 0, 1
+AUX_MOVING_PML, AUX_EXACT = 0, 1
+STATUS = {0: "PSP_OK", 1: "PSP_ERR_ARG", 2: "PSP_ERR_OOM", 3: "PSP_ERR_CUDA", 4: "PSP_ERR_ZERO_PIVOT",
+          5: "PSP_ERR_NOT_CONVERGED", 6: "PSP_ERR_TIMEOUT", 7: "PSP_ERR_STATE"}
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("h", ctypes.c_double)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("pml_C", ctypes.c_double), ("alpha", ctypes.c_double), ("pad_depth", ctypes.c_int),
+                ("leaf_size", ctypes.c_int), ("precision", ctypes.c_int), ("pml_faces", ctypes.c_int),
+                ("aux_mode", ctypes.c_int), ("reserved", ctypes.c_int * 9)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int), ("converged", ctypes.c_int),
+                ("applies", ctypes.c_int), ("relres_max", ctypes.c_double), ("solve_ms", ctypes.c_double),
+                ("status_front", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class PSPError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+
+
+def header_functions():
+    """Names of every function declared in include/psp.h."""
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"\b(psp_[a-z_]+)\s*\(", text)))
+
+
+def lib():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libpsp.so is not built ({LIB_PATH}); run `python -m paper_1204_0111_gb300.build`")
+    L = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "psp_default_options": (None, [ctypes.POINTER(Options)]),
+        "psp_setup": (_I, [ctypes.POINTER(Grid), _P, ctypes.c_double, _I, _I, ctypes.POINTER(Options), _P,
+                           ctypes.POINTER(_P)]),
+        "psp_apply": (_I, [_P, _P, _P, _I, _P]),
+        "psp_matvec": (_I, [_P, _I, _P, _P, _I, _P]),
+        "psp_solve": (_I, [_P, _P, _P, _I, ctypes.c_double, _I, _I, ctypes.POINTER(SolveInfo), _P]),
+        "psp_symbolic_export": (_I, [_P, _I, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_size_t)]),
+        "psp_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+        "psp_export_front": (_I, [_P, _I, _I, _P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+        "psp_destroy": (_I, [_P]),
+        "psp_status_string": (ctypes.c_char_p, [_I]),
+        "psp_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status):
+    if status != 0:
+        raise PSPError(status, lib().psp_last_error().decode())
+
+
+def _ptr_and_len(a, complex_=True):
+    """(pointer, element count) of a contiguous torch tensor or numpy array."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            want = torch.complex128 if complex_ else torch.float64
+            if a.dtype != want or not a.is_contiguous():
+                raise TypeError(f"expected a contiguous {want} tensor, got {a.dtype}")
+            return a.data_ptr(), a.numel()
+    except ImportError:
+        pass
+    want = np.complex128 if complex_ else np.float64
+    if not isinstance(a, np.ndarray) or a.dtype != want or not a.flags.c_contiguous:
+        raise TypeError(f"expected a C-contiguous {np.dtype(want)} array")
+    return a.ctypes.data, a.size
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(stream)
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return ctypes.c_void_p(0)
+
+
+class SweepingPreconditioner:
+    """Handle over psp_setup / psp_apply / psp_solve (Algs. 1.4, 1.5 and GMRES(k) of §2.4)."""
+
+    def __init__(self, c, h, omega, gamma, panel_depth, pad=None, leaf=64, pml_C=4.0, alpha=2 * math.pi,
+                 precision="c128", faces=63, mode="moving", stream=None):
+        nz, ny, nx = c.shape
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.N = nx * ny * nz
+        g = Grid(nx, ny, nz, float(h))
+        o = Options()
+        lib().psp_default_options(ctypes.byref(o))
+        o.pml_C = float(pml_C)
+        o.alpha = float(alpha)
+        o.pad_depth = -1 if pad is None else int(pad)
+        o.leaf_size = int(leaf)
+        o.precision = {"c128": PREC_C128, "c64": PREC_C64}[precision]
+        o.pml_faces = int(faces)
+        o.aux_mode = {"moving": AUX_MOVING_PML, "exact": AUX_EXACT}[mode]
+        cp, n = _ptr_and_len(c, complex_=False)
+        if n != self.N:
+            raise ValueError("c has the wrong size")
+        self._keep = c
+        h_ = _P()
+        st = lib().psp_setup(ctypes.byref(g), cp, float(omega), int(gamma), int(panel_depth), ctypes.byref(o),
+                             _stream(stream), ctypes.byref(h_))
+        self._h = h_
+        if st != 0:
+            msg = lib().psp_last_error().decode()
+            self.close()
+            raise PSPError(st, msg)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().psp_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _nrhs(self, a):
+        _, n = _ptr_and_len(a)
+        if n % self.N:
+            raise ValueError("vector block size is not a multiple of N")
+        return n // self.N
+
+    def apply(self, rhs, out, stream=None):
+        nr = self._nrhs(rhs)
+        if self._nrhs(out) != nr:
+            raise ValueError("rhs and out differ in size")
+        _check(lib().psp_apply(self._h, _ptr_and_len(rhs)[0], _ptr_and_len(out)[0], nr, _stream(stream)))
+        return out
+
+    def matvec(self, x, y, which=0, stream=None):
+        nr = self._nrhs(x)
+        _check(lib().psp_matvec(self._h, int(which), _ptr_and_len(x)[0], _ptr_and_len(y)[0], nr, _stream(stream)))
+        return y
+
+    def solve(self, f, u, tol=1e-5, k=20, maxit=500, stream=None, raise_on_nonconvergence=True):
+        nr = self._nrhs(f)
+        info = SolveInfo()
+        st = lib().psp_solve(self._h, _ptr_and_len(f)[0], _ptr_and_len(u)[0], nr, float(tol), int(k), int(maxit),
+                             ctypes.byref(info), _stream(stream))
+        if st != 0 and (raise_on_nonconvergence or st != 5):
+            _check(st)
+        return info.as_dict()
+
+    def info(self):
+        m = _I()
+        nf = ctypes.c_int64()
+        fb = ctypes.c_int64()
+        _check(lib().psp_info(self._h, ctypes.byref(m), ctypes.byref(nf), ctypes.byref(fb)))
+        return {"panels": m.value, "fronts": nf.value, "factor_bytes": fb.value}
+
+    def symbolic(self, panel):
+        n = ctypes.c_size_t()
+        _check(lib().psp_symbolic_export(self._h, int(panel), None, ctypes.byref(n)))
+        buf = (ctypes.c_int32 * n.value)()
+        _check(lib().psp_symbolic_export(self._h, int(panel), buf, ctypes.byref(n)))
+        return np.frombuffer(buf, dtype=np.int32).copy()
+
+    def export_front(self, panel, sn):
+        s = _I()
+        u = _I()
+        _check(lib().psp_export_front(self._h, int(panel), int(sn), None, ctypes.byref(s), ctypes.byref(u)))
+        out = np.zeros(((s.value + u.value) * s.value,), dtype=np.complex128)
+        _check(lib().psp_export_front(self._h, int(panel), int(sn), out.ctypes.data, ctypes.byref(s), ctypes.byref(u)))
+        return out.reshape(s.value, s.value + u.value).T, s.value, u.value
+
+
+def parse_symbolic(buf):
+    """Decode psp_symbolic_export's int32 stream into (meta, [(s, u, parent, nodes, struct), ...])."""
+    nx, ny, nz, lead, nsn = (int(v) for v in buf[:5])
+    p = 5
+    sns = []
+    for _ in range(nsn):
+        s, u, par = (int(v) for v in buf[p:p + 3])
+        p += 3
+        nodes = buf[p:p + s].copy()
+        p += s
+        struct = buf[p:p + u].copy()
+        p += u
+        sns.append((s, u, par, nodes, struct))
+    return {"nx": nx, "ny": ny, "nz": nz, "lead": lead, "nsn": nsn}, sns

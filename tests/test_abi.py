@@ -1,0 +1,53 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry point of include/psp.h."""
+import ctypes
+import os
+
+import pytest
+
+from paper_1204_0111_gb300 import build as B
+from paper_1204_0111_gb300 import psp
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not os.path.exists(B.LIB):
+        B.build()
+    return psp.lib()
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = psp.header_functions()
+    assert len(names) >= 11
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_defaults_and_status_strings(L):
+    o = psp.Options()
+    L.psp_default_options(ctypes.byref(o))
+    assert o.pml_C == 4.0 and abs(o.alpha - 2 * 3.141592653589793) < 1e-15
+    assert o.pad_depth == -1 and o.leaf_size == 64 and o.pml_faces == 63
+    assert o.precision == psp.PREC_C128 and o.aux_mode == psp.AUX_MOVING_PML
+    assert L.psp_status_string(4) == b"zero pivot"
+    assert L.psp_status_string(5) == b"not converged"
+
+
+def test_bad_arguments_are_rejected_before_any_device_call(L):
+    h = ctypes.c_void_p()
+    g = psp.Grid(0, 4, 4, 0.2)
+    c = (ctypes.c_double * 16)()
+    st = L.psp_setup(ctypes.byref(g), ctypes.cast(c, ctypes.c_void_p), 1.0, 2, 2, None, None, ctypes.byref(h))
+    assert st == 1 and h.value is None
+    assert b"grid" in L.psp_last_error()
+    g = psp.Grid(4, 4, 4, 0.2)
+    st = L.psp_setup(ctypes.byref(g), ctypes.cast(c, ctypes.c_void_p), -1.0, 2, 2, None, None, ctypes.byref(h))
+    assert st == 1
+    st = L.psp_setup(ctypes.byref(g), ctypes.cast(c, ctypes.c_void_p), 1.0, 2, 0, None, None, ctypes.byref(h))
+    assert st == 1
+    o = psp.Options()
+    L.psp_default_options(ctypes.byref(o))
+    o.precision = 7
+    st = L.psp_setup(ctypes.byref(g), ctypes.cast(c, ctypes.c_void_p), 1.0, 2, 2, ctypes.byref(o), None, ctypes.byref(h))
+    assert st == 1
+    assert L.psp_apply(None, None, None, 1, None) == 1
+    assert L.psp_destroy(None) == 0

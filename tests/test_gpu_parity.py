@@ -1,0 +1,193 @@
+"""CUDA path vs the complex128 oracle, element by element, through the C ABI.
+
+Tolerances: symbolic analysis bit-exact; complex128 operators, fronts and preconditioner
+applications within 1e-10 relative (Frobenius / 2-norm); GMRES solutions at a true relative
+residual below 1e-5 measured by the oracle's own sparse matvec on the host.
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+from oracle import discretize as dz
+from oracle import gmres as ogm
+from oracle import panels as opn
+from oracle import symbolic as osy
+from oracle import sweep as osw
+from paper_1204_0111_gb300 import workloads as wl
+
+from _cases import Case, small_cases
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1204_0111_gb300 import psp  # noqa: E402
+
+CASES = small_cases()
+IDS = [c.name for c in CASES]
+_oracles = {}
+
+
+def oracle_for(case: Case, mode="moving"):
+    key = (case.name, mode)
+    if key not in _oracles:
+        _oracles[key] = osw.SweepingPreconditioner(case.oracle_problem(), case.depth, case.pad, case.leaf, mode=mode)
+    return _oracles[key]
+
+
+def gpu_for(case: Case, precision="c128", mode="moving"):
+    c = torch.from_numpy(case.c).cuda()
+    return psp.SweepingPreconditioner(c, case.h, case.omega, case.gamma, case.depth, pad=case.pad, leaf=case.leaf,
+                                      pml_C=case.C, alpha=case.alpha, precision=precision, faces=case.faces, mode=mode)
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_symbolic_bit_exact(case):
+    P = gpu_for(case)
+    plan = opn.panel_plan(case.nz, case.gamma, case.depth)
+    assert P.info()["panels"] == len(plan)
+    for i, (z0, z1) in enumerate(plan):
+        meta, sns = psp.parse_symbolic(P.symbolic(i))
+        lead = 0 if z0 == 0 else case.pad
+        assert (meta["nx"], meta["ny"], meta["nz"], meta["lead"]) == (case.nx, case.ny, lead + z1 - z0, lead)
+        ref = osy.nested_dissection(case.nx, case.ny, lead + z1 - z0, case.leaf)
+        assert meta["nsn"] == len(ref.supernodes)
+        for (s, u, par, nodes, struct), sn in zip(sns, ref.supernodes):
+            assert s == len(sn.nodes) and u == len(sn.struct) and par == sn.parent
+            assert np.array_equal(nodes, sn.nodes) and np.array_equal(struct, sn.struct)
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_matvec_A_and_J(case):
+    P = gpu_for(case)
+    p = case.oracle_problem()
+    x = wl.random_vector(case.N, 3, seed=11)
+    xd = torch.from_numpy(x).cuda()
+    for which, M in ((0, dz.operator_A(p)), (1, dz.operator_J(p))):
+        yd = torch.empty_like(xd)
+        P.matvec(xd, yd, which)
+        ref = (M @ x.T).T
+        assert rel(yd.cpu().numpy(), ref) < 1e-13
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_front_factors(case):
+    P = gpu_for(case)
+    O = oracle_for(case)
+    worst = 0.0
+    for i in range(O.m):
+        for f, fr in enumerate(O.fronts[i]):
+            G, s, u = P.export_front(i, f)
+            Linv = sla.solve_triangular(fr.L_TL, np.eye(s), lower=True, unit_diagonal=True)
+            top = np.tril(Linv, -1) + np.diag(fr.d)
+            exp = np.vstack([top, fr.L_BL @ Linv])
+            got = G.copy()
+            got[:s] = np.tril(got[:s])
+            worst = max(worst, rel(got, exp))
+    assert worst < 1e-10, worst
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+@pytest.mark.parametrize("nrhs", [1, 3])
+def test_apply_matches_oracle(case, nrhs):
+    P = gpu_for(case)
+    O = oracle_for(case)
+    r = wl.random_vector(case.N, nrhs, seed=21 + nrhs)
+    ref = O.apply(r)
+    rd = torch.from_numpy(r).cuda()
+    out = torch.empty_like(rd)
+    P.apply(rd, out)
+    assert rel(out.cpu().numpy(), ref) < 1e-10
+    # in place, and through host buffers
+    P.apply(rd, rd)
+    assert rel(rd.cpu().numpy(), ref) < 1e-10
+    host_out = np.zeros_like(r)
+    P.apply(r, host_out)
+    assert rel(host_out, ref) < 1e-10
+
+
+def test_exact_mode_is_inverse_of_J():
+    case = CASES[1]
+    P = gpu_for(case, mode="exact")
+    p = case.oracle_problem()
+    x = wl.random_vector(case.N, 2, seed=5)
+    Jx = (dz.operator_J(p) @ x.T).T
+    out = np.zeros_like(x)
+    P.apply(np.ascontiguousarray(Jx), out)
+    assert rel(out, x) < 1e-9
+
+
+@pytest.mark.parametrize("case", CASES[:2], ids=IDS[:2])
+def test_gmres_solve_converges_like_oracle(case):
+    P = gpu_for(case)
+    O = oracle_for(case)
+    p = case.oracle_problem()
+    A = dz.operator_A(p)
+    f = wl.gaussian_source(case.nx, case.ny, case.nz, case.h, (0.5, 0.5, 0.5))
+    b = dz.rhs_scale(p) * f
+    _, it_oracle, _ = ogm.gmres(lambda v: A @ v, O.apply, b, tol=1e-5, k=20, maxit=300)
+    fd = torch.from_numpy(f[None, :].copy()).cuda()
+    ud = torch.zeros_like(fd)
+    info = P.solve(fd, ud, tol=1e-5, k=20, maxit=300)
+    u = ud.cpu().numpy()[0]
+    true_rel = np.linalg.norm(b - A @ u) / np.linalg.norm(b)
+    assert info["converged"] == 1 and true_rel < 1e-5
+    assert abs(info["iterations"] - it_oracle) <= 1
+
+
+def test_gmres_several_shots_and_nonconvergence():
+    case = CASES[0]
+    P = gpu_for(case)
+    p = case.oracle_problem()
+    A = dz.operator_A(p)
+    srcs = [(0.5, 0.5, 0.5), (0.3, 0.6, 0.2), (0.7, 0.2, 0.8)]
+    f = np.stack([wl.gaussian_source(case.nx, case.ny, case.nz, case.h, s) for s in srcs])
+    fd = torch.from_numpy(f).cuda()
+    ud = torch.zeros_like(fd)
+    info = P.solve(fd, ud, tol=1e-6, k=10, maxit=300)
+    u = ud.cpu().numpy()
+    b = dz.rhs_scale(p)[None, :] * f
+    for j in range(3):
+        assert np.linalg.norm(b[j] - A @ u[j]) / np.linalg.norm(b[j]) < 1e-6
+    assert info["restarts"] >= 1
+    with pytest.raises(psp.PSPError) as e:
+        P.solve(fd, ud, tol=1e-6, k=10, maxit=2)
+    assert e.value.name == "PSP_ERR_NOT_CONVERGED"
+
+
+@pytest.mark.parametrize("case", CASES[:2], ids=IDS[:2])
+def test_complex64_path_solves_to_tolerance(case):
+    P64 = gpu_for(case, precision="c64")
+    O = oracle_for(case)
+    r = wl.random_vector(case.N, 1, seed=3)
+    ref = O.apply(r)
+    out = np.zeros_like(r)
+    P64.apply(r, out)
+    err = rel(out, ref)
+    assert err < 1e-3          # single-precision fronts: the apply differs at ~1e-6..1e-4
+    p = case.oracle_problem()
+    A = dz.operator_A(p)
+    f = wl.gaussian_source(case.nx, case.ny, case.nz, case.h, (0.5, 0.5, 0.5))[None, :].copy()
+    u = np.zeros_like(f)
+    info = P64.solve(f, u, tol=1e-5, k=20, maxit=300)
+    b = dz.rhs_scale(p) * f[0]
+    assert np.linalg.norm(b - A @ u[0]) / np.linalg.norm(b) < 1e-5 and info["converged"] == 1
+
+
+def test_single_panel_and_zero_pivot_free_small_grid():
+    # panel depth >= nz: one auxiliary problem, M^{-1} = J^{-1}
+    case = Case(np.ones((7, 5, 6)), 1.0 / 8, 5.0, 1, 50, leaf=8)
+    P = gpu_for(case)
+    assert P.info()["panels"] == 1
+    p = case.oracle_problem()
+    J = dz.operator_J(p).toarray()
+    x = wl.random_vector(case.N, 1, seed=9)
+    out = np.zeros_like(x)
+    P.apply(np.ascontiguousarray((J @ x.T).T), out)
+    assert rel(out, x) < 1e-10
