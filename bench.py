@@ -1,0 +1,412 @@
+#!/usr/bin/env python
+"""Time-to-solution benchmark of the GB300 sweeping preconditioner.
+
+Workload: the 100^3 converging-lens problem, c(x) = 1 - 0.4 exp(-32 |x - 0.5|^2), omega for 10
+points per minimum wavelength, PML of 8 points on all faces, 4-plane panels padded with 8 PML
+planes, nested-dissection leaf 64, one Gaussian shot (sigma = 2h) at (0.5, 0.5, 0.1), GMRES(20) to
+a relative residual of 1e-5, complex128 on the GPU.  One step = the whole hot path on one problem:
+setup (factor every panel) + GMRES solve to 1e-5 (all preconditioner applications and matvecs).
+
+One JSON line is printed by rank 0.  `--impl reference` times the complex128 CPU oracle on a
+bounded sample of the same workload instead (see `reference_main`).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GMRES solve time & iters to 1e-5; front TFLOP/s; sweep GB/s; mixed vs FP64"
+UNIT = "solves/s"          # problems taken from c(x) and f to a solution at 1e-5 (setup + GMRES) per second
+WORKLOAD = "lens100"
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # SMs x FP64 flop/clk/SM (2 FMA) x max SM clock
+
+
+def workload():
+    from paper_1204_0111_gb300 import workloads as wl
+    return wl.cube_lens(100)
+
+
+def config_dict(w, nrhs, extra=None):
+    d = {"workload": f"{WORKLOAD}: {w.n}^3 converging lens, gamma {w.gamma}, panels of {w.panel_depth} + pad {w.pad}, "
+                     f"leaf {w.leaf}, {nrhs} shot, GMRES({w.k}) to {w.tol:g}",
+         "n": w.n, "N": w.N, "omega": w.omega, "pml_gamma": w.gamma, "panel_depth": w.panel_depth, "pad": w.pad,
+         "leaf": w.leaf, "nrhs": nrhs, "gmres_k": w.k, "tol": w.tol,
+         "l2": "inputs larger than L2 (factors of ~15 GB stream per apply)"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU oracle sample (run in a spawned process so that BLAS threading and CUDA state stay clean)
+# ---------------------------------------------------------------------------------------------
+def _oracle_sample(args):
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    os.environ["OMP_NUM_THREADS"] = "1"
+    sys.path.insert(0, ROOT)
+    import numpy as np
+
+    from oracle import discretize as dz
+    from oracle import multifrontal as mf
+    from oracle import panels as pn
+    from oracle import symbolic as sy
+    w = workload()
+    p = dz.Helmholtz(w.c, w.h, w.omega, w.gamma, w.pml_C, w.alpha)
+    plan = pn.panel_plan(p.nz, p.gamma, w.panel_depth)
+    z0, z1 = plan[1]
+    t0 = time.perf_counter()
+    ap = pn.aux_problem(p, z0, z1, w.pad)
+    sym = sy.nested_dissection(ap.nx, ap.ny, ap.depth, w.leaf)
+    fr = mf.factor(ap.H, sym)
+    t1 = time.perf_counter()
+    v = np.zeros(ap.H.shape[0], dtype=np.complex128)
+    v[ap.lead * p.nx * p.ny:] = w.rhs()[0][z0 * p.nx * p.ny:z1 * p.nx * p.ny]
+    mf.solve(fr, sym, v)
+    t2 = time.perf_counter()
+    A = dz.operator_A(p)
+    x = w.rhs()[0]
+    t3 = time.perf_counter()
+    A @ x
+    t4 = time.perf_counter()
+    return {"t_factor": t1 - t0, "t_T": t2 - t1, "t_matvec": t4 - t3, "m": len(plan)}
+
+
+def oracle_estimate(iters, k=20):
+    """Seconds per solve of the oracle, extrapolated from a one-panel sample: m panel factorisations,
+    iters x (2m - 1) panel solves plus iters + restarts true-residual matvecs; Arnoldi (k^2 N) is
+    counted from the measured matvec rate as 8 vector passes per matvec-equivalent."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(1) as pool:
+        s = pool.apply(_oracle_sample, ((),))
+    m = s["m"]
+    t_setup = m * s["t_factor"]
+    t_apply = (2 * m - 1) * s["t_T"]
+    t_mv = s["t_matvec"]
+    restarts = max(1, math.ceil(iters / k))
+    t_solve = iters * (t_apply + t_mv) + restarts * t_mv + iters * (iters + 1) / 2 / 4 * t_mv
+    total = t_setup + t_solve
+    sample = (f"one {w_desc()} panel factorisation ({s['t_factor']:.2f} s) + one panel solve ({s['t_T']:.3f} s) + "
+              f"one sparse matvec ({s['t_matvec']:.4f} s), single thread, extrapolated to m={m} panels, "
+              f"{iters} GMRES iterations")
+    return total, sample, s
+
+
+def w_desc():
+    return "100x100x12"
+
+
+def cpu_cores():
+    return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_uuid=None):
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if device_uuid:
+            cmd += ["-i", device_uuid]
+        try:
+            self.p = subprocess.Popen(cmd, stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+        self.tmp.flush()
+        self.tmp.seek(0)
+        rows = [r.strip().split(",") for r in self.tmp.read().splitlines() if r.strip()]
+        os.unlink(self.tmp.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def traffic_from_profiles(kernel):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        kv = dict(t.split("=", 1) for t in line.split() if "=" in t)
+        if kv.get("kernel") != kernel or kv.get("workload") != WORKLOAD:
+            continue
+        src = os.path.join(ROOT, "paper_1204_0111_gb300", "csrc", kv.get("source", ""))
+        if not os.path.exists(src):
+            return None
+        if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != kv.get("sha", ""):
+            return None
+        return float(kv["bytes_per_launch"])
+    return None
+
+
+# ---------------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------------
+def gpu_main(a):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1204_0111_gb300 import psp
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    w = workload()
+    nrhs = 1
+    c_dev = torch.from_numpy(w.c).to(dev)
+    f_host = w.rhs()
+    f_dev = torch.from_numpy(f_host).to(dev)
+    u_dev = torch.zeros_like(f_dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(precision="c128", stats=False):
+        P = psp.SweepingPreconditioner(c_dev, w.h, w.omega, w.gamma, w.panel_depth, pad=w.pad, leaf=w.leaf,
+                                       pml_C=w.pml_C, alpha=w.alpha, precision=precision, collect_stats=stats)
+        info = P.solve(f_dev, u_dev, tol=w.tol, k=w.k, maxit=400)
+        st = P.stats() if stats else None
+        fb = P.info()["factor_bytes"]
+        P.close()
+        return info, st, fb
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos, stats_all = [], []
+    fbytes = 0
+    for _ in range(a.steps):
+        info, st, fbytes = step(stats=True)
+        infos.append(info)
+        stats_all.append(st)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * a.steps / (ms_max / 1e3)
+
+    # kernel accounting over the timed steps
+    agg = {}
+    for st in stats_all:
+        for k, v in st.items():
+            g = agg.setdefault(k, {"launches": 0, "total_ms": 0.0, "flops": 0.0, "bytes": 0.0})
+            for f in g:
+                g[f] += v[f]
+    launches = int(sum(v["launches"] for v in agg.values()))
+    top = max(agg.items(), key=lambda kv: kv[1]["total_ms"])
+    tk, tv = top
+    achieved = tv["flops"] / (tv["total_ms"] * 1e-3) / 1e12
+    traffic = traffic_from_profiles(tk)
+    roofline = {"kernel": tk, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                "peak_source": "FP64 CUDA-core peak derived: 152 SMs x 4 flop/clk x 2.07 GHz (complex128 path)",
+                "kernel_share": tv["total_ms"] / sum(v["total_ms"] for v in agg.values())}
+    setup_ms = sum(v["total_ms"] for k, v in agg.items()
+                   if k in ("k_assemble", "k_diag_ldlt", "k_panel_right", "k_panel_left", "k_gemm", "k_copy_linv")) / a.steps
+    solve_kern = {k: v for k, v in agg.items() if k in ("k_solve_fwd", "k_solve_bwd")}
+    sweep_ms = sum(v["total_ms"] for v in solve_kern.values())
+    sweep_bytes = sum(v["bytes"] for v in solve_kern.values())
+    setup_flops = sum(v["flops"] for k, v in agg.items() if k in ("k_assemble", "k_diag_ldlt", "k_panel_right",
+                                                                  "k_panel_left", "k_gemm", "k_copy_linv"))
+    iters = [i["iterations"] for i in infos]
+    applies = sum(i["applies"] for i in infos)
+    detail = {
+        "gmres_iters": iters[-1],
+        "relres": max(i["relres_max"] for i in infos),
+        "setup_kernel_ms": setup_ms,
+        "solve_wall_ms": statistics.mean(i["solve_ms"] for i in infos),
+        "apply_ms": sweep_ms / max(applies, 1),
+        "front_tflops": setup_flops / (setup_ms * a.steps * 1e-3) / 1e12,
+        "sweep_gbs": sweep_bytes / (sweep_ms * 1e-3) / 1e9,
+        "factor_bytes": fbytes,
+        "kernels": {k: {"launches": v["launches"] // a.steps, "ms_per_step": v["total_ms"] / a.steps,
+                        "tflops": v["flops"] / max(v["total_ms"], 1e-9) / 1e9,
+                        "gbs": v["bytes"] / max(v["total_ms"], 1e-9) / 1e6} for k, v in sorted(agg.items())},
+    }
+
+    # end to end through the public API with pinned host buffers (copies inside the timed region)
+    c_pin = torch.from_numpy(w.c).pin_memory()
+    f_pin = torch.from_numpy(f_host).pin_memory()
+    u_pin = torch.zeros_like(f_pin).pin_memory()
+    e2e_steps = max(1, min(a.steps, 2))
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        P = psp.SweepingPreconditioner(c_pin, w.h, w.omega, w.gamma, w.panel_depth, pad=w.pad, leaf=w.leaf,
+                                       pml_C=w.pml_C, alpha=w.alpha)
+        P.solve(f_pin, u_pin, tol=w.tol, k=w.k, maxit=400)
+        P.close()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    tt = torch.tensor([t1 - t0], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    e2e = {"value": world * e2e_steps / float(tt.item()), "unit": UNIT,
+           "h2d_bytes_per_step": int(c_pin.numel() * 8 + f_pin.numel() * 16),
+           "d2h_bytes_per_step": int(u_pin.numel() * 16)}
+
+    # mixed precision (complex64 fronts and sweeps, complex128 GMRES) on the same workload
+    mixed = None
+    if not a.no_mixed:
+        step("c64")
+        torch.cuda.synchronize()
+        m0 = torch.cuda.Event(enable_timing=True)
+        m1 = torch.cuda.Event(enable_timing=True)
+        msteps = max(1, min(a.steps, 3))
+        m0.record(stream)
+        minfo = None
+        for _ in range(msteps):
+            minfo, _, _ = step("c64")
+        m1.record(stream)
+        torch.cuda.synchronize()
+        mms = m0.elapsed_time(m1) / msteps
+        # apply error of the complex64 preconditioner against the complex128 one
+        P128 = psp.SweepingPreconditioner(c_dev, w.h, w.omega, w.gamma, w.panel_depth, pad=w.pad, leaf=w.leaf)
+        P64 = psp.SweepingPreconditioner(c_dev, w.h, w.omega, w.gamma, w.panel_depth, pad=w.pad, leaf=w.leaf,
+                                         precision="c64")
+        g = torch.Generator(device="cpu").manual_seed(0)
+        r = torch.complex(torch.randn(w.N, generator=g, dtype=torch.float64),
+                          torch.randn(w.N, generator=g, dtype=torch.float64)).reshape(1, -1).to(dev)
+        o128 = torch.empty_like(r)
+        o64 = torch.empty_like(r)
+        P128.apply(r, o128)
+        P64.apply(r, o64)
+        torch.cuda.synchronize()
+        err = float(torch.linalg.norm(o64 - o128) / torch.linalg.norm(o128))
+        P128.close()
+        P64.close()
+        mixed = {"value": 1e3 / mms, "unit": UNIT, "ms_per_step": mms, "gmres_iters": minfo["iterations"],
+                 "relres": minfo["relres_max"], "apply_rel_err_vs_c128": err,
+                 "speedup_vs_c128": (ms_max / a.steps) / mms, "dtype": "c64 fronts/sweeps, f64 GMRES"}
+
+    if rank == 0:
+        cpu = None
+        if not a.no_cpu_baseline:
+            t_cpu, sample, _ = oracle_estimate(iters[-1], w.k)
+            cpu = {"value": 1.0 / t_cpu, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                   "seconds_per_solve": t_cpu}
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+                "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": config_dict(w, nrhs, {"parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches // a.steps,
+                "clocks": clk, "detail": detail, "mixed": mixed}
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------------------------
+# reference arm: the complex128 CPU oracle, as it stands, on a bounded sample per step
+# ---------------------------------------------------------------------------------------------
+def reference_main(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    iters = a.ref_iters
+    total_s, sample, s = None, None, None
+    for _ in range(a.warmup if a.warmup < 1 else 1):
+        oracle_estimate(iters)
+    times = []
+    for _ in range(a.steps):
+        t0 = time.perf_counter()
+        total_s, sample, s = oracle_estimate(iters)
+        times.append(time.perf_counter() - t0)
+    w = workload()
+    value = 1.0 / total_s
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": 1e3 * total_s, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": config_dict(w, 1, {"parallelism": "CPU oracle, single thread"}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample + f" (GMRES iteration count {iters} from the GPU path)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "sample_wall_s": statistics.mean(times)}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--ref-iters", type=int, default=16, help="GMRES iterations assumed by the reference arm")
+    a = ap.parse_args()
+    if a.warmup < 3 and a.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if a.impl == "reference":
+        reference_main(a)
+    else:
+        gpu_main(a)
+
+
+if __name__ == "__main__":
+    main()

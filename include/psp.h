@@ -76,7 +76,8 @@ typedef struct {
   int precision;      /* psp_precision, default PSP_PREC_C128 */
   int pml_faces;      /* bit mask x-lo 1, x-hi 2, y-lo 4, y-hi 8, z-lo 16, z-hi 32; default 63 */
   int aux_mode;       /* psp_aux_mode, default PSP_AUX_MOVING_PML */
-  int reserved[9];
+  int collect_stats;  /* 1: time every kernel launch of this handle with CUDA events (psp_stats), default 0 */
+  int reserved[8];
 } psp_options;
 
 /* Per-solve report filled by psp_solve (host struct). */
@@ -160,6 +161,25 @@ psp_status psp_info(psp_handle h, int* panels, int64_t* fronts, int64_t* factor_
  * Call with buf = NULL to get s and u.
  */
 psp_status psp_export_front(psp_handle h, int panel, int supernode, double* buf, int* s, int* u);
+
+/*
+ * Per-kernel accounting of one handle (setup, applies, matvecs and solves issued through it).
+ * Launch counts and algorithmic work are always kept; total_ms is filled only when the handle
+ * was created with collect_stats = 1 (CUDA events around every launch, on the launch stream).
+ * flops: useful real floating-point operations (a complex multiply-add counts 8); bytes: the
+ * algorithmic HBM bytes (matrix entries read once, vectors read/written once).
+ * Copies min(capacity, kinds) records into out, sets *count to the number of kernel kinds,
+ * synchronises the device, and zeroes the counters when reset != 0.
+ */
+typedef struct {
+  char name[40];
+  int64_t launches;
+  double total_ms;
+  double flops;
+  double bytes;
+} psp_kernel_stat;
+
+psp_status psp_stats(psp_handle h, psp_kernel_stat* out, int capacity, int* count, int reset);
 
 psp_status psp_destroy(psp_handle h);
 const char* psp_status_string(psp_status s);

@@ -95,6 +95,73 @@ static double sigma_axis(double xi, int n, int gam, double C, double h, bool lo,
 static double2 stretch(double sig, double omega) { return make_double2(1.0, sig / omega); }
 static double2 inv_stretch(double sig, double omega) { return cinv(stretch(sig, omega)); }
 
+// Per-kernel accounting: launch counts and algorithmic work always, CUDA-event timing on request.
+struct KStat {
+  int64_t launches = 0;
+  double flops = 0, bytes = 0, ms = 0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+};
+struct Stats {
+  bool timing = false;
+  std::map<std::string, KStat> k;
+  std::vector<cudaEvent_t> pool;
+  int64_t npending = 0;
+  cudaEvent_t get() {
+    if (pool.empty()) {
+      cudaEvent_t e;
+      PSP_CK(cudaEventCreate(&e));
+      return e;
+    }
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+  }
+  template <class F>
+  void run(const char* name, cudaStream_t st, int nlaunch, double flops, double bytes, F&& launch) {
+    KStat& s = k[name];
+    s.launches += nlaunch;
+    s.flops += flops;
+    s.bytes += bytes;
+    if (!timing) {
+      launch();
+      return;
+    }
+    cudaEvent_t e0 = get(), e1 = get();
+    PSP_CK(cudaEventRecord(e0, st));
+    launch();
+    PSP_CK(cudaEventRecord(e1, st));
+    s.pending.push_back({e0, e1});
+    if (++npending > 16384) collect(8192);
+  }
+  // resolve the oldest pending pairs (all when keep == 0)
+  void collect(int64_t keep_at_most = 0) {
+    for (auto& kv : k) {
+      auto& v = kv.second.pending;
+      size_t n = v.size();
+      if (keep_at_most > 0) n = n > (size_t)keep_at_most / 2 ? n - keep_at_most / 2 : 0;
+      for (size_t i = 0; i < n; ++i) {
+        float ms = 0.f;
+        PSP_CK(cudaEventSynchronize(v[i].second));
+        PSP_CK(cudaEventElapsedTime(&ms, v[i].first, v[i].second));
+        kv.second.ms += ms;
+        pool.push_back(v[i].first);
+        pool.push_back(v[i].second);
+      }
+      v.erase(v.begin(), v.begin() + n);
+      npending -= (int64_t)n;
+    }
+    if (npending < 0) npending = 0;
+  }
+  ~Stats() {
+    for (auto& kv : k)
+      for (auto& pr : kv.second.pending) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+      }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
 }  // namespace psp
 
 using namespace psp;
@@ -129,6 +196,8 @@ struct psp_ctx_s {
     int nfwd = 0, R = 64, smax = 0;
     int64_t bwd_off = 0;
     int nbwd = 0, ldmax = 0;
+    double entries = 0;   // factor entries read by one direction of this level
+    double vec = 0;       // vector entries gathered / written by one direction
   };
   std::vector<std::vector<LevelPlan>> splan;
   DevBuf d_stasks;
@@ -142,6 +211,7 @@ struct psp_ctx_s {
   DevBuf gm;
   int gm_nrhs = 0, gm_k = 0;
   int zero_pivot_front = -1;
+  Stats stats;
 };
 
 namespace psp {
@@ -192,6 +262,21 @@ struct ArenaPlanner {
 };
 
 static int64_t pad16(int64_t n) { return (n + 15) / 16 * 16; }
+
+// useful complex multiply-adds of a GEMM task: written C entries times structurally non-zero k
+template <typename T>
+static double gemm_cmacs(const GemmTask<T>& g) {
+  double total = 0;
+  for (int j = 0; j < g.n; ++j) {
+    const double rows = (g.flags & GF_C_LOWER) ? std::max(0, g.m - j) : g.m;
+    const int ng = g.ng0 + j;
+    double ks = g.k;
+    if (g.flags & GF_B_UNIT_LOWER_NT) ks = std::clamp(ng - g.kg0 + 1, 0, g.k);
+    else if (g.flags & GF_B_UNIT_LOWER_NN) ks = std::clamp(g.kg0 + g.k - ng, 0, g.k);
+    total += rows * ks;
+  }
+  return total;
+}
 
 // ---------------------------------------------------------------------------
 // Plan and run the factorisation of all panels, level by level (all panels' fronts of one
@@ -256,8 +341,19 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
     int64_t off;
     int count;
     int kb;
+    double flops = 0, bytes = 0;
   };
   std::vector<Launch> launches;
+  const double es = sizeof(T);
+  // work of the gemm tasks [g0, end)
+  auto gemm_work = [&](int64_t g0, double& fl, double& by) {
+    fl = 0;
+    by = 0;
+    for (size_t i = g0; i < gtasks.size(); ++i) {
+      fl += 8.0 * gemm_cmacs(gtasks[i]);
+      by += es * ((double)gtasks[i].m * gtasks[i].k + (double)gtasks[i].n * gtasks[i].k + 2.0 * gtasks[i].m * gtasks[i].n);
+    }
+  };
 
   auto tiles_lower = [&](T* C, int ldc, int M, auto&& emit) {
     for (int tj = 0; tj < M; tj += 64)
@@ -293,22 +389,47 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
         const auto& ft = fronts[f0 + f];
         for (int c = 0; c < ft.s + ft.u; c += 32) ctasks.push_back({f, c, std::min(c + 32, ft.s + ft.u)});
       }
-      launches.push_back({ASSEMBLE, f0, c0, (int)(ctasks.size() - c0), 0});
+      Launch la{ASSEMBLE, f0, c0, (int)(ctasks.size() - c0), 0};
+      for (int f = 0; f < nf; ++f) {
+        const auto& ft = fronts[f0 + f];
+        const Shape& sh = X->shapes[X->shape_of[ft.panel]];
+        double ea = 0;
+        for (int c = sh.child_ptr[ft.sn]; c < sh.child_ptr[ft.sn + 1]; ++c) {
+          const double uc = sh.u[sh.child_idx[c]];
+          ea += uc * (uc + 1) / 2;
+        }
+        la.flops += 2.0 * ea;
+        la.bytes += es * (2.0 * ea + (double)(ft.s + ft.u) * ft.s + (double)ft.s * ft.s + (double)ft.u * ft.u);
+      }
+      launches.push_back(la);
     }
     // blocked LDL^T of F_TL with the inverse of L_TL built alongside in W
     const int nblk = (smax + nb - 1) / nb;
     for (int kb = 0; kb < nblk; ++kb) {
       const int o = kb * nb;
       const int64_t d0 = (int64_t)dlist.size();
+      Launch ld{DIAG, f0, d0, 0, kb};
       for (int f = 0; f < nf; ++f)
-        if (fronts[f0 + f].s > o) dlist.push_back(f);
-      launches.push_back({DIAG, f0, d0, (int)(dlist.size() - d0), kb});
+        if (fronts[f0 + f].s > o) {
+          dlist.push_back(f);
+          const double bs = std::min(nb, fronts[f0 + f].s - o);
+          ld.flops += 8.0 * bs * bs * bs / 3;
+          ld.bytes += es * bs * bs;
+        }
+      ld.count = (int)(dlist.size() - d0);
+      launches.push_back(ld);
       const int64_t pr0 = (int64_t)ctasks.size();
       for (int f = 0; f < nf; ++f) {
         const auto& ft = fronts[f0 + f];
         for (int r = o + nb; r < ft.s; r += 64) ctasks.push_back({f, r, std::min(r + 64, ft.s)});
       }
-      launches.push_back({PRIGHT, f0, pr0, (int)(ctasks.size() - pr0), kb});
+      Launch lr{PRIGHT, f0, pr0, (int)(ctasks.size() - pr0), kb};
+      for (int64_t t = pr0; t < (int64_t)ctasks.size(); ++t) {
+        const double rows = ctasks[t].c1 - ctasks[t].c0, bs = std::min(nb, fronts[f0 + ctasks[t].front].s - o);
+        lr.flops += 8.0 * rows * bs * (bs + 1) / 2;
+        lr.bytes += es * 2 * rows * bs;
+      }
+      launches.push_back(lr);
       const int64_t pl0 = (int64_t)ctasks.size();
       for (int f = 0; f < nf; ++f) {
         const auto& ft = fronts[f0 + f];
@@ -316,7 +437,13 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
         const int cend = std::min(ft.s, o + nb);
         for (int c = 0; c < cend; c += 64) ctasks.push_back({f, c, std::min(c + 64, cend)});
       }
-      launches.push_back({PLEFT, f0, pl0, (int)(ctasks.size() - pl0), kb});
+      Launch lp{PLEFT, f0, pl0, (int)(ctasks.size() - pl0), kb};
+      for (int64_t t = pl0; t < (int64_t)ctasks.size(); ++t) {
+        const double cols = ctasks[t].c1 - ctasks[t].c0, bs = std::min(nb, fronts[f0 + ctasks[t].front].s - o);
+        lp.flops += 8.0 * cols * bs * (bs - 1) / 2;
+        lp.bytes += es * 2 * cols * bs;
+      }
+      launches.push_back(lp);
       const int64_t g0 = (int64_t)gtasks.size();
       for (int f = 0; f < nf; ++f) {
         const auto& ft = fronts[f0 + f];
@@ -357,7 +484,9 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
             gtasks.push_back(g);
           }
       }
-      launches.push_back({GEMM, f0, g0, (int)(gtasks.size() - g0), kb});
+      Launch lg{GEMM, f0, g0, (int)(gtasks.size() - g0), kb};
+      gemm_work(g0, lg.flops, lg.bytes);
+      launches.push_back(lg);
     }
     // inv(L_TL) into F_TL's strict lower part
     {
@@ -366,7 +495,9 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
         const auto& ft = fronts[f0 + f];
         for (int c = 0; c < ft.s; c += 16) ctasks.push_back({f, c, std::min(c + 16, ft.s)});
       }
-      launches.push_back({COPY, f0, c0, (int)(ctasks.size() - c0), 0});
+      Launch lc{COPY, f0, c0, (int)(ctasks.size() - c0), 0};
+      for (int f = 0; f < nf; ++f) lc.bytes += es * (double)fronts[f0 + f].s * (fronts[f0 + f].s - 1);
+      launches.push_back(lc);
     }
     // Z = F_BL inv(L_TL)^T  (= F_BL L^{-T})
     {
@@ -394,7 +525,9 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
             gtasks.push_back(g);
           }
       }
-      launches.push_back({GEMM, f0, g0, (int)(gtasks.size() - g0), -1});
+      Launch lg{GEMM, f0, g0, (int)(gtasks.size() - g0), -1};
+      gemm_work(g0, lg.flops, lg.bytes);
+      launches.push_back(lg);
     }
     // F_BR -= Z D^{-1} Z^T (lower) and M_BL = Z D^{-1} inv(L_TL)
     {
@@ -437,7 +570,9 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
             gtasks.push_back(g);
           }
       }
-      launches.push_back({GEMM, f0, g0, (int)(gtasks.size() - g0), -1});
+      Launch lg{GEMM, f0, g0, (int)(gtasks.size() - g0), -1};
+      gemm_work(g0, lg.flops, lg.bytes);
+      launches.push_back(lg);
     }
   }
 
@@ -452,18 +587,22 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
   const GemmTask<T>* GT = d_gtasks.as<GemmTask<T>>();
   int* status = X->d_status.as<int>();
   PSP_CK(cudaMemsetAsync(status, 0, 4 * sizeof(int), st));
+  static const char* names[] = {"k_assemble", "k_diag_ldlt", "k_panel_right", "k_panel_left", "k_gemm", "k_copy_linv"};
   for (const auto& l : launches) {
-    switch (l.kind) {
-      case ASSEMBLE:
-        launch_assemble_impl<T>(F + l.front_off, CT + l.off, l.count, X->d_shapes.as<ShapeDev>(),
-                                X->d_boxops.as<BoxOp>(), d_upd_ptr.as<T*>(), X->d_panel_shape.as<int32_t>(), st);
-        break;
-      case DIAG: launch_diag_ldlt<T>(F + l.front_off, DL + l.off, l.count, l.kb, tiny, status, st); break;
-      case PRIGHT: launch_panel_right<T>(F + l.front_off, CT + l.off, l.count, l.kb, st); break;
-      case PLEFT: launch_panel_left<T>(F + l.front_off, CT + l.off, l.count, l.kb, st); break;
-      case GEMM: launch_gemm<T>(GT + l.off, l.count, st); break;
-      case COPY: launch_copy_linv<T>(F + l.front_off, CT + l.off, l.count, st); break;
-    }
+    if (l.count <= 0) continue;
+    X->stats.run(names[l.kind], st, 1, l.flops, l.bytes, [&] {
+      switch (l.kind) {
+        case ASSEMBLE:
+          launch_assemble_impl<T>(F + l.front_off, CT + l.off, l.count, X->d_shapes.as<ShapeDev>(),
+                                  X->d_boxops.as<BoxOp>(), d_upd_ptr.as<T*>(), X->d_panel_shape.as<int32_t>(), st);
+          break;
+        case DIAG: launch_diag_ldlt<T>(F + l.front_off, DL + l.off, l.count, l.kb, tiny, status, st); break;
+        case PRIGHT: launch_panel_right<T>(F + l.front_off, CT + l.off, l.count, l.kb, st); break;
+        case PLEFT: launch_panel_left<T>(F + l.front_off, CT + l.off, l.count, l.kb, st); break;
+        case GEMM: launch_gemm<T>(GT + l.off, l.count, st); break;
+        case COPY: launch_copy_linv<T>(F + l.front_off, CT + l.off, l.count, st); break;
+      }
+    });
   }
   PSP_CK(cudaGetLastError());
   PSP_CK(cudaStreamSynchronize(st));
@@ -492,6 +631,11 @@ static void plan_solve(psp_ctx_s* X) {
         cols += sh.s[sn];
         P.smax = std::max(P.smax, (int)sh.s[sn]);
         P.ldmax = std::max(P.ldmax, (int)(sh.s[sn] + sh.u[sn]));
+      }
+      for (int sn : sh.level_sns[lv]) {
+        const double ss = sh.s[sn], uu = sh.u[sn];
+        P.entries += ss * (ss - 1) / 2 + uu * ss;
+        P.vec += 2 * ss + 2 * uu;
       }
       int R = 64;
       while (R > 8 && rows / R < 608) R >>= 1;
@@ -551,10 +695,17 @@ static void apply_impl(psp_ctx_s* X, double2* u, int nrhs, cudaStream_t st) {
     cx.has_next = i < X->m - 1;
     const auto& plan = X->splan[si];
     const int nl = (int)plan.size();
-    for (int lv = 0; lv < nl; ++lv)
-      launch_solve_fwd<T>(tasks + plan[lv].fwd_off, plan[lv].nfwd, cx, plan[lv].R, plan[lv].smax, st);
-    for (int lv = nl - 1; lv >= 0; --lv)
-      launch_solve_bwd<T>(tasks + plan[lv].bwd_off, plan[lv].nbwd, cx, plan[lv].ldmax, st);
+    const double es = sizeof(T);
+    for (int lv = 0; lv < nl; ++lv) {
+      const auto& P = plan[lv];
+      X->stats.run("k_solve_fwd", st, 1, 8.0 * P.entries * nrhs, P.entries * es + P.vec * es * nrhs,
+                   [&] { launch_solve_fwd<T>(tasks + P.fwd_off, P.nfwd, cx, P.R, P.smax, st); });
+    }
+    for (int lv = nl - 1; lv >= 0; --lv) {
+      const auto& P = plan[lv];
+      X->stats.run("k_solve_bwd", st, 1, 8.0 * P.entries * nrhs, P.entries * es + P.vec * es * nrhs,
+                   [&] { launch_solve_bwd<T>(tasks + P.bwd_off, P.nbwd, cx, P.ldmax, st); });
+    }
   };
   for (int i = 0; i < X->m; ++i) runT(i, 0);          // u_i := T_i (u_i - J_{i,i-1} u_{i-1})
   for (int i = X->m - 2; i >= 0; --i) runT(i, 1);     // u_i -= T_i J_{i+1,i}^T u_{i+1}
@@ -801,12 +952,30 @@ static void solve_impl(psp_ctx_s* X, const double2* f, double2* x, int nrhs, dou
   Ls.k = K; Ls.nrhs = nrhs;
   const int64_t ldv_vec = (int64_t)nrhs * N;
 
+  Stats& S = X->stats;
+  const double vb = 16.0 * N * nrhs;   // bytes of one vector block
+  auto matvec = [&](const double2* in, double2* out) {
+    S.run("k_matvec", st, 1, 8.0 * 7 * N * nrhs, 8.0 * N + 2 * vb, [&] { launch_matvec(X->opA, in, out, nrhs, N, st); });
+  };
+  auto multidot = [&](const double2* Vv, int64_t ldvv, int nvec, const double2* ww, double2* out) {
+    S.run("k_dot_partial+k_dot_final", st, 2, 8.0 * N * nvec * nrhs, (nvec + 1) * vb,
+          [&] { launch_multidot(Vv, ldvv, N, nvec, ww, N, nrhs, N, part, out, st); });
+  };
+  auto multiaxpy = [&](const double2* Vv, int nvec, const double2* hh, double2* ww, double sign) {
+    S.run("k_multiaxpy", st, 1, 8.0 * N * nvec * nrhs, (nvec + 2) * vb,
+          [&] { launch_multiaxpy(Vv, ldv_vec, N, nvec, hh, ww, N, nrhs, N, sign, st); });
+  };
+  auto axpby = [&](const double2* xx, double2* yy, const double2* al, int mode) {
+    S.run("k_axpby", st, 1, 8.0 * N * nrhs, 3 * vb, [&] { launch_axpby_batch(xx, yy, N, nrhs, al, mode, st); });
+  };
+  auto small = [&](const char* nm, auto&& fn) { S.run(nm, st, 1, 0.0, 0.0, fn); };
+
   auto t0 = std::chrono::steady_clock::now();
-  launch_scale_rhs(X->opA, f, b, nrhs, N, st);
+  S.run("k_scale_rhs", st, 1, 6.0 * N * nrhs, 2 * vb, [&] { launch_scale_rhs(X->opA, f, b, nrhs, N, st); });
   // ||b||
   std::vector<double> bnorm(nrhs), rel(nrhs, 1.0), hres(nrhs);
   std::vector<int> act(nrhs, 1), its(nrhs, 0), restarts(nrhs, 0), jrh(nrhs, 0);
-  launch_multidot(b, 0, N, 1, b, N, nrhs, N, part, nrm, st);
+  multidot(b, 0, 1, b, nrm);
   std::vector<double2> hn(nrhs);
   PSP_CK(cudaMemcpyAsync(hn.data(), nrm, nrhs * sizeof(double2), cudaMemcpyDeviceToHost, st));
   PSP_CK(cudaStreamSynchronize(st));
@@ -821,9 +990,9 @@ static void solve_impl(psp_ctx_s* X, const double2* f, double2* x, int nrhs, dou
   while (any && total_it < maxit) {
     PSP_CK(cudaMemcpyAsync(active, act.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
     // V_0 = r / ||r||
-    launch_multidot(w, 0, N, 1, w, N, nrhs, N, part, nrm, st);
-    launch_cycle_start(Ls, nrm, st);
-    launch_axpby_batch(w, V, N, nrhs, scl, 0, st);
+    multidot(w, 0, 1, w, nrm);
+    small("k_cycle_start", [&] { launch_cycle_start(Ls, nrm, st); });
+    axpby(w, V, scl, 0);
     for (int r = 0; r < nrhs; ++r) jrh[r] = 0;
     int j = 0;
     for (; j < K && total_it < maxit; ++j) {
@@ -832,15 +1001,15 @@ static void solve_impl(psp_ctx_s* X, const double2* f, double2* x, int nrhs, dou
       PSP_CK(cudaMemcpyAsync(Zj, Vj, nW * sizeof(double2), cudaMemcpyDeviceToDevice, st));
       apply_dispatch(X, Zj, nrhs, st);   // z_j = M^{-1} v_j
       ++applies;
-      launch_matvec(X->opA, Zj, w, nrhs, N, st);  // w = A z_j
+      matvec(Zj, w);  // w = A z_j
       // classical Gram-Schmidt, twice
-      launch_multidot(V, ldv_vec, N, j + 1, w, N, nrhs, N, part, h1, st);
-      launch_multiaxpy(V, ldv_vec, N, j + 1, h1, w, N, nrhs, N, -1.0, st);
-      launch_multidot(V, ldv_vec, N, j + 1, w, N, nrhs, N, part, h2, st);
-      launch_multiaxpy(V, ldv_vec, N, j + 1, h2, w, N, nrhs, N, -1.0, st);
-      launch_multidot(w, 0, N, 1, w, N, nrhs, N, part, nrm, st);
-      launch_arnoldi_step(Ls, j, h1, h2, nrm, st);
-      launch_axpby_batch(w, V + (int64_t)(j + 1) * ldv_vec, N, nrhs, scl, 0, st);
+      multidot(V, ldv_vec, j + 1, w, h1);
+      multiaxpy(V, j + 1, h1, w, -1.0);
+      multidot(V, ldv_vec, j + 1, w, h2);
+      multiaxpy(V, j + 1, h2, w, -1.0);
+      multidot(w, 0, 1, w, nrm);
+      small("k_arnoldi_step", [&] { launch_arnoldi_step(Ls, j, h1, h2, nrm, st); });
+      axpby(w, V + (int64_t)(j + 1) * ldv_vec, scl, 0);
       PSP_CK(cudaMemcpyAsync(hres.data(), resid, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
       PSP_CK(cudaStreamSynchronize(st));
       ++total_it;
@@ -857,12 +1026,12 @@ static void solve_impl(psp_ctx_s* X, const double2* f, double2* x, int nrhs, dou
     }
     // x += Z y for every rhs that iterated in this cycle
     PSP_CK(cudaMemcpyAsync(jr, jrh.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
-    launch_backsolve(Ls, jr, ybuf, st);
-    launch_multiaxpy(Z, ldv_vec, N, K, ybuf, x, N, nrhs, N, 1.0, st);
+    small("k_backsolve", [&] { launch_backsolve(Ls, jr, ybuf, st); });
+    multiaxpy(Z, K, ybuf, x, 1.0);
     // true residual r = b - A x
-    launch_matvec(X->opA, x, w, nrhs, N, st);
-    launch_axpby_batch(b, w, N, nrhs, nullptr, 1, st);
-    launch_multidot(w, 0, N, 1, w, N, nrhs, N, part, nrm, st);
+    matvec(x, w);
+    axpby(b, w, nullptr, 1);
+    multidot(w, 0, 1, w, nrm);
     PSP_CK(cudaMemcpyAsync(hn.data(), nrm, nrhs * sizeof(double2), cudaMemcpyDeviceToHost, st));
     PSP_CK(cudaStreamSynchronize(st));
     any = false;
@@ -961,6 +1130,7 @@ psp_status psp_setup(const psp_grid* g, const double* c, double omega, int pml_g
   X->gamma = pml_gamma; X->depth = panel_depth;
   X->pad = o.pad_depth < 0 ? pml_gamma : o.pad_depth;
   X->leaf = o.leaf_size; X->prec = o.precision; X->faces = o.pml_faces; X->aux_mode = o.aux_mode;
+  X->stats.timing = o.collect_stats != 0;
   *out = X;
   PSP_TRY
   setup_impl(X, c, (cudaStream_t)stream);
@@ -1010,7 +1180,8 @@ psp_status psp_matvec(psp_handle X, int which, const double* x, double* y, int n
     yd = X->stage_out.as<double2>();
   }
   if ((const void*)xd == (const void*)yd) return fail(PSP_ERR_ARG, "matvec cannot run in place");
-  launch_matvec(which == 0 ? X->opA : X->opJ, xd, yd, nrhs, X->N, st);
+  X->stats.run("k_matvec", st, 1, 8.0 * 7 * X->N * nrhs, 8.0 * X->N + 32.0 * X->N * nrhs,
+               [&] { launch_matvec(which == 0 ? X->opA : X->opJ, xd, yd, nrhs, X->N, st); });
   PSP_CK(cudaGetLastError());
   if (!dev_out) {
     PSP_CK(cudaMemcpyAsync(y, yd, bytes, cudaMemcpyDeviceToHost, st));
@@ -1102,6 +1273,33 @@ psp_status psp_export_front(psp_handle X, int panel, int sn, double* buf, int* s
     PSP_CK(cudaMemcpy(tmp.data(), src, n * 8, cudaMemcpyDeviceToHost));
     for (int64_t i = 0; i < 2 * n; ++i) buf[i] = tmp[i];
   }
+  return PSP_OK;
+  PSP_CATCH
+}
+
+psp_status psp_stats(psp_handle X, psp_kernel_stat* out, int capacity, int* count, int reset) {
+  if (!X || capacity < 0 || (capacity > 0 && !out)) return fail(PSP_ERR_ARG, "bad stats arguments");
+  PSP_TRY
+  X->stats.collect();
+  int i = 0;
+  for (auto& kv : X->stats.k) {
+    if (i < capacity) {
+      psp_kernel_stat& r = out[i];
+      std::memset(&r, 0, sizeof(r));
+      std::strncpy(r.name, kv.first.c_str(), sizeof(r.name) - 1);
+      r.launches = kv.second.launches;
+      r.total_ms = kv.second.ms;
+      r.flops = kv.second.flops;
+      r.bytes = kv.second.bytes;
+    }
+    ++i;
+  }
+  if (count) *count = i;
+  if (reset)
+    for (auto& kv : X->stats.k) {
+      kv.second.launches = 0;
+      kv.second.ms = kv.second.flops = kv.second.bytes = 0;
+    }
   return PSP_OK;
   PSP_CATCH
 }

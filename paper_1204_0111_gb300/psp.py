@@ -31,7 +31,12 @@ class Grid(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("pml_C", ctypes.c_double), ("alpha", ctypes.c_double), ("pad_depth", ctypes.c_int),
                 ("leaf_size", ctypes.c_int), ("precision", ctypes.c_int), ("pml_faces", ctypes.c_int),
-                ("aux_mode", ctypes.c_int), ("reserved", ctypes.c_int * 9)]
+                ("aux_mode", ctypes.c_int), ("collect_stats", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -78,6 +83,7 @@ def lib():
         "psp_symbolic_export": (_I, [_P, _I, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_size_t)]),
         "psp_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
         "psp_export_front": (_I, [_P, _I, _I, _P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+        "psp_stats": (_I, [_P, ctypes.POINTER(KernelStat), _I, ctypes.POINTER(_I), _I]),
         "psp_destroy": (_I, [_P]),
         "psp_status_string": (ctypes.c_char_p, [_I]),
         "psp_last_error": (ctypes.c_char_p, []),
@@ -128,7 +134,7 @@ class SweepingPreconditioner:
     """Handle over psp_setup / psp_apply / psp_solve (Algs. 1.4, 1.5 and GMRES(k) of §2.4)."""
 
     def __init__(self, c, h, omega, gamma, panel_depth, pad=None, leaf=64, pml_C=4.0, alpha=2 * math.pi,
-                 precision="c128", faces=63, mode="moving", stream=None):
+                 precision="c128", faces=63, mode="moving", stream=None, collect_stats=False):
         nz, ny, nx = c.shape
         self.nx, self.ny, self.nz = nx, ny, nz
         self.N = nx * ny * nz
@@ -142,6 +148,7 @@ class SweepingPreconditioner:
         o.precision = {"c128": PREC_C128, "c64": PREC_C64}[precision]
         o.pml_faces = int(faces)
         o.aux_mode = {"moving": AUX_MOVING_PML, "exact": AUX_EXACT}[mode]
+        o.collect_stats = 1 if collect_stats else 0
         cp, n = _ptr_and_len(c, complex_=False)
         if n != self.N:
             raise ValueError("c has the wrong size")
@@ -199,6 +206,15 @@ class SweepingPreconditioner:
         fb = ctypes.c_int64()
         _check(lib().psp_info(self._h, ctypes.byref(m), ctypes.byref(nf), ctypes.byref(fb)))
         return {"panels": m.value, "fronts": nf.value, "factor_bytes": fb.value}
+
+    def stats(self, reset=False):
+        """{kernel: {launches, total_ms, flops, bytes}} accumulated by this handle (psp_stats)."""
+        n = _I()
+        _check(lib().psp_stats(self._h, None, 0, ctypes.byref(n), 0))
+        buf = (KernelStat * max(n.value, 1))()
+        _check(lib().psp_stats(self._h, buf, n.value, ctypes.byref(n), 1 if reset else 0))
+        return {buf[i].name.decode(): {"launches": buf[i].launches, "total_ms": buf[i].total_ms,
+                                       "flops": buf[i].flops, "bytes": buf[i].bytes} for i in range(n.value)}
 
     def symbolic(self, panel):
         n = ctypes.c_size_t()
