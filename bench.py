@@ -32,9 +32,12 @@ WORKLOAD = "lens100"
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # SMs x FP64 flop/clk/SM (2 FMA) x max SM clock
 
 
+GRID_N = 100
+
+
 def workload():
     from paper_1204_0111_gb300 import workloads as wl
-    return wl.cube_lens(100)
+    return wl.cube_lens(GRID_N)
 
 
 def config_dict(w, nrhs, extra=None):
@@ -104,7 +107,7 @@ def oracle_estimate(iters, k=20):
 
 
 def w_desc():
-    return "100x100x12"
+    return f"{GRID_N}x{GRID_N}x12"
 
 
 def cpu_cores():
@@ -398,8 +401,13 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
-    ap.add_argument("--ref-iters", type=int, default=16, help="GMRES iterations assumed by the reference arm")
+    ap.add_argument("--ref-iters", type=int, default=18, help="GMRES iterations assumed by the reference arm")
+    ap.add_argument("--n", type=int, default=100, help="grid points per axis (100 = the benchmark workload; "
+                    "smaller sizes are for profiling captures)")
     a = ap.parse_args()
+    global GRID_N, WORKLOAD
+    GRID_N = a.n
+    WORKLOAD = f"lens{a.n}"
     if a.warmup < 3 and a.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if a.impl == "reference":
