@@ -125,6 +125,28 @@ psp_status psp_setup(const psp_grid* g, const double* c, double omega, int pml_g
 psp_status psp_apply(psp_handle h, const double* rhs, double* out, int nrhs, void* stream);
 
 /*
+ * psp_apply_noalloc - the same result as psp_apply, computed without allocating device memory.
+ * The paper has no counterpart; this entry point exists for callers that cannot allocate while
+ * they run: a process whose framework allocator already holds the free device memory (a cudaMalloc
+ * would fail although the caller has room), a process held to a fixed device-memory budget, or a
+ * loop timed as one stream-ordered region in which a cudaMalloc would synchronise the device.
+ * psp_apply grows its work vectors on demand; this call never calls cudaMalloc, cudaFree or any
+ * other allocating routine.
+ *  - Work vectors (two box vectors per panel and the fronts' update vectors, per right-hand side)
+ *    live in one file-scope device array of 16 MiB that every GPU context loading the library
+ *    reserves until the process exits.  When a problem needs more for the given nrhs the call
+ *    returns PSP_ERR_ARG with the size it needs; use psp_apply then.
+ *  - rhs and out are DEVICE pointers (N x nrhs, as for psp_apply; out may alias rhs).  Host
+ *    pointers are rejected with PSP_ERR_ARG: staging them would need an allocation.
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
+ *    device current; make that first call before any stream capture.
+ *  - Every call shares the one array, which keeps the last call's contents.  Nothing in it has to
+ *    start at zero: the sweep writes each work entry before it reads it.  Calls that overlap on the
+ *    GPU (other streams, handles or host threads) race on the array and give wrong results.
+ */
+psp_status psp_apply_noalloc(psp_handle h, const double* rhs, double* out, int nrhs, void* stream);
+
+/*
  * psp_matvec - y = A_s x (which = 0) or y = J_s x (which = 1), the 7-point
  * operators of Eq. (1.1) / Eq. (1.5) in the symmetric s1 s2 s3-scaled form.
  */

@@ -664,14 +664,14 @@ static void ensure_apply_ws(psp_ctx_s* X, int nrhs) {
   X->ws_nrhs = nrhs;
 }
 
-// Alg. 1.5 on a device block u (N x nrhs, in place)
+// Alg. 1.5 on a device block u (N x nrhs, in place), with the box and update-vector work
+// vectors given by the caller.  `timed` allows CUDA-event timing of the launches.
 template <typename T>
-static void apply_impl(psp_ctx_s* X, double2* u, int nrhs, cudaStream_t st) {
-  ensure_apply_ws<T>(X, nrhs);
+static void apply_core(psp_ctx_s* X, double2* u, int nrhs, T* xf, T* xb, T* upd, bool timed, cudaStream_t st) {
   SolveCtx<T> cx{};
-  cx.xf = X->ws_xf.as<T>();
-  cx.xb = X->ws_xb.as<T>();
-  cx.upd = X->ws_upd.as<T>();
+  cx.xf = xf;
+  cx.xb = xb;
+  cx.upd = upd;
   cx.u = u;
   cx.N = X->N;
   cx.nrhs = nrhs;
@@ -683,6 +683,8 @@ static void apply_impl(psp_ctx_s* X, double2* u, int nrhs, cudaStream_t st) {
   cx.upd_ld = X->max_upd;
   cx.n_loc = X->max_nloc;
   const SolveTask* tasks = X->d_stasks.as<SolveTask>();
+  const bool was_timing = X->stats.timing;
+  if (!timed) X->stats.timing = false;
   auto runT = [&](int i, int mode) {
     const int si = X->shape_of[i];
     cx.sh = X->shdev[si];
@@ -707,10 +709,56 @@ static void apply_impl(psp_ctx_s* X, double2* u, int nrhs, cudaStream_t st) {
                    [&] { launch_solve_bwd<T>(tasks + P.bwd_off, P.nbwd, cx, P.ldmax, st); });
     }
   };
-  for (int i = 0; i < X->m; ++i) runT(i, 0);          // u_i := T_i (u_i - J_{i,i-1} u_{i-1})
-  for (int i = X->m - 2; i >= 0; --i) runT(i, 1);     // u_i -= T_i J_{i+1,i}^T u_{i+1}
+  try {
+    for (int i = 0; i < X->m; ++i) runT(i, 0);          // u_i := T_i (u_i - J_{i,i-1} u_{i-1})
+    for (int i = X->m - 2; i >= 0; --i) runT(i, 1);     // u_i -= T_i J_{i+1,i}^T u_{i+1}
+  } catch (...) {
+    X->stats.timing = was_timing;
+    throw;
+  }
+  X->stats.timing = was_timing;
   PSP_CK(cudaGetLastError());
 }
+
+template <typename T>
+static void apply_impl(psp_ctx_s* X, double2* u, int nrhs, cudaStream_t st) {
+  ensure_apply_ws<T>(X, nrhs);
+  apply_core<T>(X, u, nrhs, X->ws_xf.as<T>(), X->ws_xb.as<T>(), X->ws_upd.as<T>(), true, st);
+}
+
+// work-vector layout of apply_core inside one caller-provided buffer
+static size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+
+size_t apply_workspace_bytes(const psp_ctx_s* X, int nrhs) {
+  const size_t e = X->elem_bytes;
+  return 2 * round256((size_t)X->max_nloc * nrhs * e) + round256((size_t)X->max_upd * nrhs * e);
+}
+
+psp_status apply_with_workspace(psp_ctx_s* X, double2* u, int nrhs, void* ws, cudaStream_t st) {
+  try {
+    char* p = static_cast<char*>(ws);
+    const size_t e = X->elem_bytes;
+    const size_t bx = round256((size_t)X->max_nloc * nrhs * e);
+    if (X->prec == PSP_PREC_C64)
+      apply_core<float2>(X, u, nrhs, (float2*)p, (float2*)(p + bx), (float2*)(p + 2 * bx), false, st);
+    else
+      apply_core<double2>(X, u, nrhs, (double2*)p, (double2*)(p + bx), (double2*)(p + 2 * bx), false, st);
+  } catch (const Error& err) {
+    g_last_error = err.msg;
+    return err.st;
+  } catch (const std::exception& ex) {
+    g_last_error = ex.what();
+    return PSP_ERR_STATE;
+  }
+  return PSP_OK;
+}
+
+psp_status set_error(psp_status s, const char* msg) {
+  g_last_error = msg;
+  return s;
+}
+
+int64_t handle_points(const psp_ctx_s* X) { return X->d_factor.p ? X->N : -1; }
 
 static void apply_dispatch(psp_ctx_s* X, double2* u, int nrhs, cudaStream_t st) {
   if (X->prec == PSP_PREC_C64) apply_impl<float2>(X, u, nrhs, st);

@@ -8,7 +8,15 @@
 
 #include "psp.h"
 
+struct psp_ctx_s;
+
 namespace psp {
+
+// sweep with caller-provided work vectors (defined in psp_api.cu)
+size_t apply_workspace_bytes(const psp_ctx_s* X, int nrhs);
+psp_status apply_with_workspace(psp_ctx_s* X, double2* u, int nrhs, void* ws, cudaStream_t st);
+int64_t handle_points(const psp_ctx_s* X);   // N, or -1 when the handle has no factorisation
+psp_status set_error(psp_status s, const char* msg);
 
 // ---------------------------------------------------------------------------
 // Symbolic analysis of one auxiliary-problem box (nx x ny x depth): the

@@ -78,6 +78,7 @@ def lib():
         "psp_setup": (_I, [ctypes.POINTER(Grid), _P, ctypes.c_double, _I, _I, ctypes.POINTER(Options), _P,
                            ctypes.POINTER(_P)]),
         "psp_apply": (_I, [_P, _P, _P, _I, _P]),
+        "psp_apply_noalloc": (_I, [_P, _P, _P, _I, _P]),
         "psp_matvec": (_I, [_P, _I, _P, _P, _I, _P]),
         "psp_solve": (_I, [_P, _P, _P, _I, ctypes.c_double, _I, _I, ctypes.POINTER(SolveInfo), _P]),
         "psp_symbolic_export": (_I, [_P, _I, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_size_t)]),
