@@ -76,8 +76,11 @@ typedef struct {
   int precision;      /* psp_precision, default PSP_PREC_C128 */
   int pml_faces;      /* bit mask x-lo 1, x-hi 2, y-lo 4, y-hi 8, z-lo 16, z-hi 32; default 63 */
   int aux_mode;       /* psp_aux_mode, default PSP_AUX_MOVING_PML */
-  int collect_stats;  /* 1: time every kernel launch of this handle with CUDA events (psp_stats), default 0 */
-  int reserved[8];
+  int collect_stats;  /* CUDA-event timing of launches (psp_stats): 0 none (default), 1 every kernel,
+                         2 the setup kernels only (a few hundred launches per setup) */
+  int tensor_cores;   /* complex64 path: 1 (default) runs the Schur update and the selective-inversion
+                         multiplies on tcgen05 tensor cores, 0 keeps them on CUDA cores */
+  int reserved[7];
 } psp_options;
 
 /* Per-solve report filled by psp_solve (host struct). */
@@ -186,8 +189,8 @@ psp_status psp_export_front(psp_handle h, int panel, int supernode, double* buf,
 
 /*
  * Per-kernel accounting of one handle (setup, applies, matvecs and solves issued through it).
- * Launch counts and algorithmic work are always kept; total_ms is filled only when the handle
- * was created with collect_stats = 1 (CUDA events around every launch, on the launch stream).
+ * Launch counts and algorithmic work are always kept; total_ms is filled for the kernels that the
+ * handle's collect_stats selects (CUDA events around each such launch, on the launch stream).
  * flops: useful real floating-point operations (a complex multiply-add counts 8); bytes: the
  * algorithmic HBM bytes (matrix entries read once, vectors read/written once).
  * Copies min(capacity, kinds) records into out, sets *count to the number of kernel kinds,

@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(256) k_diag_ldlt(const FrontTask<T>* __restric
   __syncthreads();
   for (int j = 0; j < bs; ++j) {
     const T d = S[j][j];
-    if (threadIdx.x == 0 && (double)cabs2(d) < tiny * tiny) atomicCAS(status, 0, (int)(1 + ft.gfid));
+    if (threadIdx.x == 0 && fmax(fabs((double)d.x), fabs((double)d.y)) < tiny) atomicCAS(status, 0, (int)(1 + ft.gfid));
     const T dinv = cdiv(CplxTraits<T>::one(), d);
     for (int i = j + 1 + threadIdx.x; i < bs; i += blockDim.x) {
       const T a = S[j][i];
@@ -135,25 +135,29 @@ __global__ void __launch_bounds__(64) k_panel_left(const FrontTask<T>* __restric
 
 // ---------------------------------------------------------------------------
 // Batched complex GEMM, one 64 x 64 output tile per CTA (16 x 16 threads, 4 x 4 each).
+// Complex products use three real multiplications (Gauss): with the pre-sums ar + ai and
+// br + bi staged in shared memory, t1 += ar br, t2 += ai bi, t3 += (ar + ai)(br + bi), and at the
+// end re = t1 - t2, im = t3 - t1 - t2.  Three FMAs per complex MAC instead of four.
 // ---------------------------------------------------------------------------
-constexpr int GT = 64, GK = 16;
+constexpr int GT = 64, GK = 8;
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_gemm(const GemmTask<T>* __restrict__ tasks) {
-  __shared__ T As[GK][GT + 1];
-  __shared__ T Bs[GK][GT + 1];
+  using R = typename CplxTraits<T>::real;
+  __shared__ R Ar[GK][GT + 1], Ai[GK][GT + 1], As[GK][GT + 1];
+  __shared__ R Br[GK][GT + 1], Bi[GK][GT + 1], Bs[GK][GT + 1];
   const GemmTask<T> tk = tasks[blockIdx.x];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const T zero = CplxTraits<T>::zero();
-  T acc[4][4];
+  R t1[4][4], t2[4][4], t3[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = zero;
+    for (int b = 0; b < 4; ++b) t1[a][b] = t2[a][b] = t3[a][b] = R(0);
 
   const bool bnn = tk.flags & GF_B_NN;
   for (int k0 = 0; k0 < tk.k; k0 += GK) {
-    // A chunk: 64 rows x 16 k
+    // A chunk: 64 rows x GK k
     for (int e = threadIdx.x; e < GT * GK; e += 256) {
       const int i = e % GT, kk = e / GT;
       T v = zero;
@@ -164,9 +168,11 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTask<T>* __restrict__ ta
           v = (tk.flags & GF_D_MUL) ? cmul(v, dd) : cdiv(v, dd);
         }
       }
-      As[kk][i] = v;
+      Ar[kk][i] = v.x;
+      Ai[kk][i] = v.y;
+      As[kk][i] = v.x + v.y;
     }
-    // B chunk: 64 n x 16 k
+    // B chunk: 64 n x GK k
     for (int e = threadIdx.x; e < GT * GK; e += 256) {
       int j, kk;
       if (bnn) { kk = e % GK; j = e / GK; } else { j = e % GT; kk = e / GT; }
@@ -179,20 +185,34 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTask<T>* __restrict__ ta
           else if ((tk.flags & GF_B_UNIT_LOWER_NT) ? (kg > ng) : (kg < ng)) v = zero;
         }
       }
-      Bs[kk][j] = v;
+      Br[kk][j] = v.x;
+      Bi[kk][j] = v.y;
+      Bs[kk][j] = v.x + v.y;
     }
     __syncthreads();
-#pragma unroll 4
+#pragma unroll
     for (int kk = 0; kk < GK; ++kk) {
-      T av[4], bv[4];
+      R ar[4], ai[4], as[4], br[4], bi[4], bs[4];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) av[a] = As[kk][ty + 16 * a];
+      for (int a = 0; a < 4; ++a) {
+        ar[a] = Ar[kk][ty + 16 * a];
+        ai[a] = Ai[kk][ty + 16 * a];
+        as[a] = As[kk][ty + 16 * a];
+      }
 #pragma unroll
-      for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][tx + 16 * b];
+      for (int b = 0; b < 4; ++b) {
+        br[b] = Br[kk][tx + 16 * b];
+        bi[b] = Bi[kk][tx + 16 * b];
+        bs[b] = Bs[kk][tx + 16 * b];
+      }
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) cfma(acc[a][b], av[a], bv[b]);
+        for (int b = 0; b < 4; ++b) {
+          t1[a][b] = fma(ar[a], br[b], t1[a][b]);
+          t2[a][b] = fma(ai[a], bi[b], t2[a][b]);
+          t3[a][b] = fma(as[a], bs[b], t3[a][b]);
+        }
     }
     __syncthreads();
   }
@@ -205,8 +225,11 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTask<T>* __restrict__ ta
     for (int b = 0; b < 4; ++b) {
       const int j = tx + 16 * b;
       if (j >= tk.n || (lower && i < j)) continue;
+      T v;
+      v.x = t1[a][b] - t2[a][b];
+      v.y = t3[a][b] - t1[a][b] - t2[a][b];
+      if (neg) v = cneg(v);
       T* c = tk.C + (int64_t)j * tk.ldc + i;
-      T v = neg ? cneg(acc[a][b]) : acc[a][b];
       *c = beta0 ? v : cadd(*c, v);
     }
   }

@@ -28,17 +28,17 @@ __device__ __forceinline__ T input_value(const SolveCtx<T>& cx, int node, int q)
   double2 v;
   if (cx.mode == 0) {
     // u_i - J_{i,i-1} u_{i-1}: J's coupling entry is -s1 s2 / s3(z0 - 1/2) / h^2
-    v = uq[g];
+    v = __ldcg(uq + g);
     if (cx.has_prev && zg == cx.z0) {
       const double2 a = cscale(cmul(cmul(cx.s1n[x], cx.s2n[y]), cx.s3h[cx.z0]), cx.inv_h2);
-      cfma(v, a, uq[g - plane]);
+      cfma(v, a, __ldcg(uq + g - plane));
     }
   } else {
     // J_{i+1,i}^T u_{i+1}: supported on the panel's last plane
     v = make_double2(0.0, 0.0);
     if (cx.has_next && zg == cx.z1 - 1) {
       const double2 a = cscale(cmul(cmul(cx.s1n[x], cx.s2n[y]), cx.s3h[cx.z1]), -cx.inv_h2);
-      v = cmul(a, uq[g + plane]);
+      v = cmul(a, __ldcg(uq + g + plane));
     }
   }
   return CplxTraits<T>::from(v);
@@ -52,15 +52,14 @@ __device__ __forceinline__ void pull_add(const SolveCtx<T>& cx, const int32_t* p
     if (o < 0) break;
 #pragma unroll
     for (int q = 0; q < RG; ++q)
-      if (rhs0 + q < cx.nrhs) out[q] = cadd(out[q], cx.upd[(int64_t)(rhs0 + q) * cx.upd_ld + o]);
+      if (rhs0 + q < cx.nrhs) out[q] = cadd(out[q], __ldcg(cx.upd + (int64_t)(rhs0 + q) * cx.upd_ld + o));
   }
 }
 
+// up-the-tree task: rows [r0, r1) of front sn, right-hand sides [rhs0, rhs0 + RG)
 template <typename T, int RG>
-__global__ void __launch_bounds__(256) k_solve_fwd(const SolveTask* __restrict__ tasks, SolveCtx<T> cx, int R) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const SolveTask tk = tasks[blockIdx.x];
-  const int rhs0 = blockIdx.y * RG;
+__device__ __forceinline__ void fwd_task(const SolveTask tk, const int rhs0, const SolveCtx<T>& cx, const int R,
+                                         unsigned char* smem_raw) {
   const int sn = tk.sn;
   const int s = cx.sh.s[sn], u = cx.sh.u[sn], ld = s + u;
   const int first = cx.sh.first[sn];
@@ -89,8 +88,20 @@ __global__ void __launch_bounds__(256) k_solve_fwd(const SolveTask* __restrict__
   if (r < tk.r1) {
     const int jmax = r < s ? r : s;   // strictly lower part of inv(L_TL), all of M_BL
     const T* Gr = G + r;
-    for (int j = grp; j < jmax; j += ngrp) {
-      const T gv = Gr[(int64_t)j * ld];
+    const int64_t step = (int64_t)ngrp * ld;
+    int j = grp;
+    // eight independent factor loads in flight per thread
+    for (; j + 7 * ngrp < jmax; j += 8 * ngrp) {
+      T gv[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) gv[t] = __ldg(Gr + (int64_t)j * ld + t * step);
+#pragma unroll
+      for (int t = 0; t < 8; ++t)
+#pragma unroll
+        for (int q = 0; q < RG; ++q) cfma(acc[q], gv[t], w[(j + t * ngrp) * RG + q]);
+    }
+    for (; j < jmax; j += ngrp) {
+      const T gv = __ldg(Gr + (int64_t)j * ld);
 #pragma unroll
       for (int q = 0; q < RG; ++q) cfma(acc[q], gv, w[j * RG + q]);
     }
@@ -122,10 +133,15 @@ __global__ void __launch_bounds__(256) k_solve_fwd(const SolveTask* __restrict__
 }
 
 template <typename T, int RG>
-__global__ void __launch_bounds__(256) k_solve_bwd(const SolveTask* __restrict__ tasks, SolveCtx<T> cx) {
+__global__ void __launch_bounds__(256) k_solve_fwd(const SolveTask* __restrict__ tasks, SolveCtx<T> cx, int R) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const SolveTask tk = tasks[blockIdx.x];
-  const int rhs0 = blockIdx.y * RG;
+  fwd_task<T, RG>(tasks[blockIdx.x], blockIdx.y * RG, cx, R, smem_raw);
+}
+
+// down-the-tree task: columns [r0, r1) of S of front sn
+template <typename T, int RG>
+__device__ __forceinline__ void bwd_task(const SolveTask tk, const int rhs0, const SolveCtx<T>& cx,
+                                         unsigned char* smem_raw) {
   const int sn = tk.sn;
   const int s = cx.sh.s[sn], u = cx.sh.u[sn], ld = s + u;
   const int first = cx.sh.first[sn];
@@ -139,7 +155,7 @@ __global__ void __launch_bounds__(256) k_solve_bwd(const SolveTask* __restrict__
       T v = CplxTraits<T>::zero();
       if (rhs0 + q < cx.nrhs) {
         const int64_t base = (int64_t)(rhs0 + q) * cx.n_loc;
-        v = (r < s) ? cx.xf[base + first + r] : cneg(cx.xb[base + sel[r - s]]);
+        v = (r < s) ? __ldcg(cx.xf + base + first + r) : cneg(__ldcg(cx.xb + base + sel[r - s]));
       }
       y[(r - c0) * RG + q] = v;
     }
@@ -151,8 +167,18 @@ __global__ void __launch_bounds__(256) k_solve_bwd(const SolveTask* __restrict__
 #pragma unroll
     for (int q = 0; q < RG; ++q) acc[q] = CplxTraits<T>::zero();
     const T* Gc = G + (int64_t)c * ld;
-    for (int r = c + 1 + lane; r < ld; r += 32) {
-      const T gv = Gc[r];
+    int r = c + 1 + lane;
+    for (; r + 7 * 32 < ld; r += 8 * 32) {   // eight independent factor loads in flight per lane
+      T gv[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) gv[t] = __ldg(Gc + r + 32 * t);
+#pragma unroll
+      for (int t = 0; t < 8; ++t)
+#pragma unroll
+        for (int q = 0; q < RG; ++q) cfma(acc[q], gv[t], y[(r + 32 * t - c0) * RG + q]);
+    }
+    for (; r < ld; r += 32) {
+      const T gv = __ldg(Gc + r);
 #pragma unroll
       for (int q = 0; q < RG; ++q) cfma(acc[q], gv, y[(r - c0) * RG + q]);
     }
@@ -176,10 +202,152 @@ __global__ void __launch_bounds__(256) k_solve_bwd(const SolveTask* __restrict__
         if (k >= cx.lead) {   // the panel's own planes (Alg. 1.3 extraction)
           double2* uq = cx.u + (int64_t)(rhs0 + q) * cx.N + g;
           const double2 o = to_c128(out);
-          *uq = (cx.mode == 0) ? o : csub(*uq, o);
+          *uq = (cx.mode == 0) ? o : csub(__ldcg(uq), o);
         }
       }
     }
+  }
+}
+
+template <typename T, int RG>
+__global__ void __launch_bounds__(256) k_solve_bwd(const SolveTask* __restrict__ tasks, SolveCtx<T> cx) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  bwd_task<T, RG>(tasks[blockIdx.x], blockIdx.y * RG, cx, smem_raw);
+}
+
+// rhs group size so that the shared-memory footprint stays below ~200 KB
+template <typename T>
+static int pick_rg(int nrhs, size_t per_rhs_bytes) {
+  int rg = 8;
+  while (rg > 1 && (rg >= 2 * nrhs || per_rhs_bytes * rg > 200 * 1024)) rg >>= 1;
+  return rg;
+}
+
+// ---------------------------------------------------------------------------
+// The whole sweep of Alg. 1.5 in one cooperative launch, as a dataflow over the elimination trees.
+// CTAs take tasks from one queue in topological order.  An up-the-tree task of a front waits until
+// every task of its children has finished (and, for the first panel solve's dependence on the one
+// before, until that whole solve has finished); a down-the-tree task waits for its parent (the
+// root: for its own up-the-tree tasks).  A task only waits on tasks earlier in the queue, which are
+// held by running CTAs, and every CTA of a cooperative launch is resident, so the waits end.  Each
+// wait is bounded anyway: a CTA that gives up sets status[2] and stops; the others then give up
+// at their next wait.
+// ---------------------------------------------------------------------------
+constexpr long long kWaitSpins = 20000000;   // x ~64 ns sleep: about a second
+
+__device__ __forceinline__ bool wait_count(const unsigned* p, unsigned target, int* status) {
+  long long it = 0;
+  while (*(volatile const unsigned*)p < target) {
+    if (*(volatile int*)(status + 2) != 0) return false;
+    if (++it > kWaitSpins) {
+      atomicExch(status + 2, 1);
+      return false;
+    }
+    __nanosleep(32);
+  }
+  return true;
+}
+
+constexpr int kMaxSweepShapes = 4, kMaxSweepSteps = 512, kMaxSweepPanels = 256;
+
+template <typename T, int RG>
+__global__ void __launch_bounds__(256) k_sweep(SweepArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_idx, s_next, s_ok;
+  __shared__ ShapeDev s_shape[kMaxSweepShapes];
+  __shared__ SweepStep s_step[kMaxSweepSteps];
+  __shared__ PanelSweep s_panel[kMaxSweepPanels];
+  // small per-sweep tables in shared memory: every task needs them
+  for (int i = threadIdx.x; i < a.nshapes; i += blockDim.x) s_shape[i] = a.shapes[i];
+  for (int i = threadIdx.x; i < a.nsteps; i += blockDim.x) s_step[i] = a.steps[i];
+  for (int i = threadIdx.x; i < a.npanels; i += blockDim.x) s_panel[i] = a.panels[i];
+  if (threadIdx.x == 0) s_next = (int)atomicAdd(a.queue_head, 1u);
+  __syncthreads();
+  SolveCtx<T> cx = a.cx;
+  const int nrg = (cx.nrhs + RG - 1) / RG;
+  for (;;) {
+    if (threadIdx.x == 0) s_idx = s_next;
+    __syncthreads();
+    const int idx = s_idx;
+    if (idx >= a.nqueue) break;
+    const QueueEntry e = a.queue[idx];
+    const SweepStep sp = s_step[e.step];
+    const PanelSweep& pi = s_panel[sp.panel];
+    cx.sh = s_shape[pi.shape];
+    cx.G = a.factor + pi.gbase;
+    cx.z0 = pi.z0;
+    cx.z1 = pi.z1;
+    cx.lead = pi.lead;
+    cx.has_prev = pi.has_prev;
+    cx.has_next = pi.has_next;
+    cx.mode = sp.mode;
+    const SolveTask tk = a.tasks[e.task];
+    const int fb = a.front_base[pi.shape];
+    unsigned* up = a.done_up + a.step_front_base[e.step];
+    unsigned* down = a.done_down + a.step_front_base[e.step];
+    if (threadIdx.x == 0) {
+      s_next = (int)atomicAdd(a.queue_head, 1u);   // next task, fetched while this one runs
+      bool ok = true;
+      if (e.dir == 0) {
+        if (e.step > 0) ok = wait_count(a.step_done + e.step - 1, (unsigned)a.step_tasks[e.step - 1], a.status);
+        for (int c = cx.sh.child_ptr[tk.sn]; ok && c < cx.sh.child_ptr[tk.sn + 1]; ++c) {
+          const int ch = cx.sh.child_idx[c];
+          ok = wait_count(up + ch, (unsigned)a.ntask_up[fb + ch], a.status);
+        }
+      } else {
+        const int par = cx.sh.parent[tk.sn];
+        ok = par >= 0 ? wait_count(down + par, (unsigned)a.ntask_down[fb + par], a.status)
+                      : wait_count(up + tk.sn, (unsigned)a.ntask_up[fb + tk.sn], a.status);
+      }
+      __threadfence();
+      s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) break;
+    for (int g = 0; g < nrg; ++g) {
+      if (e.dir == 0) fwd_task<T, RG>(tk, g * RG, cx, e.R, smem_raw);
+      else bwd_task<T, RG>(tk, g * RG, cx, smem_raw);
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd((e.dir == 0 ? up : down) + tk.sn, 1u);
+      atomicAdd(a.step_done + e.step, 1u);
+    }
+  }
+}
+
+template <typename T, int RG>
+static int sweep_rg(const SweepArgs<T>& args, size_t per_rhs_bytes, cudaStream_t st) {
+  const size_t smem = per_rhs_bytes * RG;
+  if (cudaFuncSetAttribute(k_sweep<T, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  int dev = 0, sms = 0, per_sm = 0, coop = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (!coop) return -1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep<T, RG>, 256, smem) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    return -1;
+  }
+  per_sm = per_sm > 8 ? 8 : per_sm;
+  SweepArgs<T> a = args;
+  void* kargs[] = {&a};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_sweep<T, RG>, dim3(sms * per_sm), dim3(256), kargs, smem, st);
+  return e == cudaSuccess ? 0 : (int)e;
+}
+
+template <typename T>
+int launch_sweep(const SweepArgs<T>& args, size_t per_rhs_bytes, cudaStream_t st) {
+  const int rg = pick_rg<T>(args.cx.nrhs, per_rhs_bytes);
+  switch (rg) {
+    case 8: return sweep_rg<T, 8>(args, per_rhs_bytes, st);
+    case 4: return sweep_rg<T, 4>(args, per_rhs_bytes, st);
+    case 2: return sweep_rg<T, 2>(args, per_rhs_bytes, st);
+    default: return sweep_rg<T, 1>(args, per_rhs_bytes, st);
   }
 }
 
@@ -205,14 +373,6 @@ static void bwd_rg(const SolveTask* tasks, int ntasks, const SolveCtx<T>& cx, in
   }
   dim3 grid(ntasks, (cx.nrhs + RG - 1) / RG);
   k_solve_bwd<T, RG><<<grid, 256, smem, st>>>(tasks, cx);
-}
-
-// rhs group size so that the shared-memory footprint stays below ~200 KB
-template <typename T>
-static int pick_rg(int nrhs, size_t per_rhs_bytes) {
-  int rg = 8;
-  while (rg > 1 && (rg >= 2 * nrhs || per_rhs_bytes * rg > 200 * 1024)) rg >>= 1;
-  return rg;
 }
 
 template <typename T>
@@ -243,5 +403,7 @@ template void launch_solve_fwd<double2>(const SolveTask*, int, const SolveCtx<do
 template void launch_solve_fwd<float2>(const SolveTask*, int, const SolveCtx<float2>&, int, int, cudaStream_t);
 template void launch_solve_bwd<double2>(const SolveTask*, int, const SolveCtx<double2>&, int, cudaStream_t);
 template void launch_solve_bwd<float2>(const SolveTask*, int, const SolveCtx<float2>&, int, cudaStream_t);
+template int launch_sweep<double2>(const SweepArgs<double2>&, size_t, cudaStream_t);
+template int launch_sweep<float2>(const SweepArgs<float2>&, size_t, cudaStream_t);
 
 }  // namespace psp

@@ -10,6 +10,7 @@
 #include <new>
 #include <stdexcept>
 #include <tuple>
+#include <type_traits>
 #include <string>
 #include <vector>
 
@@ -102,7 +103,8 @@ struct KStat {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
 };
 struct Stats {
-  bool timing = false;
+  bool timing = false;  // master switch (off inside the allocation-free apply)
+  int mode = 0;         // 0 none, 1 every kernel, 2 setup kernels only
   std::map<std::string, KStat> k;
   std::vector<cudaEvent_t> pool;
   int64_t npending = 0;
@@ -117,12 +119,12 @@ struct Stats {
     return e;
   }
   template <class F>
-  void run(const char* name, cudaStream_t st, int nlaunch, double flops, double bytes, F&& launch) {
+  void run(const char* name, cudaStream_t st, int nlaunch, double flops, double bytes, F&& launch, bool setup = false) {
     KStat& s = k[name];
     s.launches += nlaunch;
     s.flops += flops;
     s.bytes += bytes;
-    if (!timing) {
+    if (!timing || mode == 0 || (mode == 2 && !setup)) {
       launch();
       return;
     }
@@ -151,6 +153,11 @@ struct Stats {
       npending -= (int64_t)n;
     }
     if (npending < 0) npending = 0;
+  }
+  // host-side phase of setup/solve (wall time, recorded as "host:<phase>")
+  void host(const std::string& phase, double ms) {
+    KStat& s = k["host:" + phase];
+    s.ms += ms;
   }
   ~Stats() {
     for (auto& kv : k)
@@ -201,6 +208,13 @@ struct psp_ctx_s {
   };
   std::vector<std::vector<LevelPlan>> splan;
   DevBuf d_stasks;
+  // persistent sweep plan
+  DevBuf d_sweep_steps, d_sweep_panels, d_sweep_queue, d_sweep_meta, d_sweep_sync;
+  int sweep_nsteps = 0, sweep_nqueue = 0;
+  size_t sweep_sync_words = 0;
+  int64_t meta_front_base = 0, meta_ntask_down = 0, meta_step_front = 0, meta_step_tasks = 0;
+  size_t sweep_rhs_bytes = 0;      // shared memory per right-hand side of the widest level
+  double sweep_entries = 0, sweep_vec = 0;   // algorithmic entries / vector words per apply
   int64_t max_nloc = 0, max_upd = 0;
   // apply workspaces
   DevBuf ws_xf, ws_xb, ws_upd;
@@ -211,6 +225,8 @@ struct psp_ctx_s {
   DevBuf gm;
   int gm_nrhs = 0, gm_k = 0;
   int zero_pivot_front = -1;
+  bool use_tc = true;
+  bool persistent_sweep = true;
   Stats stats;
 };
 
@@ -282,8 +298,13 @@ static double gemm_cmacs(const GemmTask<T>& g) {
 // Plan and run the factorisation of all panels, level by level (all panels' fronts of one
 // tree level in each launch: the panels are independent, §2).
 // ---------------------------------------------------------------------------
+static double ms_since(std::chrono::steady_clock::time_point t0) {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
 template <typename T>
 static void factor_all(psp_ctx_s* X, cudaStream_t st) {
+  auto tp = std::chrono::steady_clock::now();
   const int nb = 32;
   const double tiny = sizeof(T) == 16 ? 1e-300 : 1e-30;
   int L = 0;
@@ -317,9 +338,13 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
       }
     }
   }
+  X->stats.host("plan_memory", ms_since(tp));
+  tp = std::chrono::steady_clock::now();
   DevBuf d_upd, d_temp;
   d_upd.alloc((size_t)std::max<int64_t>(ua.peak, 16) * sizeof(T));
   d_temp.alloc((size_t)std::max<int64_t>(temp_max, 16) * sizeof(T));
+  X->stats.host("alloc_work", ms_since(tp));
+  tp = std::chrono::steady_clock::now();
   T* ubase = d_upd.as<T>();
   T* tbase = d_temp.as<T>();
   T* fbase = X->d_factor.as<T>();
@@ -334,7 +359,7 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
   std::vector<ColTask> ctasks;
   std::vector<int> dlist;
   std::vector<GemmTask<T>> gtasks;
-  enum Kind { ASSEMBLE, DIAG, PRIGHT, PLEFT, GEMM, COPY };
+  enum Kind { ASSEMBLE, DIAG, PRIGHT, PLEFT, GEMM, COPY, TCGEMM };
   struct Launch {
     Kind kind;
     int64_t front_off;
@@ -499,44 +524,35 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
       for (int f = 0; f < nf; ++f) lc.bytes += es * (double)fronts[f0 + f].s * (fronts[f0 + f].s - 1);
       launches.push_back(lc);
     }
-    // Z = F_BL inv(L_TL)^T  (= F_BL L^{-T})
-    {
-      const int64_t g0 = (int64_t)gtasks.size();
-      for (int f = 0; f < nf; ++f) {
-        const auto& ft = fronts[f0 + f];
-        if (ft.u == 0) continue;
-        const int ld = ft.s + ft.u;
-        for (int tj = 0; tj < ft.s; tj += 64)
-          for (int ti = 0; ti < ft.u; ti += 64) {
-            GemmTask<T> g{};
-            const int j1 = std::min(tj + 64, ft.s);
-            g.C = ft.Z + (int64_t)tj * ft.u + ti;
-            g.ldc = ft.u;
-            g.A = ft.G + ft.s + ti;  // F_BL rows, k from 0
-            g.lda = ld;
-            g.B = ft.G + tj;         // B(n, k) = Linv[tj + n, k]
-            g.ldb = ld;
-            g.m = std::min(64, ft.u - ti);
-            g.n = j1 - tj;
-            g.k = j1;
-            g.kg0 = 0;
-            g.ng0 = tj;
-            g.flags = GF_BETA0 | GF_B_UNIT_LOWER_NT;
-            gtasks.push_back(g);
-          }
-      }
-      Launch lg{GEMM, f0, g0, (int)(gtasks.size() - g0), -1};
-      gemm_work(g0, lg.flops, lg.bytes);
-      launches.push_back(lg);
-    }
-    // F_BR -= Z D^{-1} Z^T (lower) and M_BL = Z D^{-1} inv(L_TL)
-    {
-      const int64_t g0 = (int64_t)gtasks.size();
-      for (int f = 0; f < nf; ++f) {
-        const auto& ft = fronts[f0 + f];
-        if (ft.u == 0) continue;
-        const int ld = ft.s + ft.u;
-        tiles_lower(ft.U, ft.u, ft.u, [&](T*, int, int ti, int tj, int mm, int nn) {
+    // the long-contraction GEMMs of fronts with enough work run on tcgen05 tiles of 128 x 128
+    // (complex64); smaller fronts stay on the 64 x 64 CUDA-core tiles
+    const bool tc_ok = std::is_same<T, float2>::value && X->use_tc;
+    auto use_tc = [&](const FrontTask<T>& ft) { return tc_ok && ft.s >= 96 && ft.u >= 96; };
+    auto emit_z = [&](const FrontTask<T>& ft, int TT) {
+      const int ld = ft.s + ft.u;
+      for (int tj = 0; tj < ft.s; tj += TT)
+        for (int ti = 0; ti < ft.u; ti += TT) {
+          GemmTask<T> g{};
+          const int j1 = std::min(tj + TT, ft.s);
+          g.C = ft.Z + (int64_t)tj * ft.u + ti;
+          g.ldc = ft.u;
+          g.A = ft.G + ft.s + ti;  // F_BL rows, k from 0
+          g.lda = ld;
+          g.B = ft.G + tj;         // B(n, k) = Linv[tj + n, k]
+          g.ldb = ld;
+          g.m = std::min(TT, ft.u - ti);
+          g.n = j1 - tj;
+          g.k = j1;
+          g.kg0 = 0;
+          g.ng0 = tj;
+          g.flags = GF_BETA0 | GF_B_UNIT_LOWER_NT;
+          gtasks.push_back(g);
+        }
+    };
+    auto emit_schur_m = [&](const FrontTask<T>& ft, int TT) {
+      const int ld = ft.s + ft.u;
+      for (int tj = 0; tj < ft.u; tj += TT)
+        for (int ti = tj; ti < ft.u; ti += TT) {
           GemmTask<T> g{};
           g.C = ft.U + (int64_t)tj * ft.u + ti;
           g.ldc = ft.u;
@@ -546,36 +562,52 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
           g.ldb = ft.u;
           g.d = ft.G;
           g.ldd = ld + 1;
-          g.m = mm; g.n = nn; g.k = ft.s;
+          g.m = std::min(TT, ft.u - ti);
+          g.n = std::min(TT, ft.u - tj);
+          g.k = ft.s;
           g.flags = GF_D_DIV | GF_NEG | (ti == tj ? GF_C_LOWER : 0);
           gtasks.push_back(g);
-        });
-        for (int tj = 0; tj < ft.s; tj += 64)
-          for (int ti = 0; ti < ft.u; ti += 64) {
-            GemmTask<T> g{};
-            g.C = ft.G + (int64_t)tj * ld + ft.s + ti;
-            g.ldc = ld;
-            g.A = ft.Z + (int64_t)tj * ft.u + ti;   // A(i, k) = Z[ti + i, tj + k]
-            g.lda = ft.u;
-            g.d = ft.G + (int64_t)tj * (ld + 1);
-            g.ldd = ld + 1;
-            g.B = ft.G + (int64_t)tj * ld + tj;     // B(n, k) = Linv[tj + k, tj + n]
-            g.ldb = ld;
-            g.m = std::min(64, ft.u - ti);
-            g.n = std::min(64, ft.s - tj);
-            g.k = ft.s - tj;
-            g.kg0 = tj;
-            g.ng0 = tj;
-            g.flags = GF_BETA0 | GF_D_DIV | GF_B_NN | GF_B_UNIT_LOWER_NN;
-            gtasks.push_back(g);
-          }
+        }
+      for (int tj = 0; tj < ft.s; tj += TT)
+        for (int ti = 0; ti < ft.u; ti += TT) {
+          GemmTask<T> g{};
+          g.C = ft.G + (int64_t)tj * ld + ft.s + ti;
+          g.ldc = ld;
+          g.A = ft.Z + (int64_t)tj * ft.u + ti;   // A(i, k) = Z[ti + i, tj + k]
+          g.lda = ft.u;
+          g.d = ft.G + (int64_t)tj * (ld + 1);
+          g.ldd = ld + 1;
+          g.B = ft.G + (int64_t)tj * ld + tj;     // B(n, k) = Linv[tj + k, tj + n]
+          g.ldb = ld;
+          g.m = std::min(TT, ft.u - ti);
+          g.n = std::min(TT, ft.s - tj);
+          g.k = ft.s - tj;
+          g.kg0 = tj;
+          g.ng0 = tj;
+          g.flags = GF_BETA0 | GF_D_DIV | GF_B_NN | GF_B_UNIT_LOWER_NN;
+          gtasks.push_back(g);
+        }
+    };
+    // Z = F_BL inv(L_TL)^T (= F_BL L^{-T}), then F_BR -= Z D^{-1} Z^T (lower) and M_BL = Z D^{-1} inv(L_TL)
+    for (int phase = 0; phase < 2; ++phase)
+      for (int kind = 0; kind < 2; ++kind) {   // 0: CUDA-core tiles, 1: tensor-core tiles
+        const int64_t g0 = (int64_t)gtasks.size();
+        for (int f = 0; f < nf; ++f) {
+          const auto& ft = fronts[f0 + f];
+          if (ft.u == 0 || use_tc(ft) != (kind == 1)) continue;
+          const int TT = kind ? tc_gemm_tile() : 64;
+          if (phase == 0) emit_z(ft, TT);
+          else emit_schur_m(ft, TT);
+        }
+        if ((int64_t)gtasks.size() == g0) continue;
+        Launch lg{kind ? TCGEMM : GEMM, f0, g0, (int)(gtasks.size() - g0), -1};
+        gemm_work(g0, lg.flops, lg.bytes);
+        launches.push_back(lg);
       }
-      Launch lg{GEMM, f0, g0, (int)(gtasks.size() - g0), -1};
-      gemm_work(g0, lg.flops, lg.bytes);
-      launches.push_back(lg);
-    }
   }
 
+  X->stats.host("plan_tasks", ms_since(tp));
+  tp = std::chrono::steady_clock::now();
   DevBuf d_fronts, d_ctasks, d_dlist, d_gtasks;
   upload(d_fronts, fronts);
   upload(d_ctasks, ctasks);
@@ -585,9 +617,12 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
   const ColTask* CT = d_ctasks.as<ColTask>();
   const int* DL = d_dlist.as<int>();
   const GemmTask<T>* GT = d_gtasks.as<GemmTask<T>>();
+  X->stats.host("upload_tasks", ms_since(tp));
+  tp = std::chrono::steady_clock::now();
   int* status = X->d_status.as<int>();
   PSP_CK(cudaMemsetAsync(status, 0, 4 * sizeof(int), st));
-  static const char* names[] = {"k_assemble", "k_diag_ldlt", "k_panel_right", "k_panel_left", "k_gemm", "k_copy_linv"};
+  static const char* names[] = {"k_assemble", "k_diag_ldlt", "k_panel_right", "k_panel_left", "k_gemm", "k_copy_linv",
+                                "k_tc_gemm"};
   for (const auto& l : launches) {
     if (l.count <= 0) continue;
     X->stats.run(names[l.kind], st, 1, l.flops, l.bytes, [&] {
@@ -601,13 +636,20 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
         case PLEFT: launch_panel_left<T>(F + l.front_off, CT + l.off, l.count, l.kb, st); break;
         case GEMM: launch_gemm<T>(GT + l.off, l.count, st); break;
         case COPY: launch_copy_linv<T>(F + l.front_off, CT + l.off, l.count, st); break;
+        case TCGEMM:
+          if constexpr (std::is_same<T, float2>::value) launch_tc_gemm(GT + l.off, l.count, status, st);
+          break;
       }
-    });
+    }, true);
   }
   PSP_CK(cudaGetLastError());
+  X->stats.host("enqueue_setup", ms_since(tp));
+  tp = std::chrono::steady_clock::now();
   PSP_CK(cudaStreamSynchronize(st));
+  X->stats.host("wait_setup", ms_since(tp));
   int hs[4];
   PSP_CK(cudaMemcpy(hs, status, sizeof(hs), cudaMemcpyDeviceToHost));
+  if (hs[1] != 0) throw Error{PSP_ERR_TIMEOUT, "a tensor-core GEMM gave up waiting for its MMAs"};
   if (hs[0] != 0) {
     X->zero_pivot_front = hs[0] - 1;
     throw Error{PSP_ERR_ZERO_PIVOT, "zero pivot in front " + std::to_string(hs[0] - 1)};
@@ -653,6 +695,70 @@ static void plan_solve(psp_ctx_s* X) {
     }
   }
   upload(X->d_stasks, tasks);
+
+  // persistent sweep: panel solves in Alg. 1.5 order and one task queue in topological order
+  std::vector<SweepStep> steps;
+  for (int i = 0; i < X->m; ++i) steps.push_back({i, 0});
+  for (int i = X->m - 2; i >= 0; --i) steps.push_back({i, 1});
+  // per shape: tasks per front, up and down
+  std::vector<int> front_base(X->shapes.size() + 1, 0), ntask_up, ntask_down;
+  size_t per_rhs = 0;
+  std::vector<double> shape_entries(X->shapes.size(), 0.0), shape_vec(X->shapes.size(), 0.0);
+  std::vector<int> shape_tasks(X->shapes.size(), 0);
+  for (size_t si = 0; si < X->shapes.size(); ++si) {
+    const Shape& sh = X->shapes[si];
+    front_base[si] = (int)ntask_up.size();
+    ntask_up.resize(ntask_up.size() + sh.nsn, 0);
+    ntask_down.resize(ntask_down.size() + sh.nsn, 0);
+    for (const auto& P : X->splan[si]) {
+      for (int t = 0; t < P.nfwd; ++t) ntask_up[front_base[si] + tasks[P.fwd_off + t].sn]++;
+      for (int t = 0; t < P.nbwd; ++t) ntask_down[front_base[si] + tasks[P.bwd_off + t].sn]++;
+      per_rhs = std::max(per_rhs, (size_t)std::max(P.smax + 256, P.ldmax));
+      shape_entries[si] += 2 * P.entries;
+      shape_vec[si] += 2 * P.vec;
+      shape_tasks[si] += P.nfwd + P.nbwd;
+    }
+  }
+  front_base[X->shapes.size()] = (int)ntask_up.size();
+  std::vector<QueueEntry> queue;
+  std::vector<int> step_front(steps.size() + 1, 0), step_tasks(steps.size(), 0);
+  X->sweep_entries = 0;
+  X->sweep_vec = 0;
+  for (size_t k = 0; k < steps.size(); ++k) {
+    const int si = X->shape_of[steps[k].panel];
+    step_front[k + 1] = step_front[k] + X->shapes[si].nsn;
+    step_tasks[k] = shape_tasks[si];
+    X->sweep_entries += shape_entries[si];
+    X->sweep_vec += shape_vec[si];
+    const auto& plan = X->splan[si];
+    for (size_t lv = 0; lv < plan.size(); ++lv)
+      for (int t = 0; t < plan[lv].nfwd; ++t)
+        queue.push_back({(int)k, (int)(plan[lv].fwd_off + t), 0, (short)plan[lv].R});
+    for (int lv = (int)plan.size() - 1; lv >= 0; --lv)
+      for (int t = 0; t < plan[lv].nbwd; ++t) queue.push_back({(int)k, (int)(plan[lv].bwd_off + t), 1, 0});
+  }
+  X->sweep_rhs_bytes = per_rhs;
+  X->sweep_nsteps = (int)steps.size();
+  X->sweep_nqueue = (int)queue.size();
+  upload(X->d_sweep_steps, steps);
+  upload(X->d_sweep_queue, queue);
+  // metadata: front_base | ntask_up | ntask_down | step_front | step_tasks
+  std::vector<int> meta;
+  meta.insert(meta.end(), front_base.begin(), front_base.end());
+  const int64_t o_up = (int64_t)meta.size();
+  meta.insert(meta.end(), ntask_up.begin(), ntask_up.end());
+  X->meta_ntask_down = (int64_t)meta.size();
+  meta.insert(meta.end(), ntask_down.begin(), ntask_down.end());
+  X->meta_step_front = (int64_t)meta.size();
+  meta.insert(meta.end(), step_front.begin(), step_front.end());
+  X->meta_step_tasks = (int64_t)meta.size();
+  meta.insert(meta.end(), step_tasks.begin(), step_tasks.end());
+  X->meta_front_base = o_up;
+  upload(X->d_sweep_meta, meta);
+  // counters zeroed before every sweep: head | status[4] | step_done[nsteps] | done_up | done_down
+  X->sweep_sync_words = 1 + 4 + steps.size() + 2 * (size_t)step_front[steps.size()];
+  X->d_sweep_sync.alloc(X->sweep_sync_words * 4);
+  PSP_CK(cudaMemset(X->d_sweep_sync.p, 0, X->sweep_sync_words * 4));
 }
 
 template <typename T>
@@ -710,8 +816,46 @@ static void apply_core(psp_ctx_s* X, double2* u, int nrhs, T* xf, T* xb, T* upd,
     }
   };
   try {
-    for (int i = 0; i < X->m; ++i) runT(i, 0);          // u_i := T_i (u_i - J_{i,i-1} u_{i-1})
-    for (int i = X->m - 2; i >= 0; --i) runT(i, 1);     // u_i -= T_i J_{i+1,i}^T u_{i+1}
+    // one cooperative launch for the whole sweep when the device allows it
+    SweepArgs<T> sa{};
+    sa.cx = cx;
+    sa.nshapes = (int)X->shapes.size();
+    sa.nsteps = X->sweep_nsteps;
+    sa.npanels = X->m;
+    sa.steps = X->d_sweep_steps.as<SweepStep>();
+    sa.panels = X->d_sweep_panels.as<PanelSweep>();
+    sa.shapes = X->d_shapes.as<ShapeDev>();
+    sa.tasks = tasks;
+    sa.factor = X->d_factor.as<T>();
+    sa.queue = X->d_sweep_queue.as<QueueEntry>();
+    sa.nqueue = X->sweep_nqueue;
+    const int* meta = X->d_sweep_meta.as<int>();
+    sa.front_base = meta;
+    sa.ntask_up = meta + X->meta_front_base;
+    sa.ntask_down = meta + X->meta_ntask_down;
+    sa.step_front_base = meta + X->meta_step_front;
+    sa.step_tasks = meta + X->meta_step_tasks;
+    unsigned* sync = X->d_sweep_sync.as<unsigned>();
+    const int64_t nfront_steps = ((int64_t)X->sweep_sync_words - 5 - X->sweep_nsteps) / 2;
+    sa.queue_head = sync;
+    sa.status = reinterpret_cast<int*>(sync + 1);
+    sa.step_done = sync + 5;
+    sa.done_up = sync + 5 + X->sweep_nsteps;
+    sa.done_down = sa.done_up + nfront_steps;
+    int rc = -1;
+    if (X->persistent_sweep && X->shapes.size() <= 4 && X->sweep_nsteps <= 512 && X->m <= 256) {
+      // queue head and completion counters start at zero; status[2] is cleared too
+      PSP_CK(cudaMemsetAsync(sync, 0, X->sweep_sync_words * 4, st));
+      const double es = sizeof(T);
+      X->stats.run("k_sweep", st, 1, 8.0 * X->sweep_entries * nrhs,
+                   X->sweep_entries * es + X->sweep_vec * es * nrhs,
+                   [&] { rc = launch_sweep<T>(sa, X->sweep_rhs_bytes * sizeof(T), st); });
+      if (rc > 0) throw Error{PSP_ERR_CUDA, std::string("sweep launch: ") + cudaGetErrorString((cudaError_t)rc)};
+    }
+    if (rc != 0) {
+      for (int i = 0; i < X->m; ++i) runT(i, 0);          // u_i := T_i (u_i - J_{i,i-1} u_{i-1})
+      for (int i = X->m - 2; i >= 0; --i) runT(i, 1);     // u_i -= T_i J_{i+1,i}^T u_{i+1}
+    }
   } catch (...) {
     X->stats.timing = was_timing;
     throw;
@@ -769,6 +913,7 @@ static void apply_dispatch(psp_ctx_s* X, double2* u, int nrhs, cudaStream_t st) 
 // setup
 // ---------------------------------------------------------------------------
 static void setup_impl(psp_ctx_s* X, const double* c, cudaStream_t st) {
+  auto t_start = std::chrono::steady_clock::now();
   const int nx = X->nx, ny = X->ny, nz = X->nz;
   X->N = (int64_t)nx * ny * nz;
   // wave speed (host or device input)
@@ -914,6 +1059,7 @@ static void setup_impl(psp_ctx_s* X, const double* c, cudaStream_t st) {
     size_t o_pl = put(sh.pull.data(), sh.pull.size() * 4);
     size_t o_go = put(sh.g_off.data(), sh.g_off.size() * 8);
     size_t o_uo = put(sh.upd_off.data(), sh.upd_off.size() * 8);
+    size_t o_par = put(sh.parent.data(), sh.parent.size() * 4);
     DevBuf b;
     b.alloc(blob.size());
     PSP_CK(cudaMemcpy(b.p, blob.data(), blob.size(), cudaMemcpyHostToDevice));
@@ -934,6 +1080,7 @@ static void setup_impl(psp_ctx_s* X, const double* c, cudaStream_t st) {
     d.pull = (const int32_t*)(base + o_pl);
     d.g_off = (const int64_t*)(base + o_go);
     d.upd_off = (const int64_t*)(base + o_uo);
+    d.parent = (const int32_t*)(base + o_par);
     X->shdev.push_back(d);
     X->shape_bufs.push_back(std::move(b));
   }
@@ -955,9 +1102,27 @@ static void setup_impl(psp_ctx_s* X, const double* c, cudaStream_t st) {
   X->nfronts = nf;
   X->factor_elems = fe;
   X->elem_bytes = X->prec == PSP_PREC_C64 ? 8 : 16;
+  {
+    std::vector<PanelSweep> ps(X->m);
+    for (int i = 0; i < X->m; ++i) {
+      ps[i].gbase = X->panel_fbase[i];
+      ps[i].shape = X->shape_of[i];
+      ps[i].z0 = X->z0[i];
+      ps[i].z1 = X->z1[i];
+      ps[i].lead = X->lead[i];
+      ps[i].has_prev = i > 0;
+      ps[i].has_next = i < X->m - 1;
+    }
+    upload(X->d_sweep_panels, ps);
+  }
+  X->stats.host("symbolic_tables", ms_since(t_start));
+  auto ta = std::chrono::steady_clock::now();
   X->d_factor.alloc((size_t)fe * X->elem_bytes);
   X->d_status.alloc(4 * sizeof(int));
+  X->stats.host("alloc_factors", ms_since(ta));
+  ta = std::chrono::steady_clock::now();
   plan_solve(X);
+  X->stats.host("plan_solve", ms_since(ta));
   if (X->prec == PSP_PREC_C64) factor_all<float2>(X, st);
   else factor_all<double2>(X, st);
 }
@@ -1059,7 +1224,10 @@ static void solve_impl(psp_ctx_s* X, const double2* f, double2* x, int nrhs, dou
       small("k_arnoldi_step", [&] { launch_arnoldi_step(Ls, j, h1, h2, nrm, st); });
       axpby(w, V + (int64_t)(j + 1) * ldv_vec, scl, 0);
       PSP_CK(cudaMemcpyAsync(hres.data(), resid, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+      int sweep_status = 0;
+      PSP_CK(cudaMemcpyAsync(&sweep_status, X->d_sweep_sync.as<unsigned>() + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
       PSP_CK(cudaStreamSynchronize(st));
+      if (sweep_status != 0) throw Error{PSP_ERR_TIMEOUT, "a dependency wait of the sweep gave up"};
       ++total_it;
       bool all_done = true;
       for (int r = 0; r < nrhs; ++r) {
@@ -1164,6 +1332,7 @@ psp_status psp_setup(const psp_grid* g, const double* c, double omega, int pml_g
   psp_options o;
   psp_default_options(&o);
   if (opt) o = *opt;
+  if (o.collect_stats < 0 || o.collect_stats > 2) return fail(PSP_ERR_ARG, "bad collect_stats");
   if (o.leaf_size < 1 || o.pml_faces < 0 || o.pml_faces > 63 || (o.precision != PSP_PREC_C128 && o.precision != PSP_PREC_C64) ||
       (o.aux_mode != PSP_AUX_MOVING_PML && o.aux_mode != PSP_AUX_EXACT) || !(o.alpha >= 0) || !(o.pml_C >= 0))
     return fail(PSP_ERR_ARG, "bad options");
@@ -1179,6 +1348,8 @@ psp_status psp_setup(const psp_grid* g, const double* c, double omega, int pml_g
   X->pad = o.pad_depth < 0 ? pml_gamma : o.pad_depth;
   X->leaf = o.leaf_size; X->prec = o.precision; X->faces = o.pml_faces; X->aux_mode = o.aux_mode;
   X->stats.timing = o.collect_stats != 0;
+  X->stats.mode = o.collect_stats;
+  X->use_tc = o.tensor_cores != 0;
   *out = X;
   PSP_TRY
   setup_impl(X, c, (cudaStream_t)stream);

@@ -70,6 +70,7 @@ struct ShapeDev {
   const int32_t* pull;
   const int64_t* g_off;
   const int64_t* upd_off;
+  const int32_t* parent;
 };
 
 // 7-point operator on a box: -sum_j d_j(a_j d_j u) - k2num / c^2 * s1 s2 s3 u (Eq. (1.1)/(1.5),
@@ -155,6 +156,8 @@ template <typename T>
 void launch_panel_left(const FrontTask<T>* fronts, const ColTask* tasks, int ntasks, int kb, cudaStream_t st);
 template <typename T>
 void launch_gemm(const GemmTask<T>* tasks, int ntasks, cudaStream_t st);
+void launch_tc_gemm(const GemmTask<float2>* tasks, int ntasks, int* status, cudaStream_t st);
+int tc_gemm_tile();
 template <typename T>
 void launch_copy_linv(const FrontTask<T>* fronts, const ColTask* tasks, int ntasks, cudaStream_t st);
 
@@ -186,6 +189,52 @@ template <typename T>
 void launch_solve_fwd(const SolveTask* tasks, int ntasks, const SolveCtx<T>& cx, int R, int smax, cudaStream_t st);
 template <typename T>
 void launch_solve_bwd(const SolveTask* tasks, int ntasks, const SolveCtx<T>& cx, int ldmax, cudaStream_t st);
+
+// ---- the whole sweep in one cooperative launch ----
+struct SweepStep {      // one panel solve of Alg. 1.5, in order
+  int panel, mode;      // mode 0: forward sweep (assign), 1: backward sweep (subtract)
+};
+struct PanelSweep {
+  int64_t gbase;        // factor slab offset (elements)
+  int shape, z0, z1, lead, has_prev, has_next;
+};
+struct LevelSweep {
+  int64_t fwd_off, bwd_off;
+  int nfwd, nbwd, R, pad_;
+};
+// one entry of the sweep's task queue (topological order: panel solves in Alg. 1.5 order; inside
+// one, the up-the-tree tasks level by level, then the down-the-tree tasks from the root)
+struct QueueEntry {
+  int step;                     // panel solve index
+  int task;                     // index into the shape's SolveTask list
+  short dir;                    // 0 up the tree, 1 down the tree
+  short R;                      // rows per up-the-tree task
+};
+template <typename T>
+struct SweepArgs {
+  SolveCtx<T> cx;               // fields common to every panel (vectors, sizes, coupling tables)
+  int nshapes, nsteps, npanels; // sizes of the three tables below (kept in shared memory)
+  const SweepStep* steps;
+  const PanelSweep* panels;
+  const ShapeDev* shapes;
+  const SolveTask* tasks;
+  const T* factor;
+  const QueueEntry* queue;
+  int nqueue;
+  const int* ntask_up;          // per shape-front: number of up / down tasks (shape offset: front_base)
+  const int* ntask_down;
+  const int* front_base;        // per shape: offset of its fronts in ntask_up / ntask_down
+  const int* step_front_base;   // per step: offset of its fronts in the done counters
+  const int* step_tasks;        // per step: number of tasks
+  unsigned* queue_head;         // dequeue counter (zeroed per sweep)
+  unsigned* done_up;            // per step-front completed up tasks (zeroed per sweep)
+  unsigned* done_down;
+  unsigned* step_done;          // per step completed tasks (zeroed per sweep)
+  int* status;                  // status[2] set when a wait gave up
+};
+// returns 0 on success, -1 when a cooperative launch is not possible, else a cudaError_t
+template <typename T>
+int launch_sweep(const SweepArgs<T>& args, size_t per_rhs_bytes, cudaStream_t st);
 
 // ---- GMRES helpers (complex128) ----
 // partial[b * (nvec * nrhs) + i * nrhs + r] = sum over block b's slice of conj(V_i[r]) w[r]

@@ -31,7 +31,8 @@ class Grid(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("pml_C", ctypes.c_double), ("alpha", ctypes.c_double), ("pad_depth", ctypes.c_int),
                 ("leaf_size", ctypes.c_int), ("precision", ctypes.c_int), ("pml_faces", ctypes.c_int),
-                ("aux_mode", ctypes.c_int), ("collect_stats", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
+                ("aux_mode", ctypes.c_int), ("collect_stats", ctypes.c_int), ("tensor_cores", ctypes.c_int),
+                ("reserved", ctypes.c_int * 7)]
 
 
 class KernelStat(ctypes.Structure):
@@ -135,7 +136,7 @@ class SweepingPreconditioner:
     """Handle over psp_setup / psp_apply / psp_solve (Algs. 1.4, 1.5 and GMRES(k) of §2.4)."""
 
     def __init__(self, c, h, omega, gamma, panel_depth, pad=None, leaf=64, pml_C=4.0, alpha=2 * math.pi,
-                 precision="c128", faces=63, mode="moving", stream=None, collect_stats=False):
+                 precision="c128", faces=63, mode="moving", stream=None, collect_stats=0, tensor_cores=True):
         nz, ny, nx = c.shape
         self.nx, self.ny, self.nz = nx, ny, nz
         self.N = nx * ny * nz
@@ -149,7 +150,8 @@ class SweepingPreconditioner:
         o.precision = {"c128": PREC_C128, "c64": PREC_C64}[precision]
         o.pml_faces = int(faces)
         o.aux_mode = {"moving": AUX_MOVING_PML, "exact": AUX_EXACT}[mode]
-        o.collect_stats = 1 if collect_stats else 0
+        o.collect_stats = int(collect_stats)
+        o.tensor_cores = 1 if tensor_cores else 0
         cp, n = _ptr_and_len(c, complex_=False)
         if n != self.N:
             raise ValueError("c has the wrong size")

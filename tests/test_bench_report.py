@@ -1,0 +1,54 @@
+"""bench.py's report building (no GPU): roofline, kernel shares and detail from psp_stats records."""
+import importlib.util
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def rec(launches, ms, flops, bytes_):
+    return {"launches": launches, "total_ms": ms, "flops": flops, "bytes": bytes_}
+
+
+def test_summarize_picks_dominant_kernel_and_computes_rates(bench):
+    timed = [{"k_gemm": rec(100, 1000.0, 1e12, 1e9), "k_assemble": rec(10, 50.0, 1e9, 5e10),
+              "k_sweep": rec(19, 0.0, 5e11, 3e11), "host:plan_tasks": rec(0, 70.0, 0, 0)}] * 2
+    full = {"k_gemm": rec(100, 1000.0, 1e12, 1e9), "k_assemble": rec(10, 50.0, 1e9, 5e10),
+            "k_sweep": rec(19, 400.0, 5e11, 3e11), "host:plan_tasks": rec(0, 70.0, 0, 0)}
+    infos = [{"iterations": 18, "relres_max": 6e-6, "solve_ms": 900.0, "applies": 19}] * 2
+    roof, detail, launches = bench.summarize(timed, full, infos, 16e9, 2)
+    assert roof["kernel"] == "k_gemm"
+    assert roof["achieved"] == pytest.approx(1.0)              # 2e12 flop / 2 s
+    assert roof["frac"] == pytest.approx(1.0 / bench.FP64_PEAK_TFLOPS)
+    assert roof["kernel_share"] == pytest.approx(1000.0 / 1450.0)
+    assert launches == 2 * 129
+    assert detail["apply_ms"] == pytest.approx(400.0 / 19)
+    assert detail["sweep_gbs"] == pytest.approx(3e11 / 0.4 / 1e9)
+    assert detail["host_setup_ms"] == {"plan_tasks": 70.0}
+    assert "host:plan_tasks" not in detail["kernels"]
+    assert detail["setup_kernel_ms"] == pytest.approx(1050.0)
+
+
+def test_summarize_falls_back_when_dominant_kernel_untimed(bench):
+    timed = [{"k_gemm": rec(100, 10.0, 1e10, 0), "k_sweep": rec(19, 0.0, 5e11, 3e11)}]
+    full = {"k_gemm": rec(100, 10.0, 1e10, 0), "k_sweep": rec(19, 400.0, 5e11, 3e11)}
+    infos = [{"iterations": 18, "relres_max": 6e-6, "solve_ms": 900.0, "applies": 19}]
+    roof, _, _ = bench.summarize(timed, full, infos, 1, 1)
+    assert roof["kernel"] == "k_gemm" and roof["kernel_share"] == pytest.approx(10 / 410)
+
+
+def test_gpu_main_uses_only_defined_names(bench):
+    import dis
+    code = bench.gpu_main.__code__
+    names = {ins.argval for ins in dis.get_instructions(code) if ins.opname in ("LOAD_GLOBAL",)}
+    for n in names:
+        assert hasattr(bench, n) or n in dir(__builtins__) or n in __builtins__, n

@@ -191,3 +191,31 @@ def test_single_panel_and_zero_pivot_free_small_grid():
     out = np.zeros_like(x)
     P.apply(np.ascontiguousarray((J @ x.T).T), out)
     assert rel(out, x) < 1e-10
+
+
+@pytest.mark.parametrize("case", CASES[1:], ids=IDS[1:])
+def test_tensor_core_fronts_complex64(case):
+    # complex64 fronts with the long contractions on tcgen05 (split-TF32, 3 real products) against
+    # the same path on CUDA cores and against the complex128 oracle
+    c = torch.from_numpy(case.c).cuda()
+    kw = dict(pad=case.pad, leaf=case.leaf, pml_C=case.C, alpha=case.alpha, precision="c64", faces=case.faces)
+    Ptc = psp.SweepingPreconditioner(c, case.h, case.omega, case.gamma, case.depth, tensor_cores=True, **kw)
+    Pcc = psp.SweepingPreconditioner(c, case.h, case.omega, case.gamma, case.depth, tensor_cores=False, **kw)
+    O = oracle_for(case)
+    worst_tc, worst_cc, worst_diff = 0.0, 0.0, 0.0
+    big = False   # fronts with s, u >= 96 take the 128 x 128 tensor-core tiles
+    for i in range(O.m):
+        for f, fr in enumerate(O.fronts[i]):
+            Gt, s, u = Ptc.export_front(i, f)
+            Gc, _, _ = Pcc.export_front(i, f)
+            big = big or (s >= 96 and u >= 96)
+            if u == 0:
+                continue
+            Linv = sla.solve_triangular(fr.L_TL, np.eye(s), lower=True, unit_diagonal=True)
+            exp = fr.L_BL @ Linv
+            worst_tc = max(worst_tc, rel(Gt[s:], exp))
+            worst_cc = max(worst_cc, rel(Gc[s:], exp))
+            worst_diff = max(worst_diff, rel(Gt[s:], Gc[s:]))
+    assert worst_cc < 1e-3 and worst_tc < 1e-3 and worst_diff < 1e-3, (worst_tc, worst_cc, worst_diff)
+    st = Ptc.stats()
+    assert (st.get("k_tc_gemm", {}).get("launches", 0) > 0) == big
