@@ -227,77 +227,36 @@ struct psp_ctx_s {
   int zero_pivot_front = -1;
   bool use_tc = true;
   bool persistent_sweep = true;
+  int64_t upd_arena_elems = 0;
   Stats stats;
 };
 
 namespace psp {
 
-// ---------------------------------------------------------------------------
-// first-fit interval allocator used to plan the update-matrix arena
-// ---------------------------------------------------------------------------
-struct ArenaPlanner {
-  std::map<int64_t, int64_t> free_;  // offset -> size
-  int64_t top = 0, peak = 0;
-  int64_t alloc(int64_t n) {
-    n = (n + 15) / 16 * 16;
-    for (auto it = free_.begin(); it != free_.end(); ++it) {
-      if (it->second >= n) {
-        int64_t off = it->first;
-        int64_t rem = it->second - n;
-        free_.erase(it);
-        if (rem > 0) free_[off + n] = rem;
-        return off;
-      }
-    }
-    int64_t off = top;
-    top += n;
-    peak = std::max(peak, top);
-    return off;
-  }
-  void release(int64_t off, int64_t n) {
-    n = (n + 15) / 16 * 16;
-    auto it = free_.emplace(off, n).first;
-    auto nx = std::next(it);
-    if (nx != free_.end() && it->first + it->second == nx->first) {
-      it->second += nx->second;
-      free_.erase(nx);
-    }
-    if (it != free_.begin()) {
-      auto pv = std::prev(it);
-      if (pv->first + pv->second == it->first) {
-        pv->second += it->second;
-        free_.erase(it);
-        it = pv;
-      }
-    }
-    if (it->first + it->second == top) {
-      top = it->first;
-      free_.erase(it);
-    }
-  }
-};
-
 static int64_t pad16(int64_t n) { return (n + 15) / 16 * 16; }
+
+// sum_{j=0}^{n-1} clamp(a + j, 0, k)
+static double sum_clamped(int64_t a, int64_t n, int64_t k) {
+  if (n <= 0 || k <= 0) return 0.0;
+  const int64_t j0 = std::clamp<int64_t>(1 - a, 0, n);   // first j with a + j >= 1
+  const int64_t j1 = std::clamp<int64_t>(k - a, j0, n);  // first j with a + j >= k
+  return (double)(j1 - j0) * a + 0.5 * ((double)j1 * (j1 - 1) - (double)j0 * (j0 - 1)) + (double)(n - j1) * k;
+}
 
 // useful complex multiply-adds of a GEMM task: written C entries times structurally non-zero k
 template <typename T>
 static double gemm_cmacs(const GemmTask<T>& g) {
-  double total = 0;
-  for (int j = 0; j < g.n; ++j) {
-    const double rows = (g.flags & GF_C_LOWER) ? std::max(0, g.m - j) : g.m;
-    const int ng = g.ng0 + j;
-    double ks = g.k;
-    if (g.flags & GF_B_UNIT_LOWER_NT) ks = std::clamp(ng - g.kg0 + 1, 0, g.k);
-    else if (g.flags & GF_B_UNIT_LOWER_NN) ks = std::clamp(g.kg0 + g.k - ng, 0, g.k);
-    total += rows * ks;
+  if (g.flags & GF_C_LOWER) {   // lower tiles carry no triangular operand
+    double total = 0;
+    const int64_t nn = std::min(g.n, g.m);
+    total = (double)g.k * ((double)nn * g.m - 0.5 * (double)nn * (nn - 1));
+    return total;
   }
-  return total;
+  if (g.flags & GF_B_UNIT_LOWER_NT) return (double)g.m * sum_clamped((int64_t)g.ng0 - g.kg0 + 1, g.n, g.k);
+  if (g.flags & GF_B_UNIT_LOWER_NN) return (double)g.m * sum_clamped((int64_t)g.kg0 + g.k - g.ng0 - (g.n - 1), g.n, g.k);
+  return (double)g.m * g.n * g.k;
 }
 
-// ---------------------------------------------------------------------------
-// Plan and run the factorisation of all panels, level by level (all panels' fronts of one
-// tree level in each launch: the panels are independent, §2).
-// ---------------------------------------------------------------------------
 static double ms_since(std::chrono::steady_clock::time_point t0) {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
@@ -311,8 +270,9 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
   for (auto& sh : X->shapes) L = std::max(L, sh.nlevels);
 
   // --- memory plan ---
+  // Update matrices of one tree level share a slab; a slab is released after the highest level
+  // that consumes (extend-adds) one of its blocks.  Slabs are placed first-fit on one arena.
   std::vector<int64_t> uoff(X->nfronts, -1);
-  ArenaPlanner ua;
   std::vector<std::vector<std::pair<int, int>>> lev_fronts(L);  // (panel, sn)
   for (int lv = 0; lv < L; ++lv)
     for (int p = 0; p < X->m; ++p) {
@@ -320,28 +280,51 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
       if (lv < sh.nlevels)
         for (int sn : sh.level_sns[lv]) lev_fronts[lv].push_back({p, sn});
     }
+  std::vector<int64_t> slab_size(L, 0), slab_off(L, -1);
+  std::vector<int> slab_last(L, -1);
   int64_t temp_max = 0;
   for (int lv = 0; lv < L; ++lv) {
     int64_t tsum = 0;
     for (auto [p, sn] : lev_fronts[lv]) {
       const Shape& sh = X->shapes[X->shape_of[p]];
       const int64_t s = sh.s[sn], u = sh.u[sn];
-      if (u > 0) uoff[X->sn_base[p] + sn] = ua.alloc(u * u);
+      if (u > 0) {
+        uoff[X->sn_base[p] + sn] = slab_size[lv];   // relative to the slab for now
+        slab_size[lv] += pad16(u * u);
+        slab_last[lv] = std::max(slab_last[lv], (int)sh.height[sh.parent[sn]]);
+      }
       tsum += pad16(s * s) + pad16(u * s);
     }
     temp_max = std::max(temp_max, tsum);
-    for (auto [p, sn] : lev_fronts[lv]) {
-      const Shape& sh = X->shapes[X->shape_of[p]];
-      for (int c = sh.child_ptr[sn]; c < sh.child_ptr[sn + 1]; ++c) {
-        const int ch = sh.child_idx[c];
-        ua.release(uoff[X->sn_base[p] + ch], (int64_t)sh.u[ch] * sh.u[ch]);
+  }
+  {
+    // a slab is live from its own level through the last level that extend-adds from it
+    int64_t peak = 0;
+    for (int lv = 0; lv < L; ++lv) {
+      if (slab_size[lv] == 0) continue;
+      std::vector<std::pair<int64_t, int64_t>> live;   // (offset, size), sorted by offset
+      for (int q = 0; q < lv; ++q)
+        if (slab_size[q] > 0 && slab_last[q] >= lv) live.push_back({slab_off[q], slab_size[q]});
+      std::sort(live.begin(), live.end());
+      int64_t pos = 0;
+      for (const auto& sl : live) {
+        if (sl.first - pos >= slab_size[lv]) break;
+        pos = std::max(pos, sl.first + sl.second);
       }
+      slab_off[lv] = pos;
+      peak = std::max(peak, pos + slab_size[lv]);
     }
+    for (int lv = 0; lv < L; ++lv)
+      for (auto [p, sn] : lev_fronts[lv]) {
+        int64_t& o = uoff[X->sn_base[p] + sn];
+        if (o >= 0) o += slab_off[lv];
+      }
+    X->upd_arena_elems = peak;
   }
   X->stats.host("plan_memory", ms_since(tp));
   tp = std::chrono::steady_clock::now();
   DevBuf d_upd, d_temp;
-  d_upd.alloc((size_t)std::max<int64_t>(ua.peak, 16) * sizeof(T));
+  d_upd.alloc((size_t)std::max<int64_t>(X->upd_arena_elems, 16) * sizeof(T));
   d_temp.alloc((size_t)std::max<int64_t>(temp_max, 16) * sizeof(T));
   X->stats.host("alloc_work", ms_since(tp));
   tp = std::chrono::steady_clock::now();
