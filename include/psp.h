@@ -80,7 +80,13 @@ typedef struct {
                          2 the setup kernels only (a few hundred launches per setup) */
   int tensor_cores;   /* complex64 path: 1 (default) runs the Schur update and the selective-inversion
                          multiplies on tcgen05 tensor cores, 0 keeps them on CUDA cores */
-  int reserved[7];
+  int tc_min_dim;     /* complex64 path: fronts with s >= tc_min_dim and u >= tc_min_dim take the tensor
+                         cores, the others CUDA cores; <= 0 selects the default (64) */
+  int sweep_level_tasks; /* sweep schedule: tasks a tree level is split into at least (row / column
+                            blocks of 8..64); <= 0 selects the default (608 complex64, 304 complex128) */
+  int sweep_ctas_per_sm; /* sweep schedule: resident CTAs per SM of the persistent sweep (capped by
+                            occupancy); <= 0 selects the default (8) */
+  int reserved[4];
 } psp_options;
 
 /* Per-solve report filled by psp_solve (host struct). */

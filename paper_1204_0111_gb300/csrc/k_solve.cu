@@ -249,9 +249,10 @@ __device__ __forceinline__ bool wait_count(const unsigned* p, unsigned target, i
 }
 
 constexpr int kMaxSweepShapes = 4, kMaxSweepSteps = 512, kMaxSweepPanels = 256;
+constexpr int kSweepThreads = 256;
 
 template <typename T, int RG>
-__global__ void __launch_bounds__(256) k_sweep(SweepArgs<T> a) {
+__global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_idx, s_next, s_ok;
   __shared__ ShapeDev s_shape[kMaxSweepShapes];
@@ -318,7 +319,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs<T> a) {
 }
 
 template <typename T, int RG>
-static int sweep_rg(const SweepArgs<T>& args, size_t per_rhs_bytes, cudaStream_t st) {
+static int sweep_rg(const SweepArgs<T>& args, size_t per_rhs_bytes, int max_per_sm, cudaStream_t st) {
   const size_t smem = per_rhs_bytes * RG;
   if (cudaFuncSetAttribute(k_sweep<T, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
@@ -329,25 +330,27 @@ static int sweep_rg(const SweepArgs<T>& args, size_t per_rhs_bytes, cudaStream_t
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
   if (!coop) return -1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep<T, RG>, 256, smem) != cudaSuccess || per_sm < 1) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep<T, RG>, kSweepThreads, smem) != cudaSuccess ||
+      per_sm < 1) {
     cudaGetLastError();
     return -1;
   }
-  per_sm = per_sm > 8 ? 8 : per_sm;
+  per_sm = per_sm > max_per_sm ? max_per_sm : per_sm;
   SweepArgs<T> a = args;
   void* kargs[] = {&a};
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_sweep<T, RG>, dim3(sms * per_sm), dim3(256), kargs, smem, st);
+  cudaError_t e =
+      cudaLaunchCooperativeKernel((const void*)k_sweep<T, RG>, dim3(sms * per_sm), dim3(kSweepThreads), kargs, smem, st);
   return e == cudaSuccess ? 0 : (int)e;
 }
 
 template <typename T>
-int launch_sweep(const SweepArgs<T>& args, size_t per_rhs_bytes, cudaStream_t st) {
+int launch_sweep(const SweepArgs<T>& args, size_t per_rhs_bytes, int max_per_sm, cudaStream_t st) {
   const int rg = pick_rg<T>(args.cx.nrhs, per_rhs_bytes);
   switch (rg) {
-    case 8: return sweep_rg<T, 8>(args, per_rhs_bytes, st);
-    case 4: return sweep_rg<T, 4>(args, per_rhs_bytes, st);
-    case 2: return sweep_rg<T, 2>(args, per_rhs_bytes, st);
-    default: return sweep_rg<T, 1>(args, per_rhs_bytes, st);
+    case 8: return sweep_rg<T, 8>(args, per_rhs_bytes, max_per_sm, st);
+    case 4: return sweep_rg<T, 4>(args, per_rhs_bytes, max_per_sm, st);
+    case 2: return sweep_rg<T, 2>(args, per_rhs_bytes, max_per_sm, st);
+    default: return sweep_rg<T, 1>(args, per_rhs_bytes, max_per_sm, st);
   }
 }
 
@@ -403,7 +406,7 @@ template void launch_solve_fwd<double2>(const SolveTask*, int, const SolveCtx<do
 template void launch_solve_fwd<float2>(const SolveTask*, int, const SolveCtx<float2>&, int, int, cudaStream_t);
 template void launch_solve_bwd<double2>(const SolveTask*, int, const SolveCtx<double2>&, int, cudaStream_t);
 template void launch_solve_bwd<float2>(const SolveTask*, int, const SolveCtx<float2>&, int, cudaStream_t);
-template int launch_sweep<double2>(const SweepArgs<double2>&, size_t, cudaStream_t);
-template int launch_sweep<float2>(const SweepArgs<float2>&, size_t, cudaStream_t);
+template int launch_sweep<double2>(const SweepArgs<double2>&, size_t, int, cudaStream_t);
+template int launch_sweep<float2>(const SweepArgs<float2>&, size_t, int, cudaStream_t);
 
 }  // namespace psp

@@ -1,20 +1,23 @@
 // Tensor-core (tcgen05 / TMEM) complex64 front GEMM of the complex64 path:
-//   C (128 x 128 tile) (+)= +-A diag(d)^{+-1} B^T,
-// the Schur update F_BR -= Z D^{-1} Z^T and the two triangular multiplies of selective inversion
-// (§2.2), whose contraction depth is the full supernode size.
+//   C (128 x 128 tile) (+)= +-A B^T
+// for the Schur update F_BR -= (Z D^{-1}) Z^T and the two triangular multiplies of selective
+// inversion (§2.2), whose contraction depth is the full supernode size.
 //
 // Complex products use three real products (Gauss): T1 = Ar Br, T2 = Ai Bi,
 // T3 = (Ar + Ai)(Br + Bi), Re = T1 - T2, Im = T3 - T1 - T2.  Each real operand x is split into
 // TF32 parts x = hi + lo (hi = tf32(x), lo = tf32(x - hi)) and each real product is formed as
-// hi*hi + hi*lo + lo*hi, which keeps about 22 significant bits: nine kind::tf32 MMAs per k-step,
+// hi*hi + hi*lo + lo*hi (about 22 significant bits): nine kind::tf32 MMAs per k-step of 8,
 // accumulated in FP32 in tensor memory (3 x 128 columns).
 //
-// One CTA of 256 threads per output tile.  All threads load the operands from global memory,
-// apply the diagonal scaling and the unit-triangular masks, split them and store the twelve
-// planes in the canonical K-major no-swizzle layout (8-row x 16-byte core matrices); thread 0
-// issues the MMAs and commits them to an mbarrier per stage, so loading k-block kb+1 overlaps
-// the MMAs of k-block kb (two stages).  Every mbarrier wait is bounded; a wait that gives up
-// records an error in `status` and the CTA skips its epilogue, frees its tensor memory and exits.
+// Two kernels.  k_tc_pack splits an operand once per front into the six TF32 planes (hi/lo of
+// re, im, re+im), already laid out as the MMA reads them from shared memory (K-major, no swizzle,
+// 8-row x 16-byte core matrices): one 48 KB block per 128 rows x 16 k.  k_tc_gemm then streams the
+// A and B blocks of each k-block with bulk asynchronous copies into one of two shared-memory
+// stages (96 KB each): thread 0 produces (waits for a free stage, posts the expected bytes, issues
+// the copies), thread 32 issues the MMAs once a stage is full and commits them to the stage's
+// "empty" barrier, and all eight warps read the accumulators back for the epilogue.  Every
+// mbarrier wait is bounded; a wait that gives up records an error in status[1], and the CTA skips
+// its epilogue, frees its tensor memory and returns.
 #include <cstdint>
 
 #include "cplx.cuh"
@@ -27,9 +30,10 @@ namespace {
 constexpr int TM = 128, TN = 128, KB = 16;     // tile and k-block (two tf32 MMAs of K = 8)
 constexpr int PLANE_BYTES = TM * KB * 4;       // 8 KB: 128 rows x 16 tf32
 constexpr int NPLANE = 6;                      // hi/lo of re, im, re+im
-constexpr int STAGE_BYTES = 2 * NPLANE * PLANE_BYTES;   // A and B planes: 96 KB
+constexpr int BLOCK_BYTES = NPLANE * PLANE_BYTES;      // one packed operand block: 48 KB
+constexpr int STAGE_BYTES = 2 * BLOCK_BYTES;           // A and B blocks: 96 KB
 constexpr int NSTAGE = 2;
-constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024;  // + barriers, scaling, TMEM slot
+constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024;  // + barriers and the TMEM slot
 constexpr uint32_t LBO = 128;                  // next core matrix along K
 constexpr uint32_t SBO = 512;                  // next 8-row group (4 core matrices of K per group)
 constexpr uint32_t TMEM_COLS = 512;
@@ -40,7 +44,7 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 }
 
 // byte offset of element (row r, k) inside one plane
-__device__ __forceinline__ uint32_t plane_off(int r, int k) {
+__host__ __device__ __forceinline__ uint32_t plane_off(int r, int k) {
   return (uint32_t)((r >> 3) * SBO + (k >> 2) * LBO + (r & 7) * 16 + (k & 3) * 4);
 }
 
@@ -100,6 +104,16 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
   return false;
 }
 
+__device__ __forceinline__ void expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -110,18 +124,62 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
 
 }  // namespace
 
-__global__ void __launch_bounds__(256, 1) k_tc_gemm(const GemmTask<float2>* __restrict__ tasks, int* status) {
+// ---------------------------------------------------------------------------
+// k_tc_pack: one 48 KB block (rows r0..r0+127, k k0..k0+15) of a packed operand per CTA.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_tc_pack(const TcPackTask* __restrict__ tasks) {
+  const TcPackTask tk = tasks[blockIdx.x];
+  for (int u = threadIdx.x; u < TM * (KB / 4); u += 256) {
+    const int r = u % TM, c = u / TM;
+    const int rg = tk.r0 + r;
+    uint32_t hr[4], lr[4], hi_[4], li[4], hs[4], ls[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int k = tk.k0 + 4 * c + q;
+      float2 v = make_float2(0.f, 0.f);
+      if (rg < tk.R && k < tk.K) {
+        if (tk.mode == TC_PACK_PLAIN) {
+          v = tk.src[(int64_t)k * tk.ld + rg];
+          if (tk.d) v = cdiv(v, tk.d[(int64_t)k * tk.ldd]);
+        } else if (tk.mode == TC_PACK_UNIT_LOWER) {          // T[rg, k], unit lower
+          v = (k == rg) ? make_float2(1.f, 0.f) : (k < rg ? tk.src[(int64_t)k * tk.ld + rg] : make_float2(0.f, 0.f));
+        } else {                                             // T[k, rg], unit lower (transposed read)
+          v = (k == rg) ? make_float2(1.f, 0.f) : (k > rg ? tk.src[(int64_t)rg * tk.ld + k] : make_float2(0.f, 0.f));
+        }
+      }
+      split(v.x, hr[q], lr[q]);
+      split(v.y, hi_[q], li[q]);
+      split(v.x + v.y, hs[q], ls[q]);
+    }
+    unsigned char* dst = reinterpret_cast<unsigned char*>(tk.dst) + plane_off(r, 4 * c);
+    *reinterpret_cast<uint4*>(dst + 0 * PLANE_BYTES) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
+    *reinterpret_cast<uint4*>(dst + 1 * PLANE_BYTES) = make_uint4(lr[0], lr[1], lr[2], lr[3]);
+    *reinterpret_cast<uint4*>(dst + 2 * PLANE_BYTES) = make_uint4(hi_[0], hi_[1], hi_[2], hi_[3]);
+    *reinterpret_cast<uint4*>(dst + 3 * PLANE_BYTES) = make_uint4(li[0], li[1], li[2], li[3]);
+    *reinterpret_cast<uint4*>(dst + 4 * PLANE_BYTES) = make_uint4(hs[0], hs[1], hs[2], hs[3]);
+    *reinterpret_cast<uint4*>(dst + 5 * PLANE_BYTES) = make_uint4(ls[0], ls[1], ls[2], ls[3]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_tc_gemm: one 128 x 128 output tile per CTA from packed operand blocks.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256, 1) k_tc_gemm(const TcGemmTask* __restrict__ tasks, int* status) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  const GemmTask<float2> tk = tasks[blockIdx.x];
+  const TcGemmTask tk = tasks[blockIdx.x];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  unsigned char* stage_base = smem;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + NSTAGE * STAGE_BYTES);        // 2 barriers
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + NSTAGE * STAGE_BYTES + 64);
-  int* abort_flag = reinterpret_cast<int*>(smem + NSTAGE * STAGE_BYTES + 68);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NSTAGE * STAGE_BYTES);
+  uint64_t* empty = full + NSTAGE;
+  uint64_t* done = empty + NSTAGE;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
 
   if (tid == 0) {
-    for (int s = 0; s < NSTAGE; ++s)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[s])) : "memory");
+    for (int s = 0; s < NSTAGE; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])) : "memory");
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(done)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *abort_flag = 0;
   }
@@ -135,139 +193,60 @@ __global__ void __launch_bounds__(256, 1) k_tc_gemm(const GemmTask<float2>* __re
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
+  const int nkb = tk.nkb;
 
-  const bool bnn = tk.flags & GF_B_NN;
-  const bool dmul = tk.flags & GF_D_MUL, ddiv = tk.flags & GF_D_DIV;
-  const bool bmask = tk.flags & (GF_B_UNIT_LOWER_NT | GF_B_UNIT_LOWER_NN);
-  const bool mask_nt = tk.flags & GF_B_UNIT_LOWER_NT;
-  const int nkb = (tk.k + KB - 1) / KB;
-  const uint32_t idesc = make_idesc();
-
-  // Register-staged operands of one k-block: each thread owns two A units and two B units
-  // (a unit = one row x 4 consecutive k).  All loads of a block are issued together, and the next
-  // block's loads are issued before the current block's MMAs, so global latency overlaps compute.
-  float2 ra[2][4], rd[2][4], rb[2][4];
-  auto load_block = [&](int kb) {
-    const int k0 = kb * KB;
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const int uA = tid + 256 * i;
-      const int r = uA % TM, c = uA / TM;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int k = k0 + 4 * c + q;
-        const bool in = r < tk.m && k < tk.k;
-        ra[i][q] = in ? tk.A[(int64_t)k * tk.lda + r] : make_float2(0.f, 0.f);
-        if (dmul || ddiv) rd[i][q] = (k < tk.k) ? tk.d[(int64_t)k * tk.ldd] : make_float2(1.f, 0.f);
-      }
-      int j, cb;
-      if (bnn) { cb = uA % (KB / 4); j = uA / (KB / 4); } else { j = uA % TN; cb = uA / TN; }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int k = k0 + 4 * cb + q;
-        const bool in = j < tk.n && k < tk.k;
-        rb[i][q] = in ? (bnn ? tk.B[(int64_t)j * tk.ldb + k] : tk.B[(int64_t)k * tk.ldb + j]) : make_float2(0.f, 0.f);
-      }
-    }
-  };
-  // value-dependent work happens at store time so that the loads above stay in flight
-  auto finish_block = [&](int kb) {
-    const int k0 = kb * KB;
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const int uA = tid + 256 * i;
-      if (dmul || ddiv) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) ra[i][q] = dmul ? cmul(ra[i][q], rd[i][q]) : cdiv(ra[i][q], rd[i][q]);
-      }
-      if (bmask) {
-        int j, cb;
-        if (bnn) { cb = uA % (KB / 4); j = uA / (KB / 4); } else { j = uA % TN; cb = uA / TN; }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int kg = tk.kg0 + k0 + 4 * cb + q, ng = tk.ng0 + j;
-          if (j < tk.n && k0 + 4 * cb + q < tk.k) {
-            if (kg == ng) rb[i][q] = make_float2(1.f, 0.f);
-            else if (mask_nt ? (kg > ng) : (kg < ng)) rb[i][q] = make_float2(0.f, 0.f);
-          }
-        }
-      }
-    }
-  };
-  auto store_unit = [&](unsigned char* planes, uint32_t o, const float2 (&v)[4]) {
-    uint32_t hr[4], lr[4], hi_[4], li[4], hs[4], ls[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      split(v[q].x, hr[q], lr[q]);
-      split(v[q].y, hi_[q], li[q]);
-      split(v[q].x + v[q].y, hs[q], ls[q]);
-    }
-    *reinterpret_cast<uint4*>(planes + 0 * PLANE_BYTES + o) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
-    *reinterpret_cast<uint4*>(planes + 1 * PLANE_BYTES + o) = make_uint4(lr[0], lr[1], lr[2], lr[3]);
-    *reinterpret_cast<uint4*>(planes + 2 * PLANE_BYTES + o) = make_uint4(hi_[0], hi_[1], hi_[2], hi_[3]);
-    *reinterpret_cast<uint4*>(planes + 3 * PLANE_BYTES + o) = make_uint4(li[0], li[1], li[2], li[3]);
-    *reinterpret_cast<uint4*>(planes + 4 * PLANE_BYTES + o) = make_uint4(hs[0], hs[1], hs[2], hs[3]);
-    *reinterpret_cast<uint4*>(planes + 5 * PLANE_BYTES + o) = make_uint4(ls[0], ls[1], ls[2], ls[3]);
-  };
-
-  if (nkb > 0) load_block(0);
-  for (int kb = 0; kb < nkb; ++kb) {
-    const int s = kb & 1;
-    unsigned char* st = stage_base + s * STAGE_BYTES;
-    unsigned char* sb = st + NPLANE * PLANE_BYTES;
-    if (kb >= 2) {
-      if (tid == 0 && !mbar_wait(smem_u32(&mbar[s]), (uint32_t)(((kb >> 1) - 1) & 1))) {
+  if (tid == 0) {
+    // producer: stage i & 1 holds k-block i; refill a stage once its MMAs have completed
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i & 1;
+      if (i >= 2 && !mbar_wait(smem_u32(&empty[s]), (uint32_t)(((i >> 1) - 1) & 1))) {
         *abort_flag = 1;
         atomicCAS(status + 1, 0, 1);
+        break;
       }
-      __syncthreads();
-      if (*abort_flag) break;
+      const uint32_t fb = smem_u32(&full[s]);
+      const uint32_t dst = smem_u32(smem + s * STAGE_BYTES);
+      expect_tx(fb, STAGE_BYTES);
+      bulk_copy(dst, tk.A + (int64_t)(tk.kb0 + i) * BLOCK_BYTES, BLOCK_BYTES, fb);
+      bulk_copy(dst + BLOCK_BYTES, tk.B + (int64_t)(tk.kb0 + i) * BLOCK_BYTES, BLOCK_BYTES, fb);
     }
-    finish_block(kb);
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const int uA = tid + 256 * i;
-      store_unit(st, plane_off(uA % TM, 4 * (uA / TM)), ra[i]);
-      int j, cb;
-      if (bnn) { cb = uA % (KB / 4); j = uA / (KB / 4); } else { j = uA % TN; cb = uA / TN; }
-      store_unit(sb, plane_off(j, 4 * cb), rb[i]);
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
+  } else if (tid == 32) {
+    // MMA issuer
+    const uint32_t idesc = make_idesc();
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i & 1;
+      if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((i >> 1) & 1))) {
+        *abort_flag = 1;
+        atomicCAS(status + 1, 0, 1);
+        break;
+      }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a0 = smem_u32(st), b0 = smem_u32(sb);
+      const uint32_t a0 = smem_u32(smem + s * STAGE_BYTES), b0 = a0 + BLOCK_BYTES;
 #pragma unroll
       for (int t = 0; t < KB / 8; ++t) {
         const uint32_t ko = (uint32_t)t * 2 * LBO;  // two core matrices of K per MMA
-        // product p: accumulator, A plane pair, B plane pair  (T1: re*re, T2: im*im, T3: sum*sum)
 #pragma unroll
-        for (int p = 0; p < 3; ++p) {
+        for (int p = 0; p < 3; ++p) {               // T1: re*re, T2: im*im, T3: sum*sum
           const uint32_t dt = tmem + (uint32_t)(p * TN);
           const uint32_t ahi = a0 + (2 * p) * PLANE_BYTES + ko, alo = a0 + (2 * p + 1) * PLANE_BYTES + ko;
           const uint32_t bhi = b0 + (2 * p) * PLANE_BYTES + ko, blo = b0 + (2 * p + 1) * PLANE_BYTES + ko;
-          const uint32_t first = (kb == 0 && t == 0) ? 0u : 1u;
+          const uint32_t first = (i == 0 && t == 0) ? 0u : 1u;
           mma_tf32(dt, make_desc(ahi), make_desc(bhi), idesc, first);
           mma_tf32(dt, make_desc(ahi), make_desc(blo), idesc, 1u);
           mma_tf32(dt, make_desc(alo), make_desc(bhi), idesc, 1u);
         }
       }
-      mma_commit(smem_u32(&mbar[s]));
+      mma_commit(smem_u32(&empty[s]));
     }
-    if (kb + 1 < nkb) load_block(kb + 1);   // next block's loads overlap this block's MMAs
+    mma_commit(smem_u32(done));   // completes when every MMA above has completed
   }
-
-  // wait for the last commit (it covers every earlier MMA of this thread)
-  if (nkb > 0 && !*abort_flag) {
-    if (tid == 0) {
-      const int kl = nkb - 1;
-      if (!mbar_wait(smem_u32(&mbar[kl & 1]), (uint32_t)((kl >> 1) & 1))) {
-        *abort_flag = 1;
-        atomicCAS(status + 1, 0, 1);
-      }
-    }
-    __syncthreads();
+  __syncthreads();
+  // every thread waits for the accumulators (bounded); skipped when the main loop gave up
+  if (!*abort_flag && nkb > 0 && !mbar_wait(smem_u32(done), 0u)) {
+    *abort_flag = 1;
+    atomicCAS(status + 1, 0, 1);
   }
+  __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
   if (!*abort_flag) {
@@ -309,7 +288,11 @@ __global__ void __launch_bounds__(256, 1) k_tc_gemm(const GemmTask<float2>* __re
   }
 }
 
-void launch_tc_gemm(const GemmTask<float2>* tasks, int ntasks, int* status, cudaStream_t st) {
+void launch_tc_pack(const TcPackTask* tasks, int ntasks, cudaStream_t st) {
+  if (ntasks > 0) k_tc_pack<<<ntasks, 256, 0, st>>>(tasks);
+}
+
+void launch_tc_gemm(const TcGemmTask* tasks, int ntasks, int* status, cudaStream_t st) {
   if (ntasks <= 0) return;
   static bool attr = false;
   if (!attr) {
@@ -320,5 +303,7 @@ void launch_tc_gemm(const GemmTask<float2>* tasks, int ntasks, int* status, cuda
 }
 
 int tc_gemm_tile() { return TM; }
+int tc_block_k() { return KB; }
+int64_t tc_block_bytes() { return BLOCK_BYTES; }
 
 }  // namespace psp

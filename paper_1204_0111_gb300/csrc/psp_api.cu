@@ -226,6 +226,8 @@ struct psp_ctx_s {
   int gm_nrhs = 0, gm_k = 0;
   int zero_pivot_front = -1;
   bool use_tc = true;
+  int tc_min_dim = 64;
+  int sweep_level_tasks = 608, sweep_ctas_per_sm = 8;
   bool persistent_sweep = true;
   int64_t upd_arena_elems = 0;
   Stats stats;
@@ -280,6 +282,14 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
       if (lv < sh.nlevels)
         for (int sn : sh.level_sns[lv]) lev_fronts[lv].push_back({p, sn});
     }
+  const bool tc_ok = std::is_same<T, float2>::value && X->use_tc;
+  auto use_tc = [&](int64_t s_, int64_t u_) { return tc_ok && s_ >= X->tc_min_dim && u_ >= X->tc_min_dim; };
+  const int64_t TBLK = tc_block_bytes() / (int64_t)sizeof(T);   // packed block in T elements
+  auto nrb = [](int64_t r) { return (r + 127) / 128; };
+  auto nkb16 = [](int64_t k) { return (k + 15) / 16; };
+  auto packed_elems = [&](int64_t s_, int64_t u_) {   // F_BL, Z D^-1, Z (u x s) and two inv(L) (s x s)
+    return TBLK * (3 * nrb(u_) * nkb16(s_) + 2 * nrb(s_) * nkb16(s_));
+  };
   std::vector<int64_t> slab_size(L, 0), slab_off(L, -1);
   std::vector<int> slab_last(L, -1);
   int64_t temp_max = 0;
@@ -294,6 +304,7 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
         slab_last[lv] = std::max(slab_last[lv], (int)sh.height[sh.parent[sn]]);
       }
       tsum += pad16(s * s) + pad16(u * s);
+      if (use_tc(s, u)) tsum += packed_elems(s, u);
     }
     temp_max = std::max(temp_max, tsum);
   }
@@ -342,7 +353,10 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
   std::vector<ColTask> ctasks;
   std::vector<int> dlist;
   std::vector<GemmTask<T>> gtasks;
-  enum Kind { ASSEMBLE, DIAG, PRIGHT, PLEFT, GEMM, COPY, TCGEMM };
+  std::vector<unsigned char*> packs;     // per front: base of its packed operands (tensor-core fronts)
+  std::vector<TcPackTask> ptasks;
+  std::vector<TcGemmTask> ttasks;
+  enum Kind { ASSEMBLE, DIAG, PRIGHT, PLEFT, GEMM, COPY, TCGEMM, TCPACK };
   struct Launch {
     Kind kind;
     int64_t front_off;
@@ -387,6 +401,11 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
       ft.Z = tbase + toff;
       toff += pad16((int64_t)ft.u * ft.s);
       fronts.push_back(ft);
+      packs.push_back(nullptr);
+      if (use_tc(ft.s, ft.u)) {
+        packs.back() = reinterpret_cast<unsigned char*>(tbase + toff);
+        toff += packed_elems(ft.s, ft.u);
+      }
       smax = std::max(smax, ft.s);
     }
     const int nf = (int)(fronts.size() - f0);
@@ -507,23 +526,22 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
       for (int f = 0; f < nf; ++f) lc.bytes += es * (double)fronts[f0 + f].s * (fronts[f0 + f].s - 1);
       launches.push_back(lc);
     }
-    // the long-contraction GEMMs of fronts with enough work run on tcgen05 tiles of 128 x 128
-    // (complex64); smaller fronts stay on the 64 x 64 CUDA-core tiles
-    const bool tc_ok = std::is_same<T, float2>::value && X->use_tc;
-    auto use_tc = [&](const FrontTask<T>& ft) { return tc_ok && ft.s >= 96 && ft.u >= 96; };
-    auto emit_z = [&](const FrontTask<T>& ft, int TT) {
+    // Z = F_BL inv(L_TL)^T (= F_BL L^{-T}), then F_BR -= Z D^{-1} Z^T (lower) and M_BL = Z D^{-1} inv(L_TL).
+    // Fronts with s, u >= 96 (complex64) run them on tcgen05 tiles of 128 x 128 from packed operands;
+    // the others on 64 x 64 CUDA-core tiles.
+    auto emit_z = [&](const FrontTask<T>& ft) {
       const int ld = ft.s + ft.u;
-      for (int tj = 0; tj < ft.s; tj += TT)
-        for (int ti = 0; ti < ft.u; ti += TT) {
+      for (int tj = 0; tj < ft.s; tj += 64)
+        for (int ti = 0; ti < ft.u; ti += 64) {
           GemmTask<T> g{};
-          const int j1 = std::min(tj + TT, ft.s);
+          const int j1 = std::min(tj + 64, ft.s);
           g.C = ft.Z + (int64_t)tj * ft.u + ti;
           g.ldc = ft.u;
           g.A = ft.G + ft.s + ti;  // F_BL rows, k from 0
           g.lda = ld;
           g.B = ft.G + tj;         // B(n, k) = Linv[tj + n, k]
           g.ldb = ld;
-          g.m = std::min(TT, ft.u - ti);
+          g.m = std::min(64, ft.u - ti);
           g.n = j1 - tj;
           g.k = j1;
           g.kg0 = 0;
@@ -532,10 +550,10 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
           gtasks.push_back(g);
         }
     };
-    auto emit_schur_m = [&](const FrontTask<T>& ft, int TT) {
+    auto emit_schur_m = [&](const FrontTask<T>& ft) {
       const int ld = ft.s + ft.u;
-      for (int tj = 0; tj < ft.u; tj += TT)
-        for (int ti = tj; ti < ft.u; ti += TT) {
+      for (int tj = 0; tj < ft.u; tj += 64)
+        for (int ti = tj; ti < ft.u; ti += 64) {
           GemmTask<T> g{};
           g.C = ft.U + (int64_t)tj * ft.u + ti;
           g.ldc = ft.u;
@@ -545,14 +563,14 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
           g.ldb = ft.u;
           g.d = ft.G;
           g.ldd = ld + 1;
-          g.m = std::min(TT, ft.u - ti);
-          g.n = std::min(TT, ft.u - tj);
+          g.m = std::min(64, ft.u - ti);
+          g.n = std::min(64, ft.u - tj);
           g.k = ft.s;
           g.flags = GF_D_DIV | GF_NEG | (ti == tj ? GF_C_LOWER : 0);
           gtasks.push_back(g);
         }
-      for (int tj = 0; tj < ft.s; tj += TT)
-        for (int ti = 0; ti < ft.u; ti += TT) {
+      for (int tj = 0; tj < ft.s; tj += 64)
+        for (int ti = 0; ti < ft.u; ti += 64) {
           GemmTask<T> g{};
           g.C = ft.G + (int64_t)tj * ld + ft.s + ti;
           g.ldc = ld;
@@ -562,8 +580,8 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
           g.ldd = ld + 1;
           g.B = ft.G + (int64_t)tj * ld + tj;     // B(n, k) = Linv[tj + k, tj + n]
           g.ldb = ld;
-          g.m = std::min(TT, ft.u - ti);
-          g.n = std::min(TT, ft.s - tj);
+          g.m = std::min(64, ft.u - ti);
+          g.n = std::min(64, ft.s - tj);
           g.k = ft.s - tj;
           g.kg0 = tj;
           g.ng0 = tj;
@@ -571,27 +589,142 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
           gtasks.push_back(g);
         }
     };
-    // Z = F_BL inv(L_TL)^T (= F_BL L^{-T}), then F_BR -= Z D^{-1} Z^T (lower) and M_BL = Z D^{-1} inv(L_TL)
-    for (int phase = 0; phase < 2; ++phase)
-      for (int kind = 0; kind < 2; ++kind) {   // 0: CUDA-core tiles, 1: tensor-core tiles
+    // packed operands of a tensor-core front: F_BL | Z D^-1 | Z (u x s each) | inv(L) | inv(L)^T (s x s)
+    struct Packed { unsigned char *bl, *zd, *z, *l, *lt; int64_t ku; };
+    auto packed_of = [&](int f) {
+      const auto& ft = fronts[f0 + f];
+      const int64_t bb = tc_block_bytes();
+      const int64_t uu = nrb(ft.u) * nkb16(ft.s) * bb, ss = nrb(ft.s) * nkb16(ft.s) * bb;
+      unsigned char* b = packs[f0 + f];
+      return Packed{b, b + uu, b + 2 * uu, b + 3 * uu, b + 3 * uu + ss, nkb16(ft.s)};
+    };
+    auto pack = [&](const T* src, const T* d, unsigned char* dst, int ld_, int ldd_, int R, int K, int mode) {
+      for (int rb = 0; rb < nrb(R); ++rb)
+        for (int kb = 0; kb < nkb16(K); ++kb) {
+          TcPackTask t{};
+          t.src = reinterpret_cast<const float2*>(src);
+          t.d = reinterpret_cast<const float2*>(d);
+          t.dst = dst + ((int64_t)rb * nkb16(K) + kb) * tc_block_bytes();
+          t.ld = ld_;
+          t.ldd = ldd_;
+          t.r0 = rb * 128;
+          t.k0 = kb * 16;
+          t.R = R;
+          t.K = K;
+          t.mode = mode;
+          ptasks.push_back(t);
+        }
+    };
+    auto tc_work = [&](double& fl, double& by, int64_t t0) {
+      fl = 0;
+      by = 0;
+      for (size_t i = t0; i < ttasks.size(); ++i) by += 2.0 * ttasks[i].nkb * tc_block_bytes();
+      (void)fl;
+    };
+    for (int phase = 0; phase < 2; ++phase) {
+      // CUDA-core fronts
+      {
         const int64_t g0 = (int64_t)gtasks.size();
         for (int f = 0; f < nf; ++f) {
           const auto& ft = fronts[f0 + f];
-          if (ft.u == 0 || use_tc(ft) != (kind == 1)) continue;
-          const int TT = kind ? tc_gemm_tile() : 64;
-          if (phase == 0) emit_z(ft, TT);
-          else emit_schur_m(ft, TT);
+          if (ft.u == 0 || packs[f0 + f]) continue;
+          if (phase == 0) emit_z(ft);
+          else emit_schur_m(ft);
         }
-        if ((int64_t)gtasks.size() == g0) continue;
-        Launch lg{kind ? TCGEMM : GEMM, f0, g0, (int)(gtasks.size() - g0), -1};
-        gemm_work(g0, lg.flops, lg.bytes);
-        launches.push_back(lg);
+        if ((int64_t)gtasks.size() > g0) {
+          Launch lg{GEMM, f0, g0, (int)(gtasks.size() - g0), -1};
+          gemm_work(g0, lg.flops, lg.bytes);
+          launches.push_back(lg);
+        }
       }
+      // tensor-core fronts: pack, then tiles
+      const int64_t p0 = (int64_t)ptasks.size(), t0 = (int64_t)ttasks.size();
+      double tflops = 0;
+      for (int f = 0; f < nf; ++f) {
+        const auto& ft = fronts[f0 + f];
+        if (ft.u == 0 || !packs[f0 + f]) continue;
+        const int ld = ft.s + ft.u;
+        const Packed P = packed_of(f);
+        const int64_t bb = tc_block_bytes();
+        if (phase == 0) {
+          pack(ft.G + ft.s, nullptr, P.bl, ld, 0, ft.u, ft.s, TC_PACK_PLAIN);
+          pack(ft.G, nullptr, P.l, ld, 0, ft.s, ft.s, TC_PACK_UNIT_LOWER);
+          pack(ft.G, nullptr, P.lt, ld, 0, ft.s, ft.s, TC_PACK_UNIT_LOWER_T);
+          for (int tj = 0; tj < ft.s; tj += 128)
+            for (int ti = 0; ti < ft.u; ti += 128) {
+              const int j1 = std::min(tj + 128, ft.s);
+              TcGemmTask t{};
+              t.A = P.bl + (int64_t)(ti / 128) * P.ku * bb;
+              t.B = P.l + (int64_t)(tj / 128) * P.ku * bb;
+              t.C = reinterpret_cast<float2*>(ft.Z + (int64_t)tj * ft.u + ti);
+              t.ldc = ft.u;
+              t.m = std::min(128, ft.u - ti);
+              t.n = j1 - tj;
+              t.kb0 = 0;
+              t.nkb = (int)nkb16(j1);
+              t.flags = GF_BETA0;
+              ttasks.push_back(t);
+              GemmTask<T> sh{};
+              sh.m = t.m; sh.n = t.n; sh.k = j1; sh.kg0 = 0; sh.ng0 = tj; sh.flags = GF_B_UNIT_LOWER_NT;
+              tflops += 8.0 * gemm_cmacs(sh);
+            }
+        } else {
+          pack(ft.Z, ft.G, P.zd, ft.u, ld + 1, ft.u, ft.s, TC_PACK_PLAIN);
+          pack(ft.Z, nullptr, P.z, ft.u, 0, ft.u, ft.s, TC_PACK_PLAIN);
+          for (int tj = 0; tj < ft.u; tj += 128)
+            for (int ti = tj; ti < ft.u; ti += 128) {
+              TcGemmTask t{};
+              t.A = P.zd + (int64_t)(ti / 128) * P.ku * bb;
+              t.B = P.z + (int64_t)(tj / 128) * P.ku * bb;
+              t.C = reinterpret_cast<float2*>(ft.U + (int64_t)tj * ft.u + ti);
+              t.ldc = ft.u;
+              t.m = std::min(128, ft.u - ti);
+              t.n = std::min(128, ft.u - tj);
+              t.kb0 = 0;
+              t.nkb = (int)nkb16(ft.s);
+              t.flags = GF_NEG | (ti == tj ? GF_C_LOWER : 0);
+              ttasks.push_back(t);
+              GemmTask<T> sh{};
+              sh.m = t.m; sh.n = t.n; sh.k = ft.s; sh.flags = (ti == tj ? GF_C_LOWER : 0);
+              tflops += 8.0 * gemm_cmacs(sh);
+            }
+          for (int tj = 0; tj < ft.s; tj += 128)
+            for (int ti = 0; ti < ft.u; ti += 128) {
+              TcGemmTask t{};
+              t.A = P.zd + (int64_t)(ti / 128) * P.ku * bb;
+              t.B = P.lt + (int64_t)(tj / 128) * P.ku * bb;
+              t.C = reinterpret_cast<float2*>(ft.G + (int64_t)tj * ld + ft.s + ti);
+              t.ldc = ld;
+              t.m = std::min(128, ft.u - ti);
+              t.n = std::min(128, ft.s - tj);
+              t.kb0 = tj / 16;
+              t.nkb = (int)(nkb16(ft.s) - tj / 16);
+              t.flags = GF_BETA0;
+              ttasks.push_back(t);
+              GemmTask<T> sh{};
+              sh.m = t.m; sh.n = t.n; sh.k = ft.s - tj; sh.kg0 = tj; sh.ng0 = tj; sh.flags = GF_B_UNIT_LOWER_NN;
+              tflops += 8.0 * gemm_cmacs(sh);
+            }
+        }
+      }
+      if ((int64_t)ptasks.size() > p0) {
+        Launch lp{TCPACK, f0, p0, (int)(ptasks.size() - p0), -1};
+        lp.bytes = (double)(ptasks.size() - p0) * (tc_block_bytes() + 128.0 * 16 * sizeof(T));
+        launches.push_back(lp);
+        Launch lt{TCGEMM, f0, t0, (int)(ttasks.size() - t0), -1};
+        double fl_unused = 0;
+        tc_work(fl_unused, lt.bytes, t0);
+        lt.flops = tflops;
+        launches.push_back(lt);
+      }
+    }
   }
 
   X->stats.host("plan_tasks", ms_since(tp));
   tp = std::chrono::steady_clock::now();
-  DevBuf d_fronts, d_ctasks, d_dlist, d_gtasks;
+  DevBuf d_fronts, d_ctasks, d_dlist, d_gtasks, d_ptasks, d_ttasks;
+  upload(d_ptasks, ptasks);
+  upload(d_ttasks, ttasks);
   upload(d_fronts, fronts);
   upload(d_ctasks, ctasks);
   upload(d_dlist, dlist);
@@ -605,7 +738,7 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
   int* status = X->d_status.as<int>();
   PSP_CK(cudaMemsetAsync(status, 0, 4 * sizeof(int), st));
   static const char* names[] = {"k_assemble", "k_diag_ldlt", "k_panel_right", "k_panel_left", "k_gemm", "k_copy_linv",
-                                "k_tc_gemm"};
+                                "k_tc_gemm", "k_tc_pack"};
   for (const auto& l : launches) {
     if (l.count <= 0) continue;
     X->stats.run(names[l.kind], st, 1, l.flops, l.bytes, [&] {
@@ -619,9 +752,8 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
         case PLEFT: launch_panel_left<T>(F + l.front_off, CT + l.off, l.count, l.kb, st); break;
         case GEMM: launch_gemm<T>(GT + l.off, l.count, st); break;
         case COPY: launch_copy_linv<T>(F + l.front_off, CT + l.off, l.count, st); break;
-        case TCGEMM:
-          if constexpr (std::is_same<T, float2>::value) launch_tc_gemm(GT + l.off, l.count, status, st);
-          break;
+        case TCGEMM: launch_tc_gemm(d_ttasks.as<TcGemmTask>() + l.off, l.count, status, st); break;
+        case TCPACK: launch_tc_pack(d_ptasks.as<TcPackTask>() + l.off, l.count, st); break;
       }
     }, true);
   }
@@ -663,10 +795,10 @@ static void plan_solve(psp_ctx_s* X) {
         P.vec += 2 * ss + 2 * uu;
       }
       int R = 64;
-      while (R > 8 && rows / R < 608) R >>= 1;
+      while (R > 8 && rows / R < X->sweep_level_tasks) R >>= 1;
       P.R = R;
       int Cc = 64;
-      while (Cc > 8 && cols / Cc < 608) Cc >>= 1;
+      while (Cc > 8 && cols / Cc < X->sweep_level_tasks) Cc >>= 1;
       P.fwd_off = (int64_t)tasks.size();
       for (int sn : sh.level_sns[lv])
         for (int r = 0; r < sh.s[sn] + sh.u[sn]; r += R) tasks.push_back({sn, r, std::min(r + R, sh.s[sn] + sh.u[sn])});
@@ -832,7 +964,7 @@ static void apply_core(psp_ctx_s* X, double2* u, int nrhs, T* xf, T* xb, T* upd,
       const double es = sizeof(T);
       X->stats.run("k_sweep", st, 1, 8.0 * X->sweep_entries * nrhs,
                    X->sweep_entries * es + X->sweep_vec * es * nrhs,
-                   [&] { rc = launch_sweep<T>(sa, X->sweep_rhs_bytes * sizeof(T), st); });
+                   [&] { rc = launch_sweep<T>(sa, X->sweep_rhs_bytes * sizeof(T), X->sweep_ctas_per_sm, st); });
       if (rc > 0) throw Error{PSP_ERR_CUDA, std::string("sweep launch: ") + cudaGetErrorString((cudaError_t)rc)};
     }
     if (rc != 0) {
@@ -1333,6 +1465,10 @@ psp_status psp_setup(const psp_grid* g, const double* c, double omega, int pml_g
   X->stats.timing = o.collect_stats != 0;
   X->stats.mode = o.collect_stats;
   X->use_tc = o.tensor_cores != 0;
+  X->tc_min_dim = o.tc_min_dim > 0 ? o.tc_min_dim : 64;
+  // measured on lens100: complex64 sweeps are fastest at >= 608 tasks per level, complex128 at 304
+  X->sweep_level_tasks = o.sweep_level_tasks > 0 ? o.sweep_level_tasks : (o.precision == PSP_PREC_C64 ? 608 : 304);
+  X->sweep_ctas_per_sm = o.sweep_ctas_per_sm > 0 ? o.sweep_ctas_per_sm : 8;
   *out = X;
   PSP_TRY
   setup_impl(X, c, (cudaStream_t)stream);

@@ -156,7 +156,30 @@ template <typename T>
 void launch_panel_left(const FrontTask<T>* fronts, const ColTask* tasks, int ntasks, int kb, cudaStream_t st);
 template <typename T>
 void launch_gemm(const GemmTask<T>* tasks, int ntasks, cudaStream_t st);
-void launch_tc_gemm(const GemmTask<float2>* tasks, int ntasks, int* status, cudaStream_t st);
+// tensor-core path (complex64): operands packed once per front into TF32 planes, then tiles
+enum TcPackMode { TC_PACK_PLAIN = 0, TC_PACK_UNIT_LOWER = 1, TC_PACK_UNIT_LOWER_T = 2 };
+struct TcPackTask {        // one 128-row x 16-k block of a packed operand
+  const float2* src;       // column-major source, ld
+  const float2* d;         // PLAIN only: divide column k by d[k * ldd] (nullptr: no scaling)
+  void* dst;               // 48 KB destination block
+  int ld, ldd;
+  int r0, k0;              // first row / k of the block
+  int R, K;                // source extents (rows, k); outside -> 0
+  int mode;                // TcPackMode: PLAIN X[r, k]; UNIT_LOWER T[r, k]; UNIT_LOWER_T T[k, r]
+  int pad_;
+};
+struct TcGemmTask {        // one 128 x 128 tile of C (+)= +-A B^T from packed blocks
+  const unsigned char* A;  // packed A row block (k-blocks contiguous)
+  const unsigned char* B;  // packed B row block
+  float2* C;
+  int ldc, m, n;
+  int kb0, nkb;            // k-blocks [kb0, kb0 + nkb)
+  int flags;               // GF_NEG, GF_BETA0, GF_C_LOWER
+};
+void launch_tc_pack(const TcPackTask* tasks, int ntasks, cudaStream_t st);
+void launch_tc_gemm(const TcGemmTask* tasks, int ntasks, int* status, cudaStream_t st);
+int tc_block_k();
+int64_t tc_block_bytes();
 int tc_gemm_tile();
 template <typename T>
 void launch_copy_linv(const FrontTask<T>* fronts, const ColTask* tasks, int ntasks, cudaStream_t st);
@@ -234,7 +257,7 @@ struct SweepArgs {
 };
 // returns 0 on success, -1 when a cooperative launch is not possible, else a cudaError_t
 template <typename T>
-int launch_sweep(const SweepArgs<T>& args, size_t per_rhs_bytes, cudaStream_t st);
+int launch_sweep(const SweepArgs<T>& args, size_t per_rhs_bytes, int max_per_sm, cudaStream_t st);
 
 // ---- GMRES helpers (complex128) ----
 // partial[b * (nvec * nrhs) + i * nrhs + r] = sum over block b's slice of conj(V_i[r]) w[r]

@@ -32,7 +32,8 @@ class Options(ctypes.Structure):
     _fields_ = [("pml_C", ctypes.c_double), ("alpha", ctypes.c_double), ("pad_depth", ctypes.c_int),
                 ("leaf_size", ctypes.c_int), ("precision", ctypes.c_int), ("pml_faces", ctypes.c_int),
                 ("aux_mode", ctypes.c_int), ("collect_stats", ctypes.c_int), ("tensor_cores", ctypes.c_int),
-                ("reserved", ctypes.c_int * 7)]
+                ("tc_min_dim", ctypes.c_int),
+                ("sweep_level_tasks", ctypes.c_int), ("sweep_ctas_per_sm", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 class KernelStat(ctypes.Structure):
@@ -136,7 +137,8 @@ class SweepingPreconditioner:
     """Handle over psp_setup / psp_apply / psp_solve (Algs. 1.4, 1.5 and GMRES(k) of §2.4)."""
 
     def __init__(self, c, h, omega, gamma, panel_depth, pad=None, leaf=64, pml_C=4.0, alpha=2 * math.pi,
-                 precision="c128", faces=63, mode="moving", stream=None, collect_stats=0, tensor_cores=True):
+                 precision="c128", faces=63, mode="moving", stream=None, collect_stats=0, tensor_cores=True,
+                 tc_min_dim=0, sweep_level_tasks=0, sweep_ctas_per_sm=0):
         nz, ny, nx = c.shape
         self.nx, self.ny, self.nz = nx, ny, nz
         self.N = nx * ny * nz
@@ -152,6 +154,9 @@ class SweepingPreconditioner:
         o.aux_mode = {"moving": AUX_MOVING_PML, "exact": AUX_EXACT}[mode]
         o.collect_stats = int(collect_stats)
         o.tensor_cores = 1 if tensor_cores else 0
+        o.tc_min_dim = int(tc_min_dim)
+        o.sweep_level_tasks = int(sweep_level_tasks)
+        o.sweep_ctas_per_sm = int(sweep_ctas_per_sm)
         cp, n = _ptr_and_len(c, complex_=False)
         if n != self.N:
             raise ValueError("c has the wrong size")
