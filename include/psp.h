@@ -86,7 +86,12 @@ typedef struct {
                             blocks of 8..64); <= 0 selects the default (608 complex64, 304 complex128) */
   int sweep_ctas_per_sm; /* sweep schedule: resident CTAs per SM of the persistent sweep (capped by
                             occupancy); <= 0 selects the default (8) */
-  int reserved[4];
+  int setup_temp_mb;   /* cap, in MiB, on the per-front temporaries of one batch of fronts during setup
+                          (a level whose fronts need more is factored in several batches); <= 0: up
+                          to 80 % of the device memory left after the factors and update matrices */
+  int sweep_rhs_group; /* sweep schedule: most right-hand sides (1, 2, 4 or 8) one CTA carries through a
+                          pass over a factor block; <= 0: as many as keep its shared memory within 64 KB */
+  int reserved[2];
 } psp_options;
 
 /* Per-solve report filled by psp_solve (host struct). */
@@ -123,6 +128,33 @@ void psp_default_options(psp_options* opt);
  */
 psp_status psp_setup(const psp_grid* g, const double* c, double omega, int pml_gamma, int panel_depth,
                      const psp_options* opt, void* stream, psp_handle* out);
+
+/*
+ * psp_setup_batch - psp_setup for nprob independent problems (own grid, c, omega, gamma and panel
+ * depth each; one options struct for all, pad_depth < 0 meaning each problem's own gamma) in one
+ * handle.  The panels of every problem are factored together: each tree level of all problems'
+ * fronts is one batch of launches (§2.1: the panels' factorisations are independent), and each
+ * application runs the problems' sweeps (Alg. 1.5) side by side in one persistent launch.
+ *
+ *   grids, c, omega, pml_gamma, panel_depth   arrays of nprob entries; c[q] as for psp_setup
+ *   out          receives the handle
+ * The handle's vectors are batched: with nrhs right-hand sides per problem, a vector block holds
+ * problem 0's N_0 x nrhs block (column per right-hand side, x fastest), then problem 1's, and so
+ * on (psp_batch_layout gives the N_q).  psp_apply, psp_apply_noalloc, psp_matvec and psp_solve take
+ * such blocks (their nrhs is per problem); psp_solve runs one GMRES(k) per problem and right-hand
+ * side, in lockstep.  Panel indices of psp_symbolic_export and psp_export_front count all
+ * problems' panels in order.  Errors as for psp_setup, PSP_ERR_ARG for a bad entry of any array.
+ */
+psp_status psp_setup_batch(int nprob, const psp_grid* grids, const double* const* c, const double* omega,
+                           const int* pml_gamma, const int* panel_depth, const psp_options* opt, void* stream,
+                           psp_handle* out);
+
+/*
+ * psp_batch_layout - the number of problems of a handle (1 for psp_setup) and, in points[0 ..
+ * capacity), each problem's point count N_q.  Errors: PSP_ERR_ARG for a NULL handle or a
+ * negative capacity, or points NULL with capacity > 0.
+ */
+psp_status psp_batch_layout(psp_handle h, int* nprob, int64_t* points, int capacity);
 
 /*
  * psp_apply - Alg. 1.5: out = M^{-1} rhs, a forward sweep u_i := T_i u_i,

@@ -1,91 +1,111 @@
 // Complex128 building blocks of right-preconditioned restarted GMRES(k) (§2.4): batched inner
 // products with a fixed two-stage reduction (no atomics, so every run sums in the same order and
 // the Krylov recurrence is reproducible), multi-vector updates, and the Hessenberg least-squares
-// by complex Givens rotations, one thread per right-hand side.
+// by complex Givens rotations, one thread per column.  A column is one right-hand side of one
+// problem; columns may differ in length (independent problems of a batch).
 #include "cplx.cuh"
 #include "psp_internal.h"
 
 namespace psp {
 
-constexpr int kDotBlocks = 152 * 2;
+constexpr int kDotBlocks = 152 * 2;    // most partial blocks per column
+constexpr int64_t kDotMinChunk = 1024;   // fewest elements per partial block
 
-// partial[(b * nvec + i) * nrhs + r] = sum_{g in slice b} conj(V_i,r[g]) * w_r[g]
-__global__ void __launch_bounds__(256) k_dot_partial(const double2* __restrict__ V, int64_t ldv_vec, int64_t ldv_rhs,
-                                                     const double2* __restrict__ w, int64_t ldw, int nrhs, int64_t N,
-                                                     double2* __restrict__ partial) {
+// blocks that column `len` is cut into: a function of its own length only, so a column sums in
+// the same order whatever other columns share the launch
+__device__ __host__ __forceinline__ int dot_blocks_for(int64_t len) {
+  int64_t b = (len + kDotMinChunk - 1) / kDotMinChunk;
+  return (int)(b < 1 ? 1 : (b > kDotBlocks ? kDotBlocks : b));
+}
+
+int multidot_blocks(int64_t maxlen) { return dot_blocks_for(maxlen); }
+
+// partial[(b * nvec + i) * ncol + c] = sum_{g in slice b of column c} conj(V_i[c][g]) * w[c][g]
+__global__ void __launch_bounds__(256) k_dot_partial(const double2* __restrict__ V, int64_t ldv_vec,
+                                                     const double2* __restrict__ w, const ColSpan* __restrict__ cols,
+                                                     int ncol, double2* __restrict__ partial) {
   __shared__ double2 red[256];
-  const int b = blockIdx.x, i = blockIdx.y, r = blockIdx.z;
-  const double2* v = V + i * ldv_vec + r * ldv_rhs;
-  const double2* ww = w + r * ldw;
+  const int b = blockIdx.x, i = blockIdx.y, c = blockIdx.z;
+  const ColSpan cs = cols[c];
+  const int nb = dot_blocks_for(cs.len);
   double2 acc = make_double2(0.0, 0.0);
-  const int64_t chunk = (N + gridDim.x - 1) / gridDim.x;
-  const int64_t g0 = b * chunk, g1 = min(N, g0 + chunk);
-  for (int64_t g = g0 + threadIdx.x; g < g1; g += blockDim.x) cfma(acc, cconj(v[g]), ww[g]);
+  if (b < nb) {
+    const double2* v = V + i * ldv_vec + cs.off;
+    const double2* ww = w + cs.off;
+    const int64_t chunk = (cs.len + nb - 1) / nb;
+    const int64_t g0 = b * chunk, g1 = min(cs.len, g0 + chunk);
+    for (int64_t g = g0 + threadIdx.x; g < g1; g += blockDim.x) cfma(acc, cconj(v[g]), ww[g]);
+  }
   red[threadIdx.x] = acc;
   __syncthreads();
   for (int o = 128; o > 0; o >>= 1) {
     if (threadIdx.x < o) red[threadIdx.x] = cadd(red[threadIdx.x], red[threadIdx.x + o]);
     __syncthreads();
   }
-  if (threadIdx.x == 0) partial[((int64_t)b * gridDim.y + i) * nrhs + r] = red[0];
+  if (threadIdx.x == 0) partial[((int64_t)b * gridDim.y + i) * ncol + c] = red[0];
 }
 
-__global__ void k_dot_final(const double2* __restrict__ partial, int nblk, int nvec, int nrhs, double2* __restrict__ out) {
+__global__ void k_dot_final(const double2* __restrict__ partial, int nblk, int nvec, int ncol, double2* __restrict__ out) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nvec * nrhs) return;
+  if (t >= nvec * ncol) return;
   double2 acc = make_double2(0.0, 0.0);
-  for (int b = 0; b < nblk; ++b) acc = cadd(acc, partial[(int64_t)b * nvec * nrhs + t]);
+  for (int b = 0; b < nblk; ++b) acc = cadd(acc, partial[(int64_t)b * nvec * ncol + t]);
   out[t] = acc;
 }
 
-void launch_multidot(const double2* V, int64_t ldv_vec, int64_t ldv_rhs, int nvec, const double2* w, int64_t ldw,
-                     int nrhs, int64_t N, double2* partial, double2* out, cudaStream_t st) {
-  dim3 grid(kDotBlocks, nvec, nrhs);
-  k_dot_partial<<<grid, 256, 0, st>>>(V, ldv_vec, ldv_rhs, w, ldw, nrhs, N, partial);
-  const int t = nvec * nrhs;
-  k_dot_final<<<(t + 127) / 128, 128, 0, st>>>(partial, kDotBlocks, nvec, nrhs, out);
+void launch_multidot(const double2* V, int64_t ldv_vec, int nvec, const double2* w, const ColSpan* cols, int ncol,
+                     int64_t maxlen, double2* partial, double2* out, cudaStream_t st) {
+  const int nblk = dot_blocks_for(maxlen);
+  dim3 grid(nblk, nvec, ncol);
+  k_dot_partial<<<grid, 256, 0, st>>>(V, ldv_vec, w, cols, ncol, partial);
+  const int t = nvec * ncol;
+  k_dot_final<<<(t + 127) / 128, 128, 0, st>>>(partial, nblk, nvec, ncol, out);
 }
 
-// w_r += sign * sum_i h[i * nrhs + r] * V_i,r
-__global__ void k_multiaxpy(const double2* __restrict__ V, int64_t ldv_vec, int64_t ldv_rhs, int nvec,
-                            const double2* __restrict__ h, double2* __restrict__ w, int64_t ldw, int nrhs, int64_t N,
-                            double sign) {
-  const int r = blockIdx.y;
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < N; g += (int64_t)gridDim.x * blockDim.x) {
+static unsigned elementwise_blocks(int64_t maxlen) {
+  int64_t blocks = (maxlen + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  return (unsigned)(blocks < 1 ? 1 : blocks);
+}
+
+// w[c] += sign * sum_i h[i * ncol + c] * V_i[c]
+__global__ void k_multiaxpy(const double2* __restrict__ V, int64_t ldv_vec, int nvec, const double2* __restrict__ h,
+                            double2* __restrict__ w, const ColSpan* __restrict__ cols, int ncol, double sign) {
+  const int c = blockIdx.y;
+  const ColSpan cs = cols[c];
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < cs.len; g += (int64_t)gridDim.x * blockDim.x) {
     double2 acc = make_double2(0.0, 0.0);
-    for (int i = 0; i < nvec; ++i) cfma(acc, h[i * nrhs + r], V[i * ldv_vec + r * ldv_rhs + g]);
-    double2* p = w + r * ldw + g;
+    for (int i = 0; i < nvec; ++i) cfma(acc, h[i * ncol + c], V[i * ldv_vec + cs.off + g]);
+    double2* p = w + cs.off + g;
     *p = make_double2(p->x + sign * acc.x, p->y + sign * acc.y);
   }
 }
 
-void launch_multiaxpy(const double2* V, int64_t ldv_vec, int64_t ldv_rhs, int nvec, const double2* h, double2* w,
-                      int64_t ldw, int nrhs, int64_t N, double sign, cudaStream_t st) {
-  int64_t blocks = (N + 255) / 256;
-  if (blocks > 152 * 8) blocks = 152 * 8;
-  dim3 grid((unsigned)blocks, nrhs);
-  k_multiaxpy<<<grid, 256, 0, st>>>(V, ldv_vec, ldv_rhs, nvec, h, w, ldw, nrhs, N, sign);
+void launch_multiaxpy(const double2* V, int64_t ldv_vec, int nvec, const double2* h, double2* w, const ColSpan* cols,
+                      int ncol, int64_t maxlen, double sign, cudaStream_t st) {
+  dim3 grid(elementwise_blocks(maxlen), ncol);
+  k_multiaxpy<<<grid, 256, 0, st>>>(V, ldv_vec, nvec, h, w, cols, ncol, sign);
 }
 
-// y_r = alpha_r * x_r (mode 0), y_r = x_r - y_r (mode 1), y_r += alpha_r * x_r (mode 2)
-__global__ void k_axpby(const double2* __restrict__ x, double2* __restrict__ y, int64_t N, const double2* alpha, int mode) {
-  const int r = blockIdx.y;
-  const double2 a = alpha ? alpha[r] : make_double2(1.0, 0.0);
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < N; g += (int64_t)gridDim.x * blockDim.x) {
-    const double2 xv = x[r * N + g];
-    double2* p = y + r * N + g;
+// y[c] = alpha_c x[c] (mode 0), y[c] = x[c] - y[c] (mode 1), y[c] += alpha_c x[c] (mode 2)
+__global__ void k_axpby(const double2* __restrict__ x, double2* __restrict__ y, const ColSpan* __restrict__ cols,
+                        const double2* alpha, int mode) {
+  const int c = blockIdx.y;
+  const ColSpan cs = cols[c];
+  const double2 a = alpha ? alpha[c] : make_double2(1.0, 0.0);
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < cs.len; g += (int64_t)gridDim.x * blockDim.x) {
+    const double2 xv = x[cs.off + g];
+    double2* p = y + cs.off + g;
     if (mode == 0) *p = cmul(a, xv);
     else if (mode == 1) *p = csub(xv, *p);
     else cfma(*p, a, xv);
   }
 }
 
-void launch_axpby_batch(const double2* x, double2* y, int64_t N, int nrhs, const double2* alpha, int alpha_mode,
-                        cudaStream_t st) {
-  int64_t blocks = (N + 255) / 256;
-  if (blocks > 152 * 8) blocks = 152 * 8;
-  dim3 grid((unsigned)blocks, nrhs);
-  k_axpby<<<grid, 256, 0, st>>>(x, y, N, alpha, alpha_mode);
+void launch_axpby_batch(const double2* x, double2* y, const ColSpan* cols, int ncol, int64_t maxlen,
+                        const double2* alpha, int alpha_mode, cudaStream_t st) {
+  dim3 grid(elementwise_blocks(maxlen), ncol);
+  k_axpby<<<grid, 256, 0, st>>>(x, y, cols, alpha, alpha_mode);
 }
 
 // ---- Hessenberg least squares (one thread per right-hand side) ----

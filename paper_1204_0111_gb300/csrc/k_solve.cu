@@ -227,7 +227,8 @@ static int pick_rg(int nrhs, size_t per_rhs_bytes) {
 // The whole sweep of Alg. 1.5 in one cooperative launch, as a dataflow over the elimination trees.
 // CTAs take tasks from one queue in topological order.  An up-the-tree task of a front waits until
 // every task of its children has finished (and, for the first panel solve's dependence on the one
-// before, until that whole solve has finished); a down-the-tree task waits for its parent (the
+// before it in its problem's chain, until that whole solve has finished; the chains of a batch of
+// independent problems are interleaved in the queue and run side by side); a down-the-tree task waits for its parent (the
 // root: for its own up-the-tree tasks).  A task only waits on tasks earlier in the queue, which are
 // held by running CTAs, and every CTA of a cooperative launch is resident, so the waits end.  Each
 // wait is bounded anyway: a CTA that gives up sets status[2] and stops; the others then give up
@@ -254,43 +255,67 @@ constexpr int kSweepThreads = 256;
 template <typename T, int RG>
 __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int s_idx, s_next, s_ok;
+  __shared__ int s_idx, s_next, s_ok, s_dir, s_R;
+  __shared__ SolveTask s_tk;
+  __shared__ SolveCtx<T> s_cx;      // this task's panel solve, filled by thread 0
   __shared__ ShapeDev s_shape[kMaxSweepShapes];
   __shared__ SweepStep s_step[kMaxSweepSteps];
   __shared__ PanelSweep s_panel[kMaxSweepPanels];
-  // small per-sweep tables in shared memory: every task needs them
-  for (int i = threadIdx.x; i < a.nshapes; i += blockDim.x) s_shape[i] = a.shapes[i];
-  for (int i = threadIdx.x; i < a.nsteps; i += blockDim.x) s_step[i] = a.steps[i];
-  for (int i = threadIdx.x; i < a.npanels; i += blockDim.x) s_panel[i] = a.panels[i];
-  if (threadIdx.x == 0) s_next = (int)atomicAdd(a.queue_head, 1u);
+  // small per-sweep tables in shared memory when they fit; larger ones (batches of problems) are
+  // read from global memory by thread 0
+  const bool tab_smem = a.nshapes <= kMaxSweepShapes && a.nsteps <= kMaxSweepSteps && a.npanels <= kMaxSweepPanels;
+  if (tab_smem) {
+    for (int i = threadIdx.x; i < a.nshapes; i += blockDim.x) s_shape[i] = a.shapes[i];
+    for (int i = threadIdx.x; i < a.nsteps; i += blockDim.x) s_step[i] = a.steps[i];
+    for (int i = threadIdx.x; i < a.npanels; i += blockDim.x) s_panel[i] = a.panels[i];
+  }
+  if (threadIdx.x == 0) {
+    s_next = (int)atomicAdd(a.queue_head, 1u);
+    s_cx = a.cx;   // fields common to every task; thread 0 sets the per-task ones below
+  }
   __syncthreads();
-  SolveCtx<T> cx = a.cx;
-  const int nrg = (cx.nrhs + RG - 1) / RG;
+  const int nrg = (a.cx.nrhs + RG - 1) / RG;
   for (;;) {
     if (threadIdx.x == 0) s_idx = s_next;
     __syncthreads();
     const int idx = s_idx;
     if (idx >= a.nqueue) break;
-    const QueueEntry e = a.queue[idx];
-    const SweepStep sp = s_step[e.step];
-    const PanelSweep& pi = s_panel[sp.panel];
-    cx.sh = s_shape[pi.shape];
-    cx.G = a.factor + pi.gbase;
-    cx.z0 = pi.z0;
-    cx.z1 = pi.z1;
-    cx.lead = pi.lead;
-    cx.has_prev = pi.has_prev;
-    cx.has_next = pi.has_next;
-    cx.mode = sp.mode;
-    const SolveTask tk = a.tasks[e.task];
-    const int fb = a.front_base[pi.shape];
-    unsigned* up = a.done_up + a.step_front_base[e.step];
-    unsigned* down = a.done_down + a.step_front_base[e.step];
     if (threadIdx.x == 0) {
       s_next = (int)atomicAdd(a.queue_head, 1u);   // next task, fetched while this one runs
+      const QueueEntry e = a.queue[idx];
+      const SweepStep sp = tab_smem ? s_step[e.step] : a.steps[e.step];
+      const PanelSweep pi = tab_smem ? s_panel[sp.panel] : a.panels[sp.panel];
+      SolveCtx<T>& cx = s_cx;
+      cx.sh = tab_smem ? s_shape[pi.shape] : a.shapes[pi.shape];
+      cx.G = a.factor + pi.gbase;
+      cx.z0 = pi.z0;
+      cx.z1 = pi.z1;
+      cx.lead = pi.lead;
+      cx.has_prev = pi.has_prev;
+      cx.has_next = pi.has_next;
+      cx.mode = sp.mode;
+      if (a.nprobs > 1) {
+        // the problem's own vector block, coupling tables and work vectors
+        const ProblemSweep& pr = a.probs[sp.prob];
+        cx.u = a.cx.u + pr.off1 * a.cx.nrhs;
+        cx.N = pr.N;
+        cx.nz = pr.nz;
+        cx.s1n = pr.s1n;
+        cx.s2n = pr.s2n;
+        cx.s3h = pr.s3h;
+        cx.inv_h2 = pr.inv_h2;
+        cx.xf = a.cx.xf + (int64_t)sp.prob * a.cx.n_loc * a.cx.nrhs;
+        cx.xb = a.cx.xb + (int64_t)sp.prob * a.cx.n_loc * a.cx.nrhs;
+        cx.upd = a.cx.upd + (int64_t)sp.prob * a.cx.upd_ld * a.cx.nrhs;
+      }
+      const SolveTask tk = a.tasks[e.task];
+      const int fb = a.front_base[pi.shape];
+      const unsigned* up = a.done_up + a.step_front_base[e.step];
+      const unsigned* down = a.done_down + a.step_front_base[e.step];
       bool ok = true;
       if (e.dir == 0) {
-        if (e.step > 0) ok = wait_count(a.step_done + e.step - 1, (unsigned)a.step_tasks[e.step - 1], a.status);
+        const int prev = a.step_prev ? a.step_prev[e.step] : e.step - 1;
+        if (prev >= 0) ok = wait_count(a.step_done + prev, (unsigned)a.step_tasks[prev], a.status);
         for (int c = cx.sh.child_ptr[tk.sn]; ok && c < cx.sh.child_ptr[tk.sn + 1]; ++c) {
           const int ch = cx.sh.child_idx[c];
           ok = wait_count(up + ch, (unsigned)a.ntask_up[fb + ch], a.status);
@@ -301,18 +326,26 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs<T> a) {
                       : wait_count(up + tk.sn, (unsigned)a.ntask_up[fb + tk.sn], a.status);
       }
       __threadfence();
+      s_tk = tk;
+      s_dir = e.dir;
+      s_R = e.R;
       s_ok = ok;
     }
     __syncthreads();
     if (!s_ok) break;
+    const SolveTask tk = s_tk;
+    const int dir = s_dir;
     for (int g = 0; g < nrg; ++g) {
-      if (e.dir == 0) fwd_task<T, RG>(tk, g * RG, cx, e.R, smem_raw);
-      else bwd_task<T, RG>(tk, g * RG, cx, smem_raw);
+      if (dir == 0) fwd_task<T, RG>(tk, g * RG, s_cx, s_R, smem_raw);
+      else bwd_task<T, RG>(tk, g * RG, s_cx, smem_raw);
       __syncthreads();
     }
     if (threadIdx.x == 0) {
+      // completion counters of this task's step and front (the queue entry is re-read: cheap)
+      const QueueEntry e = a.queue[idx];
+      const int front0 = a.step_front_base[e.step];
       __threadfence();
-      atomicAdd((e.dir == 0 ? up : down) + tk.sn, 1u);
+      atomicAdd((dir == 0 ? a.done_up : a.done_down) + front0 + tk.sn, 1u);
       atomicAdd(a.step_done + e.step, 1u);
     }
   }
@@ -343,9 +376,17 @@ static int sweep_rg(const SweepArgs<T>& args, size_t per_rhs_bytes, int max_per_
   return e == cudaSuccess ? 0 : (int)e;
 }
 
+// rhs_group > 0 caps the right-hand sides a CTA carries per pass over a factor block; 0 keeps the
+// group's shared memory within 64 KB so that several CTAs stay resident per SM (a CTA that waits
+// on a dependency then leaves the SM to the others)
 template <typename T>
-int launch_sweep(const SweepArgs<T>& args, size_t per_rhs_bytes, int max_per_sm, cudaStream_t st) {
-  const int rg = pick_rg<T>(args.cx.nrhs, per_rhs_bytes);
+int launch_sweep(const SweepArgs<T>& args, size_t per_rhs_bytes, int max_per_sm, int rhs_group, cudaStream_t st) {
+  int rg = pick_rg<T>(args.cx.nrhs, per_rhs_bytes);
+  if (rhs_group > 0) {
+    while (rg > 1 && rg > rhs_group) rg >>= 1;
+  } else {
+    while (rg > 1 && per_rhs_bytes * rg > 64 * 1024) rg >>= 1;
+  }
   switch (rg) {
     case 8: return sweep_rg<T, 8>(args, per_rhs_bytes, max_per_sm, st);
     case 4: return sweep_rg<T, 4>(args, per_rhs_bytes, max_per_sm, st);
@@ -406,7 +447,7 @@ template void launch_solve_fwd<double2>(const SolveTask*, int, const SolveCtx<do
 template void launch_solve_fwd<float2>(const SolveTask*, int, const SolveCtx<float2>&, int, int, cudaStream_t);
 template void launch_solve_bwd<double2>(const SolveTask*, int, const SolveCtx<double2>&, int, cudaStream_t);
 template void launch_solve_bwd<float2>(const SolveTask*, int, const SolveCtx<float2>&, int, cudaStream_t);
-template int launch_sweep<double2>(const SweepArgs<double2>&, size_t, int, cudaStream_t);
-template int launch_sweep<float2>(const SweepArgs<float2>&, size_t, int, cudaStream_t);
+template int launch_sweep<double2>(const SweepArgs<double2>&, size_t, int, int, cudaStream_t);
+template int launch_sweep<float2>(const SweepArgs<float2>&, size_t, int, int, cudaStream_t);
 
 }  // namespace psp

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <new>
 #include <stdexcept>
 #include <tuple>
@@ -227,9 +228,25 @@ struct psp_ctx_s {
   int zero_pivot_front = -1;
   bool use_tc = true;
   int tc_min_dim = 64;
-  int sweep_level_tasks = 608, sweep_ctas_per_sm = 8;
+  int sweep_level_tasks = 608, sweep_ctas_per_sm = 8, sweep_rhs_group = 0;
   bool persistent_sweep = true;
   int64_t upd_arena_elems = 0;
+  int64_t temp_budget_elems = 0;   // cap on setup temporaries per level group (0: what the device has free)
+  // problems: one, or the independent problems of a batch (psp_setup_batch) with their panels
+  // concatenated; a batched vector holds problem q's N_q x nrhs block at off1_q * nrhs
+  struct Prob {
+    int64_t N = 0, off1 = 0;
+    int panel0 = 0, m = 0, nz = 0;
+    double h = 0;
+    BoxOp opA{}, opJ{};
+    const double2 *s1n = nullptr, *s2n = nullptr, *s3hi = nullptr;
+  };
+  std::vector<Prob> probs;
+  std::vector<std::unique_ptr<psp_ctx_s>> subs;   // a batch's problems: their wave speeds and tables
+  std::vector<BoxOp> h_boxops;                    // per panel, uploaded to d_boxops
+  DevBuf d_sweep_probs, d_cols;
+  int cols_nrhs = 0;
+  int64_t meta_step_prev = -1;
   Stats stats;
 };
 
@@ -268,19 +285,27 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
   auto tp = std::chrono::steady_clock::now();
   const int nb = 32;
   const double tiny = sizeof(T) == 16 ? 1e-300 : 1e-30;
+  // --- levels and memory plan ---
+  // Fronts are batched by depth from the root, deepest first: level lv holds the fronts of depth
+  // L - 1 - lv of every panel, so each child sits exactly one level below its parent.  The update
+  // matrices made at one level are all consumed (extend-added) by the next, so two arenas used
+  // alternately hold every update matrix.
   int L = 0;
-  for (auto& sh : X->shapes) L = std::max(L, sh.nlevels);
-
-  // --- memory plan ---
-  // Update matrices of one tree level share a slab; a slab is released after the highest level
-  // that consumes (extend-adds) one of its blocks.  Slabs are placed first-fit on one arena.
+  for (auto& sh : X->shapes) L = std::max(L, sh.ndepths);
+  std::vector<std::vector<std::vector<int>>> depth_sns(X->shapes.size());
+  for (size_t si = 0; si < X->shapes.size(); ++si) {
+    const Shape& sh = X->shapes[si];
+    depth_sns[si].assign(sh.ndepths, {});
+    for (int sn = 0; sn < sh.nsn; ++sn) depth_sns[si][sh.depth[sn]].push_back(sn);
+  }
   std::vector<int64_t> uoff(X->nfronts, -1);
   std::vector<std::vector<std::pair<int, int>>> lev_fronts(L);  // (panel, sn)
   for (int lv = 0; lv < L; ++lv)
     for (int p = 0; p < X->m; ++p) {
-      const Shape& sh = X->shapes[X->shape_of[p]];
-      if (lv < sh.nlevels)
-        for (int sn : sh.level_sns[lv]) lev_fronts[lv].push_back({p, sn});
+      const int si = X->shape_of[p];
+      const int d = L - 1 - lv;
+      if (d < (int)depth_sns[si].size())
+        for (int sn : depth_sns[si][d]) lev_fronts[lv].push_back({p, sn});
     }
   const bool tc_ok = std::is_same<T, float2>::value && X->use_tc;
   auto use_tc = [&](int64_t s_, int64_t u_) { return tc_ok && s_ >= X->tc_min_dim && u_ >= X->tc_min_dim; };
@@ -290,55 +315,70 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
   auto packed_elems = [&](int64_t s_, int64_t u_) {   // F_BL, Z D^-1, Z (u x s) and two inv(L) (s x s)
     return TBLK * (3 * nrb(u_) * nkb16(s_) + 2 * nrb(s_) * nkb16(s_));
   };
-  std::vector<int64_t> slab_size(L, 0), slab_off(L, -1);
-  std::vector<int> slab_last(L, -1);
-  int64_t temp_max = 0;
+  auto front_temp = [&](int64_t s_, int64_t u_) {     // W (s x s), Z (u x s), packed operands
+    return pad16(s_ * s_) + pad16(u_ * s_) + (use_tc(s_, u_) ? packed_elems(s_, u_) : 0);
+  };
+  int64_t arena[2] = {0, 0}, temp_level_max = 0, temp_front_max = 16;
   for (int lv = 0; lv < L; ++lv) {
-    int64_t tsum = 0;
+    int64_t slab = 0, tsum = 0;
     for (auto [p, sn] : lev_fronts[lv]) {
       const Shape& sh = X->shapes[X->shape_of[p]];
       const int64_t s = sh.s[sn], u = sh.u[sn];
       if (u > 0) {
-        uoff[X->sn_base[p] + sn] = slab_size[lv];   // relative to the slab for now
-        slab_size[lv] += pad16(u * u);
-        slab_last[lv] = std::max(slab_last[lv], (int)sh.height[sh.parent[sn]]);
+        uoff[X->sn_base[p] + sn] = slab;
+        slab += pad16(u * u);
       }
-      tsum += pad16(s * s) + pad16(u * s);
-      if (use_tc(s, u)) tsum += packed_elems(s, u);
+      const int64_t t = front_temp(s, u);
+      tsum += t;
+      temp_front_max = std::max(temp_front_max, t);
     }
-    temp_max = std::max(temp_max, tsum);
+    arena[lv & 1] = std::max(arena[lv & 1], slab);
+    temp_level_max = std::max(temp_level_max, tsum);
   }
-  {
-    // a slab is live from its own level through the last level that extend-adds from it
-    int64_t peak = 0;
-    for (int lv = 0; lv < L; ++lv) {
-      if (slab_size[lv] == 0) continue;
-      std::vector<std::pair<int64_t, int64_t>> live;   // (offset, size), sorted by offset
-      for (int q = 0; q < lv; ++q)
-        if (slab_size[q] > 0 && slab_last[q] >= lv) live.push_back({slab_off[q], slab_size[q]});
-      std::sort(live.begin(), live.end());
-      int64_t pos = 0;
-      for (const auto& sl : live) {
-        if (sl.first - pos >= slab_size[lv]) break;
-        pos = std::max(pos, sl.first + sl.second);
-      }
-      slab_off[lv] = pos;
-      peak = std::max(peak, pos + slab_size[lv]);
-    }
-    for (int lv = 0; lv < L; ++lv)
-      for (auto [p, sn] : lev_fronts[lv]) {
-        int64_t& o = uoff[X->sn_base[p] + sn];
-        if (o >= 0) o += slab_off[lv];
-      }
-    X->upd_arena_elems = peak;
-  }
+  X->upd_arena_elems = arena[0] + arena[1];
   X->stats.host("plan_memory", ms_since(tp));
   tp = std::chrono::steady_clock::now();
   DevBuf d_upd, d_temp;
   d_upd.alloc((size_t)std::max<int64_t>(X->upd_arena_elems, 16) * sizeof(T));
-  d_temp.alloc((size_t)std::max<int64_t>(temp_max, 16) * sizeof(T));
+  // per-front temporaries of one group of a level; a level whose temporaries exceed what the device
+  // has left is processed in several groups
+  int64_t temp_budget = temp_level_max;
+  {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+      const double avail = 0.8 * ((double)free_b - 2.0e9);
+      const int64_t cap = (int64_t)std::max(0.0, avail / (double)sizeof(T));
+      if (X->temp_budget_elems > 0) temp_budget = std::min(temp_budget, X->temp_budget_elems);
+      temp_budget = std::max(temp_front_max, std::min(temp_budget, cap));
+    } else {
+      cudaGetLastError();
+    }
+  }
+  d_temp.alloc((size_t)std::max<int64_t>(temp_budget, 16) * sizeof(T));
   X->stats.host("alloc_work", ms_since(tp));
   tp = std::chrono::steady_clock::now();
+  std::vector<std::vector<std::pair<int, int>>> groups;   // (panel, sn) lists, in level order
+  for (int lv = 0; lv < L; ++lv) {
+    int64_t run = 0;
+    bool fresh = true;   // every level starts a new group
+    for (auto [p, sn] : lev_fronts[lv]) {
+      const Shape& sh = X->shapes[X->shape_of[p]];
+      const int64_t t = front_temp(sh.s[sn], sh.u[sn]);
+      if (fresh || run + t > temp_budget) {
+        groups.emplace_back();
+        run = 0;
+        fresh = false;
+      }
+      groups.back().push_back({p, sn});
+      run += t;
+    }
+  }
+  // odd levels use the second arena
+  for (int lv = 1; lv < L; lv += 2)
+    for (auto [p, sn] : lev_fronts[lv]) {
+      int64_t& o = uoff[X->sn_base[p] + sn];
+      if (o >= 0) o += arena[0];
+    }
   T* ubase = d_upd.as<T>();
   T* tbase = d_temp.as<T>();
   T* fbase = X->d_factor.as<T>();
@@ -382,11 +422,11 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
       for (int ti = tj; ti < M; ti += 64) emit(C, ldc, ti, tj, std::min(64, M - ti), std::min(64, M - tj));
   };
 
-  for (int lv = 0; lv < L; ++lv) {
+  for (const auto& grp : groups) {
     const int64_t f0 = (int64_t)fronts.size();
     int smax = 0;
     int64_t toff = 0;
-    for (auto [p, sn] : lev_fronts[lv]) {
+    for (auto [p, sn] : grp) {
       const Shape& sh = X->shapes[X->shape_of[p]];
       FrontTask<T> ft{};
       ft.s = sh.s[sn];
@@ -811,10 +851,30 @@ static void plan_solve(psp_ctx_s* X) {
   }
   upload(X->d_stasks, tasks);
 
-  // persistent sweep: panel solves in Alg. 1.5 order and one task queue in topological order
+  // persistent sweep: panel solves in Alg. 1.5 order and one task queue in topological order.  The
+  // chains of a batch's problems are interleaved step by step; each step follows the previous step
+  // of its own problem.
   std::vector<SweepStep> steps;
-  for (int i = 0; i < X->m; ++i) steps.push_back({i, 0});
-  for (int i = X->m - 2; i >= 0; --i) steps.push_back({i, 1});
+  std::vector<int> step_prev;
+  {
+    const int np = (int)X->probs.size();
+    std::vector<std::vector<SweepStep>> chain(np);
+    size_t longest = 0;
+    for (int q = 0; q < np; ++q) {
+      const auto& pr = X->probs[q];
+      for (int i = 0; i < pr.m; ++i) chain[q].push_back({pr.panel0 + i, 0, q});
+      for (int i = pr.m - 2; i >= 0; --i) chain[q].push_back({pr.panel0 + i, 1, q});
+      longest = std::max(longest, chain[q].size());
+    }
+    std::vector<int> last(np, -1);
+    for (size_t t = 0; t < longest; ++t)
+      for (int q = 0; q < np; ++q)
+        if (t < chain[q].size()) {
+          step_prev.push_back(last[q]);
+          last[q] = (int)steps.size();
+          steps.push_back(chain[q][t]);
+        }
+  }
   // per shape: tasks per front, up and down
   std::vector<int> front_base(X->shapes.size() + 1, 0), ntask_up, ntask_down;
   size_t per_rhs = 0;
@@ -868,20 +928,38 @@ static void plan_solve(psp_ctx_s* X) {
   meta.insert(meta.end(), step_front.begin(), step_front.end());
   X->meta_step_tasks = (int64_t)meta.size();
   meta.insert(meta.end(), step_tasks.begin(), step_tasks.end());
+  X->meta_step_prev = (int64_t)meta.size();
+  meta.insert(meta.end(), step_prev.begin(), step_prev.end());
   X->meta_front_base = o_up;
   upload(X->d_sweep_meta, meta);
+  std::vector<ProblemSweep> pss;
+  for (const auto& pr : X->probs) {
+    ProblemSweep p{};
+    p.off1 = pr.off1;
+    p.N = pr.N;
+    p.s1n = pr.s1n;
+    p.s2n = pr.s2n;
+    p.s3h = pr.s3hi;
+    p.inv_h2 = 1.0 / (pr.h * pr.h);
+    p.nz = pr.nz;
+    pss.push_back(p);
+  }
+  upload(X->d_sweep_probs, pss);
   // counters zeroed before every sweep: head | status[4] | step_done[nsteps] | done_up | done_down
   X->sweep_sync_words = 1 + 4 + steps.size() + 2 * (size_t)step_front[steps.size()];
   X->d_sweep_sync.alloc(X->sweep_sync_words * 4);
   PSP_CK(cudaMemset(X->d_sweep_sync.p, 0, X->sweep_sync_words * 4));
 }
 
+// work vectors of one sweep: per problem (a batch's chains run side by side) a box vector pair of
+// max_nloc x nrhs and update vectors of max_upd x nrhs
 template <typename T>
 static void ensure_apply_ws(psp_ctx_s* X, int nrhs) {
   if (X->ws_nrhs >= nrhs) return;
-  X->ws_xf.alloc((size_t)X->max_nloc * nrhs * sizeof(T));
-  X->ws_xb.alloc((size_t)X->max_nloc * nrhs * sizeof(T));
-  X->ws_upd.alloc((size_t)X->max_upd * nrhs * sizeof(T));
+  const size_t np = X->probs.size();
+  X->ws_xf.alloc((size_t)X->max_nloc * nrhs * np * sizeof(T));
+  X->ws_xb.alloc((size_t)X->max_nloc * nrhs * np * sizeof(T));
+  X->ws_upd.alloc((size_t)X->max_upd * nrhs * np * sizeof(T));
   X->ws_nrhs = nrhs;
 }
 
@@ -890,23 +968,36 @@ static void ensure_apply_ws(psp_ctx_s* X, int nrhs) {
 template <typename T>
 static void apply_core(psp_ctx_s* X, double2* u, int nrhs, T* xf, T* xb, T* upd, bool timed, cudaStream_t st) {
   SolveCtx<T> cx{};
+  const int np = (int)X->probs.size();
+  // problem q's vectors and work vectors
+  auto set_problem = [&](int q) {
+    const auto& pr = X->probs[q];
+    cx.xf = xf + (int64_t)q * X->max_nloc * nrhs;
+    cx.xb = xb + (int64_t)q * X->max_nloc * nrhs;
+    cx.upd = upd + (int64_t)q * X->max_upd * nrhs;
+    cx.u = u + pr.off1 * nrhs;
+    cx.N = pr.N;
+    cx.nz = pr.nz;
+    cx.s1n = pr.s1n;
+    cx.s2n = pr.s2n;
+    cx.s3h = pr.s3hi;
+    cx.inv_h2 = 1.0 / (pr.h * pr.h);
+  };
+  cx.nrhs = nrhs;
+  cx.upd_ld = X->max_upd;
+  cx.n_loc = X->max_nloc;
+  set_problem(0);
+  // the persistent sweep offsets problem q's pointers itself: hand it the bases
   cx.xf = xf;
   cx.xb = xb;
   cx.upd = upd;
   cx.u = u;
-  cx.N = X->N;
-  cx.nrhs = nrhs;
-  cx.nz = X->nz;
-  cx.s1n = X->s1n;
-  cx.s2n = X->s2n;
-  cx.s3h = X->s3hi;
-  cx.inv_h2 = 1.0 / (X->h * X->h);
-  cx.upd_ld = X->max_upd;
-  cx.n_loc = X->max_nloc;
   const SolveTask* tasks = X->d_stasks.as<SolveTask>();
   const bool was_timing = X->stats.timing;
   if (!timed) X->stats.timing = false;
-  auto runT = [&](int i, int mode) {
+  auto runT = [&](int q, int i, int mode) {
+    const auto& pr = X->probs[q];
+    set_problem(q);
     const int si = X->shape_of[i];
     cx.sh = X->shdev[si];
     cx.G = X->d_factor.as<T>() + X->panel_fbase[i];
@@ -914,8 +1005,8 @@ static void apply_core(psp_ctx_s* X, double2* u, int nrhs, T* xf, T* xb, T* upd,
     cx.z1 = X->z1[i];
     cx.lead = X->lead[i];
     cx.mode = mode;
-    cx.has_prev = i > 0;
-    cx.has_next = i < X->m - 1;
+    cx.has_prev = i > pr.panel0;
+    cx.has_next = i < pr.panel0 + pr.m - 1;
     const auto& plan = X->splan[si];
     const int nl = (int)plan.size();
     const double es = sizeof(T);
@@ -950,6 +1041,9 @@ static void apply_core(psp_ctx_s* X, double2* u, int nrhs, T* xf, T* xb, T* upd,
     sa.ntask_down = meta + X->meta_ntask_down;
     sa.step_front_base = meta + X->meta_step_front;
     sa.step_tasks = meta + X->meta_step_tasks;
+    sa.nprobs = np;
+    sa.probs = X->d_sweep_probs.as<ProblemSweep>();
+    sa.step_prev = np > 1 ? meta + X->meta_step_prev : nullptr;
     unsigned* sync = X->d_sweep_sync.as<unsigned>();
     const int64_t nfront_steps = ((int64_t)X->sweep_sync_words - 5 - X->sweep_nsteps) / 2;
     sa.queue_head = sync;
@@ -958,18 +1052,21 @@ static void apply_core(psp_ctx_s* X, double2* u, int nrhs, T* xf, T* xb, T* upd,
     sa.done_up = sync + 5 + X->sweep_nsteps;
     sa.done_down = sa.done_up + nfront_steps;
     int rc = -1;
-    if (X->persistent_sweep && X->shapes.size() <= 4 && X->sweep_nsteps <= 512 && X->m <= 256) {
+    if (X->persistent_sweep) {
       // queue head and completion counters start at zero; status[2] is cleared too
       PSP_CK(cudaMemsetAsync(sync, 0, X->sweep_sync_words * 4, st));
       const double es = sizeof(T);
       X->stats.run("k_sweep", st, 1, 8.0 * X->sweep_entries * nrhs,
                    X->sweep_entries * es + X->sweep_vec * es * nrhs,
-                   [&] { rc = launch_sweep<T>(sa, X->sweep_rhs_bytes * sizeof(T), X->sweep_ctas_per_sm, st); });
+                   [&] { rc = launch_sweep<T>(sa, X->sweep_rhs_bytes * sizeof(T), X->sweep_ctas_per_sm, X->sweep_rhs_group, st); });
       if (rc > 0) throw Error{PSP_ERR_CUDA, std::string("sweep launch: ") + cudaGetErrorString((cudaError_t)rc)};
     }
     if (rc != 0) {
-      for (int i = 0; i < X->m; ++i) runT(i, 0);          // u_i := T_i (u_i - J_{i,i-1} u_{i-1})
-      for (int i = X->m - 2; i >= 0; --i) runT(i, 1);     // u_i -= T_i J_{i+1,i}^T u_{i+1}
+      for (int q = 0; q < np; ++q) {
+        const auto& pr = X->probs[q];
+        for (int i = 0; i < pr.m; ++i) runT(q, pr.panel0 + i, 0);        // u_i := T_i (u_i - J_{i,i-1} u_{i-1})
+        for (int i = pr.m - 2; i >= 0; --i) runT(q, pr.panel0 + i, 1);   // u_i -= T_i J_{i+1,i}^T u_{i+1}
+      }
     }
   } catch (...) {
     X->stats.timing = was_timing;
@@ -989,15 +1086,15 @@ static void apply_impl(psp_ctx_s* X, double2* u, int nrhs, cudaStream_t st) {
 static size_t round256(size_t b) { return (b + 255) / 256 * 256; }
 
 size_t apply_workspace_bytes(const psp_ctx_s* X, int nrhs) {
-  const size_t e = X->elem_bytes;
-  return 2 * round256((size_t)X->max_nloc * nrhs * e) + round256((size_t)X->max_upd * nrhs * e);
+  const size_t e = X->elem_bytes, np = X->probs.size();
+  return 2 * round256((size_t)X->max_nloc * nrhs * np * e) + round256((size_t)X->max_upd * nrhs * np * e);
 }
 
 psp_status apply_with_workspace(psp_ctx_s* X, double2* u, int nrhs, void* ws, cudaStream_t st) {
   try {
     char* p = static_cast<char*>(ws);
     const size_t e = X->elem_bytes;
-    const size_t bx = round256((size_t)X->max_nloc * nrhs * e);
+    const size_t bx = round256((size_t)X->max_nloc * nrhs * X->probs.size() * e);
     if (X->prec == PSP_PREC_C64)
       apply_core<float2>(X, u, nrhs, (float2*)p, (float2*)(p + bx), (float2*)(p + 2 * bx), false, st);
     else
@@ -1027,7 +1124,9 @@ static void apply_dispatch(psp_ctx_s* X, double2* u, int nrhs, cudaStream_t st) 
 // ---------------------------------------------------------------------------
 // setup
 // ---------------------------------------------------------------------------
-static void setup_impl(psp_ctx_s* X, const double* c, cudaStream_t st) {
+// One problem's own part of setup: wave speed, PML tables, panel plan, shapes and box operators
+// (kept on the host in X->h_boxops); no factor storage yet.
+static void build_problem(psp_ctx_s* X, const double* c, cudaStream_t st) {
   auto t_start = std::chrono::steady_clock::now();
   const int nx = X->nx, ny = X->ny, nz = X->nz;
   X->N = (int64_t)nx * ny * nz;
@@ -1139,10 +1238,30 @@ static void setup_impl(psp_ctx_s* X, const double* c, cudaStream_t st) {
   const double2 k2J = make_double2(X->omega * X->omega - X->alpha * X->alpha, 2.0 * X->omega * X->alpha);
   X->opA = make_op(nz, k2A, CP + gcpl, G + goff[4], G + goff[5]);
   X->opJ = make_op(nz, k2J, CP + gcpl, G + goff[4], G + goff[5]);
-  std::vector<BoxOp> bops(X->m);
+  X->h_boxops.assign(X->m, BoxOp{});
   for (int i = 0; i < X->m; ++i)
-    bops[i] = make_op(X->lead[i] + X->z1[i] - X->z0[i], k2J, CP + p_cpl[i], G + p_s3n[i], G + p_s3h[i]);
-  upload(X->d_boxops, bops);
+    X->h_boxops[i] = make_op(X->lead[i] + X->z1[i] - X->z0[i], k2J, CP + p_cpl[i], G + p_s3n[i], G + p_s3h[i]);
+  psp_ctx_s::Prob pr;
+  pr.N = X->N;
+  pr.off1 = 0;
+  pr.panel0 = 0;
+  pr.m = X->m;
+  pr.nz = nz;
+  pr.h = X->h;
+  pr.opA = X->opA;
+  pr.opJ = X->opJ;
+  pr.s1n = X->s1n;
+  pr.s2n = X->s2n;
+  pr.s3hi = X->s3hi;
+  X->probs.assign(1, pr);
+  X->stats.host("symbolic_tables", ms_since(t_start));
+}
+
+// Shared part of setup, over every panel of the handle (one problem or a batch): device shapes and
+// operators, factor storage, the solve plan, and the batched factorisation.
+static void finish_setup(psp_ctx_s* X, cudaStream_t st) {
+  auto t_start = std::chrono::steady_clock::now();
+  upload(X->d_boxops, X->h_boxops);
 
   // shapes to the device
   X->shape_bufs.clear();
@@ -1219,18 +1338,19 @@ static void setup_impl(psp_ctx_s* X, const double* c, cudaStream_t st) {
   X->elem_bytes = X->prec == PSP_PREC_C64 ? 8 : 16;
   {
     std::vector<PanelSweep> ps(X->m);
-    for (int i = 0; i < X->m; ++i) {
-      ps[i].gbase = X->panel_fbase[i];
-      ps[i].shape = X->shape_of[i];
-      ps[i].z0 = X->z0[i];
-      ps[i].z1 = X->z1[i];
-      ps[i].lead = X->lead[i];
-      ps[i].has_prev = i > 0;
-      ps[i].has_next = i < X->m - 1;
-    }
+    for (const auto& pr : X->probs)
+      for (int i = pr.panel0; i < pr.panel0 + pr.m; ++i) {
+        ps[i].gbase = X->panel_fbase[i];
+        ps[i].shape = X->shape_of[i];
+        ps[i].z0 = X->z0[i];
+        ps[i].z1 = X->z1[i];
+        ps[i].lead = X->lead[i];
+        ps[i].has_prev = i > pr.panel0;
+        ps[i].has_next = i < pr.panel0 + pr.m - 1;
+      }
     upload(X->d_sweep_panels, ps);
   }
-  X->stats.host("symbolic_tables", ms_since(t_start));
+  X->stats.host("device_tables", ms_since(t_start));
   auto ta = std::chrono::steady_clock::now();
   X->d_factor.alloc((size_t)fe * X->elem_bytes);
   X->d_status.alloc(4 * sizeof(int));
@@ -1242,18 +1362,74 @@ static void setup_impl(psp_ctx_s* X, const double* c, cudaStream_t st) {
   else factor_all<double2>(X, st);
 }
 
+static void setup_impl(psp_ctx_s* X, const double* c, cudaStream_t st) {
+  build_problem(X, c, st);
+  finish_setup(X, st);
+}
+
+// A batch: every problem's own tables, then its panels appended to the handle's panel list.
+static void setup_batch_impl(psp_ctx_s* B, int nprob, const double* const* c, cudaStream_t st) {
+  B->m = 0;
+  B->N = 0;
+  B->probs.clear();
+  for (int q = 0; q < nprob; ++q) {
+    psp_ctx_s* X = B->subs[q].get();
+    build_problem(X, c[q], st);
+    const int shape0 = (int)B->shapes.size();
+    for (auto& sh : X->shapes) B->shapes.push_back(std::move(sh));
+    X->shapes.clear();
+    psp_ctx_s::Prob pr = X->probs[0];
+    pr.off1 = B->N;
+    pr.panel0 = B->m;
+    B->probs.push_back(pr);
+    for (int i = 0; i < X->m; ++i) {
+      B->z0.push_back(X->z0[i]);
+      B->z1.push_back(X->z1[i]);
+      B->lead.push_back(X->lead[i]);
+      B->shape_of.push_back(shape0 + X->shape_of[i]);
+      B->h_boxops.push_back(X->h_boxops[i]);
+    }
+    B->m += X->m;
+    B->N += X->N;
+    for (auto& kv : X->stats.k)
+      if (kv.first.rfind("host:", 0) == 0) B->stats.host(kv.first.substr(5).c_str(), kv.second.ms);
+  }
+  B->nx = B->subs[0]->nx;
+  B->ny = B->subs[0]->ny;
+  B->nz = B->subs[0]->nz;
+  B->h = B->subs[0]->h;
+  B->opA = B->subs[0]->opA;
+  B->opJ = B->subs[0]->opJ;
+  finish_setup(B, st);
+}
+
 // ---------------------------------------------------------------------------
 // GMRES(k), right preconditioned, x0 = 0, complex128 (§2.4, §3)
 // ---------------------------------------------------------------------------
-static void solve_impl(psp_ctx_s* X, const double2* f, double2* x, int nrhs, double tol, int k, int maxit,
+static void solve_impl(psp_ctx_s* X, const double2* f, double2* x, int nrhs_in, double tol, int k, int maxit,
                        psp_solve_info* info, cudaStream_t st) {
-  const int64_t N = X->N;
+  // GMRES columns: right-hand side r of problem q is column q * nrhs + r, the span
+  // [off1_q nrhs + r N_q, + N_q) of every vector block; all columns iterate in lockstep but each
+  // has its own Krylov basis, Hessenberg matrix and convergence test
+  const int np = (int)X->probs.size();
+  const int nrhs = np * nrhs_in;        // columns
+  const int64_t NT = X->N * nrhs_in;    // elements of one vector block
+  int64_t maxlen = 0;
+  if (X->cols_nrhs != nrhs_in) {
+    std::vector<ColSpan> cols;
+    for (const auto& pr : X->probs)
+      for (int r = 0; r < nrhs_in; ++r) cols.push_back({pr.off1 * nrhs_in + r * pr.N, pr.N});
+    upload(X->d_cols, cols);
+    X->cols_nrhs = nrhs_in;
+  }
+  for (const auto& pr : X->probs) maxlen = std::max(maxlen, pr.N);
+  const ColSpan* cols = X->d_cols.as<ColSpan>();
   const int K = k;
   // workspace layout (double2 elements)
-  const int64_t nV = (int64_t)(K + 1) * nrhs * N, nZ = (int64_t)K * nrhs * N, nW = (int64_t)nrhs * N;
+  const int64_t nV = (int64_t)(K + 1) * NT, nZ = (int64_t)K * NT, nW = NT;
   const int64_t nB = nW;
   const int64_t nH = (int64_t)(K + 1) * K * nrhs, nSn = (int64_t)K * nrhs, nG = (int64_t)(K + 1) * nrhs;
-  const int64_t nPart = (int64_t)304 * (K + 1) * nrhs, nDot = (int64_t)(K + 1) * nrhs;
+  const int64_t nPart = (int64_t)multidot_blocks(maxlen) * (K + 1) * nrhs, nDot = (int64_t)(K + 1) * nrhs;
   const int64_t total = nV + nZ + nW + nB + nH + nSn + nG + nPart + 3 * nDot + 3 * nrhs + (int64_t)K * nrhs + 64;
   X->gm.ensure((size_t)total * sizeof(double2) + (size_t)(K + 8) * nrhs * sizeof(double) + 4 * nrhs * sizeof(int));
   double2* base = X->gm.as<double2>();
@@ -1278,28 +1454,36 @@ static void solve_impl(psp_ctx_s* X, const double2* f, double2* x, int nrhs, dou
   LsqState Ls{};
   Ls.H = Hm; Ls.cs = cs; Ls.sn = sn; Ls.g = g; Ls.resid = resid; Ls.scl = scl; Ls.active = active;
   Ls.k = K; Ls.nrhs = nrhs;
-  const int64_t ldv_vec = (int64_t)nrhs * N;
+  const int64_t ldv_vec = NT;
 
   Stats& S = X->stats;
-  const double vb = 16.0 * N * nrhs;   // bytes of one vector block
+  const double vb = 16.0 * NT;   // bytes of one vector block
   auto matvec = [&](const double2* in, double2* out) {
-    S.run("k_matvec", st, 1, 8.0 * 7 * N * nrhs, 8.0 * N + 2 * vb, [&] { launch_matvec(X->opA, in, out, nrhs, N, st); });
+    for (const auto& pr : X->probs) {
+      const int64_t o = pr.off1 * nrhs_in;
+      S.run("k_matvec", st, 1, 8.0 * 7 * pr.N * nrhs_in, 8.0 * pr.N + 32.0 * pr.N * nrhs_in,
+            [&] { launch_matvec(pr.opA, in + o, out + o, nrhs_in, pr.N, st); });
+    }
   };
   auto multidot = [&](const double2* Vv, int64_t ldvv, int nvec, const double2* ww, double2* out) {
-    S.run("k_dot_partial+k_dot_final", st, 2, 8.0 * N * nvec * nrhs, (nvec + 1) * vb,
-          [&] { launch_multidot(Vv, ldvv, N, nvec, ww, N, nrhs, N, part, out, st); });
+    S.run("k_dot_partial+k_dot_final", st, 2, 8.0 * NT * nvec, (nvec + 1) * vb,
+          [&] { launch_multidot(Vv, ldvv, nvec, ww, cols, nrhs, maxlen, part, out, st); });
   };
   auto multiaxpy = [&](const double2* Vv, int nvec, const double2* hh, double2* ww, double sign) {
-    S.run("k_multiaxpy", st, 1, 8.0 * N * nvec * nrhs, (nvec + 2) * vb,
-          [&] { launch_multiaxpy(Vv, ldv_vec, N, nvec, hh, ww, N, nrhs, N, sign, st); });
+    S.run("k_multiaxpy", st, 1, 8.0 * NT * nvec, (nvec + 2) * vb,
+          [&] { launch_multiaxpy(Vv, ldv_vec, nvec, hh, ww, cols, nrhs, maxlen, sign, st); });
   };
   auto axpby = [&](const double2* xx, double2* yy, const double2* al, int mode) {
-    S.run("k_axpby", st, 1, 8.0 * N * nrhs, 3 * vb, [&] { launch_axpby_batch(xx, yy, N, nrhs, al, mode, st); });
+    S.run("k_axpby", st, 1, 8.0 * NT, 3 * vb, [&] { launch_axpby_batch(xx, yy, cols, nrhs, maxlen, al, mode, st); });
   };
   auto small = [&](const char* nm, auto&& fn) { S.run(nm, st, 1, 0.0, 0.0, fn); };
 
   auto t0 = std::chrono::steady_clock::now();
-  S.run("k_scale_rhs", st, 1, 6.0 * N * nrhs, 2 * vb, [&] { launch_scale_rhs(X->opA, f, b, nrhs, N, st); });
+  for (const auto& pr : X->probs) {
+    const int64_t o = pr.off1 * nrhs_in;
+    S.run("k_scale_rhs", st, 1, 6.0 * pr.N * nrhs_in, 32.0 * pr.N * nrhs_in,
+          [&] { launch_scale_rhs(pr.opA, f + o, b + o, nrhs_in, pr.N, st); });
+  }
   // ||b||
   std::vector<double> bnorm(nrhs), rel(nrhs, 1.0), hres(nrhs);
   std::vector<int> act(nrhs, 1), its(nrhs, 0), restarts(nrhs, 0), jrh(nrhs, 0);
@@ -1327,7 +1511,7 @@ static void solve_impl(psp_ctx_s* X, const double2* f, double2* x, int nrhs, dou
       double2* Vj = V + (int64_t)j * ldv_vec;
       double2* Zj = Z + (int64_t)j * ldv_vec;
       PSP_CK(cudaMemcpyAsync(Zj, Vj, nW * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-      apply_dispatch(X, Zj, nrhs, st);   // z_j = M^{-1} v_j
+      apply_dispatch(X, Zj, nrhs_in, st);   // z_j = M^{-1} v_j
       ++applies;
       matvec(Zj, w);  // w = A z_j
       // classical Gram-Schmidt, twice
@@ -1436,31 +1620,28 @@ static psp_status fail(psp_status s, const std::string& m) {
   catch (const std::bad_alloc&) { return fail(PSP_ERR_OOM, "host allocation failed"); } \
   catch (const std::exception& e) { return fail(PSP_ERR_STATE, e.what()); }
 
-psp_status psp_setup(const psp_grid* g, const double* c, double omega, int pml_gamma, int panel_depth,
-                     const psp_options* opt, void* stream, psp_handle* out) {
-  if (!out) return fail(PSP_ERR_ARG, "out is NULL");
-  *out = nullptr;
+static psp_status check_options(const psp_options* opt, psp_options* o) {
+  psp_default_options(o);
+  if (opt) *o = *opt;
+  if (o->collect_stats < 0 || o->collect_stats > 2) return fail(PSP_ERR_ARG, "bad collect_stats");
+  if (o->leaf_size < 1 || o->pml_faces < 0 || o->pml_faces > 63 ||
+      (o->precision != PSP_PREC_C128 && o->precision != PSP_PREC_C64) ||
+      (o->aux_mode != PSP_AUX_MOVING_PML && o->aux_mode != PSP_AUX_EXACT) || !(o->alpha >= 0) || !(o->pml_C >= 0))
+    return fail(PSP_ERR_ARG, "bad options");
+  return PSP_OK;
+}
+
+static psp_status check_problem(const psp_grid* g, const double* c, double omega, int pml_gamma, int panel_depth) {
   if (!g || !c) return fail(PSP_ERR_ARG, "grid or c is NULL");
   if (g->nx < 1 || g->ny < 1 || g->nz < 1 || !(g->h > 0)) return fail(PSP_ERR_ARG, "bad grid");
   if ((int64_t)g->nx * g->ny * g->nz > (int64_t)1 << 31) return fail(PSP_ERR_ARG, "grid too large");
   if (!(omega > 0) || pml_gamma < 0 || panel_depth < 1) return fail(PSP_ERR_ARG, "bad omega, gamma or panel depth");
-  psp_options o;
-  psp_default_options(&o);
-  if (opt) o = *opt;
-  if (o.collect_stats < 0 || o.collect_stats > 2) return fail(PSP_ERR_ARG, "bad collect_stats");
-  if (o.leaf_size < 1 || o.pml_faces < 0 || o.pml_faces > 63 || (o.precision != PSP_PREC_C128 && o.precision != PSP_PREC_C64) ||
-      (o.aux_mode != PSP_AUX_MOVING_PML && o.aux_mode != PSP_AUX_EXACT) || !(o.alpha >= 0) || !(o.pml_C >= 0))
-    return fail(PSP_ERR_ARG, "bad options");
-  psp_ctx_s* X = nullptr;
-  try {
-    X = new psp_ctx_s();
-  } catch (...) {
-    return fail(PSP_ERR_OOM, "host allocation failed");
-  }
-  X->nx = g->nx; X->ny = g->ny; X->nz = g->nz; X->h = g->h;
-  X->omega = omega; X->alpha = o.alpha; X->C = o.pml_C;
-  X->gamma = pml_gamma; X->depth = panel_depth;
-  X->pad = o.pad_depth < 0 ? pml_gamma : o.pad_depth;
+  return PSP_OK;
+}
+
+// handle-wide settings from the options
+static void init_options(psp_ctx_s* X, const psp_options& o) {
+  X->alpha = o.alpha; X->C = o.pml_C;
   X->leaf = o.leaf_size; X->prec = o.precision; X->faces = o.pml_faces; X->aux_mode = o.aux_mode;
   X->stats.timing = o.collect_stats != 0;
   X->stats.mode = o.collect_stats;
@@ -1469,11 +1650,82 @@ psp_status psp_setup(const psp_grid* g, const double* c, double omega, int pml_g
   // measured on lens100: complex64 sweeps are fastest at >= 608 tasks per level, complex128 at 304
   X->sweep_level_tasks = o.sweep_level_tasks > 0 ? o.sweep_level_tasks : (o.precision == PSP_PREC_C64 ? 608 : 304);
   X->sweep_ctas_per_sm = o.sweep_ctas_per_sm > 0 ? o.sweep_ctas_per_sm : 8;
+  X->sweep_rhs_group = o.sweep_rhs_group > 0 ? o.sweep_rhs_group : 0;
+  X->temp_budget_elems = o.setup_temp_mb > 0 ? ((int64_t)o.setup_temp_mb << 20) / (o.precision == PSP_PREC_C64 ? 8 : 16) : 0;
+}
+
+static void init_problem(psp_ctx_s* X, const psp_grid* g, double omega, int pml_gamma, int panel_depth,
+                         const psp_options& o) {
+  X->nx = g->nx; X->ny = g->ny; X->nz = g->nz; X->h = g->h;
+  X->omega = omega;
+  X->gamma = pml_gamma; X->depth = panel_depth;
+  X->pad = o.pad_depth < 0 ? pml_gamma : o.pad_depth;
+  init_options(X, o);
+}
+
+psp_status psp_setup(const psp_grid* g, const double* c, double omega, int pml_gamma, int panel_depth,
+                     const psp_options* opt, void* stream, psp_handle* out) {
+  if (!out) return fail(PSP_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  psp_status cs = check_problem(g, c, omega, pml_gamma, panel_depth);
+  if (cs != PSP_OK) return cs;
+  psp_options o;
+  cs = check_options(opt, &o);
+  if (cs != PSP_OK) return cs;
+  psp_ctx_s* X = nullptr;
+  try {
+    X = new psp_ctx_s();
+  } catch (...) {
+    return fail(PSP_ERR_OOM, "host allocation failed");
+  }
+  init_problem(X, g, omega, pml_gamma, panel_depth, o);
   *out = X;
   PSP_TRY
   setup_impl(X, c, (cudaStream_t)stream);
   return PSP_OK;
   PSP_CATCH
+}
+
+psp_status psp_setup_batch(int nprob, const psp_grid* grids, const double* const* c, const double* omega,
+                           const int* pml_gamma, const int* panel_depth, const psp_options* opt, void* stream,
+                           psp_handle* out) {
+  if (!out) return fail(PSP_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (nprob < 1 || !grids || !c || !omega || !pml_gamma || !panel_depth) return fail(PSP_ERR_ARG, "bad batch arguments");
+  int64_t total = 0;
+  for (int q = 0; q < nprob; ++q) {
+    psp_status cs = check_problem(grids + q, c[q], omega[q], pml_gamma[q], panel_depth[q]);
+    if (cs != PSP_OK) return cs;
+    total += (int64_t)grids[q].nx * grids[q].ny * grids[q].nz;
+  }
+  if (total > (int64_t)1 << 31) return fail(PSP_ERR_ARG, "batch too large");
+  psp_options o;
+  psp_status cs = check_options(opt, &o);
+  if (cs != PSP_OK) return cs;
+  psp_ctx_s* B = nullptr;
+  try {
+    B = new psp_ctx_s();
+    for (int q = 0; q < nprob; ++q) {
+      B->subs.emplace_back(new psp_ctx_s());
+      init_problem(B->subs.back().get(), grids + q, omega[q], pml_gamma[q], panel_depth[q], o);
+    }
+  } catch (...) {
+    delete B;
+    return fail(PSP_ERR_OOM, "host allocation failed");
+  }
+  init_problem(B, grids, omega[0], pml_gamma[0], panel_depth[0], o);
+  *out = B;
+  PSP_TRY
+  setup_batch_impl(B, nprob, c, (cudaStream_t)stream);
+  return PSP_OK;
+  PSP_CATCH
+}
+
+psp_status psp_batch_layout(psp_handle X, int* nprob, int64_t* points, int capacity) {
+  if (!X || capacity < 0 || (capacity > 0 && !points)) return fail(PSP_ERR_ARG, "bad layout arguments");
+  if (nprob) *nprob = (int)X->probs.size();
+  for (int q = 0; q < capacity && q < (int)X->probs.size(); ++q) points[q] = X->probs[q].N;
+  return PSP_OK;
 }
 
 psp_status psp_apply(psp_handle X, const double* rhs, double* out, int nrhs, void* stream) {
@@ -1518,8 +1770,11 @@ psp_status psp_matvec(psp_handle X, int which, const double* x, double* y, int n
     yd = X->stage_out.as<double2>();
   }
   if ((const void*)xd == (const void*)yd) return fail(PSP_ERR_ARG, "matvec cannot run in place");
-  X->stats.run("k_matvec", st, 1, 8.0 * 7 * X->N * nrhs, 8.0 * X->N + 32.0 * X->N * nrhs,
-               [&] { launch_matvec(which == 0 ? X->opA : X->opJ, xd, yd, nrhs, X->N, st); });
+  for (const auto& pr : X->probs) {
+    const int64_t o = pr.off1 * nrhs;
+    X->stats.run("k_matvec", st, 1, 8.0 * 7 * pr.N * nrhs, 8.0 * pr.N + 32.0 * pr.N * nrhs,
+                 [&] { launch_matvec(which == 0 ? pr.opA : pr.opJ, xd + o, yd + o, nrhs, pr.N, st); });
+  }
   PSP_CK(cudaGetLastError());
   if (!dev_out) {
     PSP_CK(cudaMemcpyAsync(y, yd, bytes, cudaMemcpyDeviceToHost, st));

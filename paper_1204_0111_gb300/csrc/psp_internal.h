@@ -38,6 +38,8 @@ struct Shape {
   std::vector<int32_t> height;      // leaves 0, parent = 1 + max(children)
   int nlevels = 0;
   std::vector<std::vector<int32_t>> level_sns;
+  std::vector<int32_t> depth;       // root 0, child = parent + 1
+  int ndepths = 0;
   // solve-side pull map: for each front row position p of S u struct(S), up to two
   // offsets (within the per-panel update-vector slab) of children's update entries
   std::vector<int64_t> pull_ptr;    // nsn + 1, = sum (s + u)
@@ -216,6 +218,17 @@ void launch_solve_bwd(const SolveTask* tasks, int ntasks, const SolveCtx<T>& cx,
 // ---- the whole sweep in one cooperative launch ----
 struct SweepStep {      // one panel solve of Alg. 1.5, in order
   int panel, mode;      // mode 0: forward sweep (assign), 1: backward sweep (subtract)
+  int prob;             // problem of a batch (0 for a single problem)
+};
+// per problem of a batch: where its vectors sit and its coupling tables
+struct ProblemSweep {
+  int64_t off1;         // offset of the problem's block in a batched vector, per right-hand side
+  int64_t N;            // points of the problem
+  const double2* s1n;
+  const double2* s2n;
+  const double2* s3h;
+  double inv_h2;
+  int nz, pad_;
 };
 struct PanelSweep {
   int64_t gbase;        // factor slab offset (elements)
@@ -254,20 +267,31 @@ struct SweepArgs {
   unsigned* done_down;
   unsigned* step_done;          // per step completed tasks (zeroed per sweep)
   int* status;                  // status[2] set when a wait gave up
+  // batches of independent problems (nprobs > 1): each problem's steps form their own chain
+  int nprobs;
+  const ProblemSweep* probs;    // per problem; cx's vectors and work vectors are offset per problem
+  const int* step_prev;         // per step: the step it follows (-1: none); nullptr: step - 1
 };
 // returns 0 on success, -1 when a cooperative launch is not possible, else a cudaError_t
 template <typename T>
-int launch_sweep(const SweepArgs<T>& args, size_t per_rhs_bytes, int max_per_sm, cudaStream_t st);
+int launch_sweep(const SweepArgs<T>& args, size_t per_rhs_bytes, int max_per_sm, int rhs_group, cudaStream_t st);
 
 // ---- GMRES helpers (complex128) ----
-// partial[b * (nvec * nrhs) + i * nrhs + r] = sum over block b's slice of conj(V_i[r]) w[r]
-void launch_multidot(const double2* V, int64_t ldv_vec, int64_t ldv_rhs, int nvec, const double2* w, int64_t ldw,
-                     int nrhs, int64_t N, double2* partial, double2* out, cudaStream_t st);
-// w[r] -= sum_i h[i, r] V_i[r]
-void launch_multiaxpy(const double2* V, int64_t ldv_vec, int64_t ldv_rhs, int nvec, const double2* h, double2* w,
-                      int64_t ldw, int nrhs, int64_t N, double sign, cudaStream_t st);
-void launch_axpby_batch(const double2* x, double2* y, int64_t N, int nrhs, const double2* alpha, int alpha_mode,
-                        cudaStream_t st);
+// A block of vectors holds ncol columns (right-hand sides, and problems of a batch); column c of
+// every vector of the block is the span [off, off + len).
+struct ColSpan {
+  int64_t off, len;
+};
+// out[i * ncol + c] = sum_g conj(V_i[c][g]) w[c][g], V_i = V + i * ldv_vec; fixed two-stage order
+void launch_multidot(const double2* V, int64_t ldv_vec, int nvec, const double2* w, const ColSpan* cols, int ncol,
+                     int64_t maxlen, double2* partial, double2* out, cudaStream_t st);
+int multidot_blocks(int64_t maxlen);   // partial blocks per column (size partial as blocks * nvec * ncol)
+// w[c] += sign * sum_i h[i * ncol + c] V_i[c]
+void launch_multiaxpy(const double2* V, int64_t ldv_vec, int nvec, const double2* h, double2* w, const ColSpan* cols,
+                      int ncol, int64_t maxlen, double sign, cudaStream_t st);
+// y[c] = alpha_c x[c] (mode 0), y[c] = x[c] - y[c] (mode 1), y[c] += alpha_c x[c] (mode 2)
+void launch_axpby_batch(const double2* x, double2* y, const ColSpan* cols, int ncol, int64_t maxlen,
+                        const double2* alpha, int alpha_mode, cudaStream_t st);
 
 // Hessenberg least-squares state, one column block per right-hand side
 struct LsqState {

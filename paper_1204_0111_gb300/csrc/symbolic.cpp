@@ -158,6 +158,14 @@ void build_shape(Shape& sh, int nx, int ny, int nz, int leaf) {
   sh.nlevels = hmax + 1;
   sh.level_sns.assign(sh.nlevels, {});
   for (int f = 0; f < nsn; ++f) sh.level_sns[sh.height[f]].push_back(f);
+  // depths (root 0, child = parent + 1; postorder puts every parent after its children)
+  sh.depth.assign(nsn, 0);
+  int dmax = 0;
+  for (int f = nsn - 1; f >= 0; --f) {
+    if (sh.parent[f] >= 0) sh.depth[f] = sh.depth[sh.parent[f]] + 1;
+    dmax = std::max(dmax, (int)sh.depth[f]);
+  }
+  sh.ndepths = dmax + 1;
 
   // per-panel layouts: G blocks (padded to 16 elements) and update vectors
   sh.g_off.assign(nsn, 0);

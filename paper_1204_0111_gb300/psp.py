@@ -33,7 +33,9 @@ class Options(ctypes.Structure):
                 ("leaf_size", ctypes.c_int), ("precision", ctypes.c_int), ("pml_faces", ctypes.c_int),
                 ("aux_mode", ctypes.c_int), ("collect_stats", ctypes.c_int), ("tensor_cores", ctypes.c_int),
                 ("tc_min_dim", ctypes.c_int),
-                ("sweep_level_tasks", ctypes.c_int), ("sweep_ctas_per_sm", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("sweep_level_tasks", ctypes.c_int), ("sweep_ctas_per_sm", ctypes.c_int),
+                ("setup_temp_mb", ctypes.c_int), ("sweep_rhs_group", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 class KernelStat(ctypes.Structure):
@@ -79,6 +81,10 @@ def lib():
         "psp_default_options": (None, [ctypes.POINTER(Options)]),
         "psp_setup": (_I, [ctypes.POINTER(Grid), _P, ctypes.c_double, _I, _I, ctypes.POINTER(Options), _P,
                            ctypes.POINTER(_P)]),
+        "psp_setup_batch": (_I, [_I, ctypes.POINTER(Grid), ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(Options), _P,
+                                 ctypes.POINTER(_P)]),
+        "psp_batch_layout": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_int64), _I]),
         "psp_apply": (_I, [_P, _P, _P, _I, _P]),
         "psp_apply_noalloc": (_I, [_P, _P, _P, _I, _P]),
         "psp_matvec": (_I, [_P, _I, _P, _P, _I, _P]),
@@ -138,25 +144,14 @@ class SweepingPreconditioner:
 
     def __init__(self, c, h, omega, gamma, panel_depth, pad=None, leaf=64, pml_C=4.0, alpha=2 * math.pi,
                  precision="c128", faces=63, mode="moving", stream=None, collect_stats=0, tensor_cores=True,
-                 tc_min_dim=0, sweep_level_tasks=0, sweep_ctas_per_sm=0):
+                 tc_min_dim=0, sweep_level_tasks=0, sweep_ctas_per_sm=0, setup_temp_mb=0, sweep_rhs_group=0):
         nz, ny, nx = c.shape
         self.nx, self.ny, self.nz = nx, ny, nz
         self.N = nx * ny * nz
+        self.points = [self.N]
         g = Grid(nx, ny, nz, float(h))
-        o = Options()
-        lib().psp_default_options(ctypes.byref(o))
-        o.pml_C = float(pml_C)
-        o.alpha = float(alpha)
-        o.pad_depth = -1 if pad is None else int(pad)
-        o.leaf_size = int(leaf)
-        o.precision = {"c128": PREC_C128, "c64": PREC_C64}[precision]
-        o.pml_faces = int(faces)
-        o.aux_mode = {"moving": AUX_MOVING_PML, "exact": AUX_EXACT}[mode]
-        o.collect_stats = int(collect_stats)
-        o.tensor_cores = 1 if tensor_cores else 0
-        o.tc_min_dim = int(tc_min_dim)
-        o.sweep_level_tasks = int(sweep_level_tasks)
-        o.sweep_ctas_per_sm = int(sweep_ctas_per_sm)
+        o = _options(pad, leaf, pml_C, alpha, precision, faces, mode, collect_stats, tensor_cores, tc_min_dim,
+                     sweep_level_tasks, sweep_ctas_per_sm, setup_temp_mb, sweep_rhs_group)
         cp, n = _ptr_and_len(c, complex_=False)
         if n != self.N:
             raise ValueError("c has the wrong size")
@@ -164,6 +159,9 @@ class SweepingPreconditioner:
         h_ = _P()
         st = lib().psp_setup(ctypes.byref(g), cp, float(omega), int(gamma), int(panel_depth), ctypes.byref(o),
                              _stream(stream), ctypes.byref(h_))
+        self._finish(h_, st)
+
+    def _finish(self, h_, st):
         self._h = h_
         if st != 0:
             msg = lib().psp_last_error().decode()
@@ -238,6 +236,93 @@ class SweepingPreconditioner:
         out = np.zeros(((s.value + u.value) * s.value,), dtype=np.complex128)
         _check(lib().psp_export_front(self._h, int(panel), int(sn), out.ctypes.data, ctypes.byref(s), ctypes.byref(u)))
         return out.reshape(s.value, s.value + u.value).T, s.value, u.value
+
+
+class SweepingPreconditionerBatch(SweepingPreconditioner):
+    """Handle over psp_setup_batch: independent problems factored, swept and solved together.
+
+    ``problems`` is a list of dicts with keys c (nz, ny, nx), h, omega, gamma, panel_depth; the other
+    keyword arguments are the shared options of SweepingPreconditioner.  Vectors are batched blocks
+    (see pack / unpack): problem q's N_q x nrhs block after problem q-1's."""
+
+    def __init__(self, problems, pad=None, leaf=64, pml_C=4.0, alpha=2 * math.pi, precision="c128", faces=63,
+                 mode="moving", stream=None, collect_stats=0, tensor_cores=True, tc_min_dim=0, sweep_level_tasks=0,
+                 sweep_ctas_per_sm=0, setup_temp_mb=0, sweep_rhs_group=0):
+        n = len(problems)
+        grids = (Grid * n)()
+        cs = (_P * n)()
+        om = (ctypes.c_double * n)()
+        ga = (_I * n)()
+        de = (_I * n)()
+        self._keep = []
+        self.points = []
+        for q, pr in enumerate(problems):
+            c = pr["c"]
+            nz, ny, nx = c.shape
+            grids[q] = Grid(nx, ny, nz, float(pr["h"]))
+            cp, cnt = _ptr_and_len(c, complex_=False)
+            if cnt != nx * ny * nz:
+                raise ValueError("c has the wrong size")
+            cs[q] = cp
+            om[q] = float(pr["omega"])
+            ga[q] = int(pr["gamma"])
+            de[q] = int(pr["panel_depth"])
+            self._keep.append(c)
+            self.points.append(nx * ny * nz)
+        self.N = sum(self.points)
+        o = _options(pad, leaf, pml_C, alpha, precision, faces, mode, collect_stats, tensor_cores, tc_min_dim,
+                     sweep_level_tasks, sweep_ctas_per_sm, setup_temp_mb, sweep_rhs_group)
+        h_ = _P()
+        st = lib().psp_setup_batch(n, grids, cs, om, ga, de, ctypes.byref(o), _stream(stream), ctypes.byref(h_))
+        self._finish(h_, st)
+        if st == 0:
+            m = _I()
+            pts = (ctypes.c_int64 * n)()
+            _check(lib().psp_batch_layout(self._h, ctypes.byref(m), pts, n))
+            assert m.value == n and list(pts) == self.points
+
+    def offsets(self, nrhs):
+        """Start of each problem's block in a batched vector block with nrhs right-hand sides."""
+        out, o = [], 0
+        for n in self.points:
+            out.append(o)
+            o += n * nrhs
+        return out
+
+    def pack(self, blocks):
+        """[(nrhs, N_q) arrays or tensors] -> one flat batched block."""
+        try:
+            import torch
+            if isinstance(blocks[0], torch.Tensor):
+                return torch.cat([b.reshape(-1) for b in blocks])
+        except ImportError:
+            pass
+        return np.concatenate([np.asarray(b).reshape(-1) for b in blocks])
+
+    def unpack(self, flat, nrhs):
+        """Flat batched block -> [(nrhs, N_q) views]."""
+        return [flat[o:o + n * nrhs].reshape(nrhs, n) for o, n in zip(self.offsets(nrhs), self.points)]
+
+
+def _options(pad, leaf, pml_C, alpha, precision, faces, mode, collect_stats, tensor_cores, tc_min_dim,
+             sweep_level_tasks, sweep_ctas_per_sm, setup_temp_mb, sweep_rhs_group=0):
+    o = Options()
+    lib().psp_default_options(ctypes.byref(o))
+    o.pml_C = float(pml_C)
+    o.alpha = float(alpha)
+    o.pad_depth = -1 if pad is None else int(pad)
+    o.leaf_size = int(leaf)
+    o.precision = {"c128": PREC_C128, "c64": PREC_C64}[precision]
+    o.pml_faces = int(faces)
+    o.aux_mode = {"moving": AUX_MOVING_PML, "exact": AUX_EXACT}[mode]
+    o.collect_stats = int(collect_stats)
+    o.tensor_cores = 1 if tensor_cores else 0
+    o.tc_min_dim = int(tc_min_dim)
+    o.sweep_level_tasks = int(sweep_level_tasks)
+    o.sweep_ctas_per_sm = int(sweep_ctas_per_sm)
+    o.setup_temp_mb = int(setup_temp_mb)
+    o.sweep_rhs_group = int(sweep_rhs_group)
+    return o
 
 
 def parse_symbolic(buf):

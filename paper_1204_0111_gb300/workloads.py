@@ -138,8 +138,39 @@ def cube_lens(n=100, gamma=8, panel_depth=4, pad=None, ppw=10.0, leaf=64):
                     gamma if pad is None else pad, leaf, sources=[(0.5, 0.5, 0.1)])
 
 
-def cube_layered(n=200, gamma=10, panel_depth=4, pad=None, ppw=10.0, leaf=64, seed=3):
+def cube_layered(n=200, gamma=10, panel_depth=4, pad=None, ppw=10.0, leaf=64, seed=3, pml_C=8.0):
+    """Layered and faulted model on n^3, shot at (0.5, 0.5, 0.1).  PML amplitude 8: on this
+    high-contrast model the sweep needs a stronger PML than the smooth ones (oracle, n = 40: 34
+    iterations at C = 4, 19 at C = 8)."""
     h = 1.0 / (n + 1)
     c = velocity_layered_faulted(n, n, n, h, seed=seed)
     return Workload(f"layered{n}", n, c, h, omega_for_ppw(float(c.min()), ppw, h), gamma, panel_depth,
-                    gamma if pad is None else pad, leaf, sources=[(0.5, 0.5, 0.1)])
+                    gamma if pad is None else pad, leaf, pml_C=pml_C, sources=[(0.5, 0.5, 0.1)])
+
+
+def top_shots(n, h, gamma, nx_shots, ny_shots, lo=0.2, hi=0.8):
+    """Shot positions on an nx_shots x ny_shots grid of (x, y) in [lo, hi]^2, in the first plane
+    below the top PML (plane n - gamma - 1, at z = (n - gamma) h)."""
+    xs = np.linspace(lo, hi, nx_shots)
+    ys = np.linspace(lo, hi, ny_shots)
+    z = (n - gamma) * h
+    return [(float(x), float(y), z) for y in ys for x in xs]
+
+
+def cube_smooth(k, gamma=8, panel_depth=4, pad=None, ppw=10.0, leaf=64, base_seed=400):
+    """Problem k of the batch of independent problems: n_k = 40 + 8 (k mod 11), smooth random
+    velocity (seed base_seed + k), 8 shots on a 4 x 2 grid below the top PML."""
+    n = 40 + 8 * (k % 11)
+    h = 1.0 / (n + 1)
+    c = velocity_smooth_random(n, n, n, h, seed=base_seed + k)
+    return Workload(f"smooth{n}_k{k}", n, c, h, omega_for_ppw(float(c.min()), ppw, h), gamma, panel_depth,
+                    gamma if pad is None else pad, leaf, sources=top_shots(n, h, gamma, 4, 2))
+
+
+def cube_salt(n=256, gamma=12, panel_depth=8, pad=8, ppw=8.0, leaf=64, shots=(8, 4)):
+    """Salt body in a depth gradient on n^3, 8 points per wavelength, shots on a grid below the top
+    PML, GMRES(30)."""
+    h = 1.0 / (n + 1)
+    c = velocity_salt(n, n, n, h)
+    return Workload(f"salt{n}", n, c, h, omega_for_ppw(float(c.min()), ppw, h), gamma, panel_depth,
+                    gamma if pad is None else pad, leaf, sources=top_shots(n, h, gamma, *shots), k=30)

@@ -51,3 +51,22 @@ def test_bad_arguments_are_rejected_before_any_device_call(L):
     assert st == 1
     assert L.psp_apply(None, None, None, 1, None) == 1
     assert L.psp_destroy(None) == 0
+
+
+def test_batch_arguments_are_rejected_before_any_device_call(L):
+    h = ctypes.c_void_p()
+    grids = (psp.Grid * 2)(psp.Grid(4, 4, 4, 0.2), psp.Grid(4, 0, 4, 0.2))
+    c = (ctypes.c_double * 64)()
+    cs = (ctypes.c_void_p * 2)(ctypes.cast(c, ctypes.c_void_p), ctypes.cast(c, ctypes.c_void_p))
+    om = (ctypes.c_double * 2)(1.0, 1.0)
+    ga = (ctypes.c_int * 2)(2, 2)
+    de = (ctypes.c_int * 2)(2, 2)
+    assert L.psp_setup_batch(0, grids, cs, om, ga, de, None, None, ctypes.byref(h)) == 1 and h.value is None
+    assert L.psp_setup_batch(2, grids, cs, om, ga, de, None, None, ctypes.byref(h)) == 1   # second grid is empty
+    assert b"grid" in L.psp_last_error()
+    grids[1] = psp.Grid(4, 4, 4, 0.2)
+    de[1] = 0
+    assert L.psp_setup_batch(2, grids, cs, om, ga, de, None, None, ctypes.byref(h)) == 1
+    assert L.psp_setup_batch(2, grids, None, om, ga, de, None, None, ctypes.byref(h)) == 1
+    n = ctypes.c_int()
+    assert L.psp_batch_layout(None, ctypes.byref(n), None, 0) == 1

@@ -147,3 +147,14 @@ def test_cube_constant_20_converges_in_few_iterations():
     b = dz.rhs_scale(p) * w.rhs()[0]
     x, it, rr = gm.gmres(lambda v: A @ v, P.apply, b, tol=1e-5, k=20, maxit=200)
     assert rr < 1e-5 and it <= 20
+
+
+def test_apply_is_complex_symmetric():
+    # Alg. 1.5 applies L^{-T} D^{-1} L^{-1} with L's blocks J_{i+1,i} T_i and D's blocks T_i^{-1}; each T_i
+    # is a diagonal block of H_i^{-1} with H_i = H_i^T (§1.1), and J_{i,i+1} = J_{i+1,i}^T, so the whole
+    # preconditioner is complex symmetric (transpose, not conjugate transpose)
+    p = _prob(n=5, nz=11, seed=4)
+    P = sw.SweepingPreconditioner(p, 2, pad=2, leaf=8)
+    M = P.apply(np.eye(p.N, dtype=np.complex128)).T
+    assert np.linalg.norm(M - M.T) / np.linalg.norm(M) < 1e-12
+    assert np.linalg.norm(M - M.conj().T) / np.linalg.norm(M) > 1e-3
