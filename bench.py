@@ -182,7 +182,8 @@ def traffic_from_profiles(kernel):
     return None
 
 
-SETUP_KERNELS = ("k_assemble", "k_diag_ldlt", "k_panel_right", "k_panel_left", "k_gemm", "k_copy_linv", "k_tc_gemm")
+SETUP_KERNELS = ("k_assemble", "k_diag_ldlt", "k_panel_right", "k_panel_left", "k_gemm", "k_copy_linv", "k_tc_gemm",
+                 "k_tc_pack", "k_scale_zd")
 SWEEP_KERNELS = ("k_sweep", "k_solve_fwd", "k_solve_bwd")
 
 

@@ -83,7 +83,7 @@ typedef struct {
   int tc_min_dim;     /* complex64 path: fronts with s >= tc_min_dim and u >= tc_min_dim take the tensor
                          cores, the others CUDA cores; <= 0 selects the default (64) */
   int sweep_level_tasks; /* sweep schedule: tasks a tree level is split into at least (row / column
-                            blocks of 8..64); <= 0 selects the default (608 complex64, 304 complex128) */
+                            blocks of 8..64); <= 0 selects the default (608) */
   int sweep_ctas_per_sm; /* sweep schedule: resident CTAs per SM of the persistent sweep (capped by
                             occupancy); <= 0 selects the default (8) */
   int setup_temp_mb;   /* cap, in MiB, on the per-front temporaries of one batch of fronts during setup

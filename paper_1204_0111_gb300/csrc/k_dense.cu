@@ -134,7 +134,9 @@ __global__ void __launch_bounds__(64) k_panel_left(const FrontTask<T>* __restric
 }
 
 // ---------------------------------------------------------------------------
-// Batched complex GEMM, one 64 x 64 output tile per CTA (16 x 16 threads, 4 x 4 each).
+// Batched complex GEMM, one 64 x 64 output tile per CTA (16 x 16 threads, 4 x 4 each; thread
+// (tx, ty) owns rows ty + 16 a and columns tx + 16 b, so each 16 x 16 block (a, b) is spread over
+// the whole CTA and can be skipped as a unit).
 // Complex products use three real multiplications (Gauss): with the pre-sums ar + ai and
 // br + bi staged in shared memory, t1 += ar br, t2 += ai bi, t3 += (ar + ai)(br + bi), and at the
 // end re = t1 - t2, im = t3 - t1 - t2.  Three FMAs per complex MAC instead of four.
@@ -155,7 +157,7 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTask<T>* __restrict__ ta
 #pragma unroll
     for (int b = 0; b < 4; ++b) t1[a][b] = t2[a][b] = t3[a][b] = R(0);
 
-  const bool bnn = tk.flags & GF_B_NN;
+  const bool bnn = tk.flags & GF_B_NN, lower = tk.flags & GF_C_LOWER;
   for (int k0 = 0; k0 < tk.k; k0 += GK) {
     // A chunk: 64 rows x GK k
     for (int e = threadIdx.x; e < GT * GK; e += 256) {
@@ -190,33 +192,67 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTask<T>* __restrict__ ta
       Bs[kk][j] = v.x + v.y;
     }
     __syncthreads();
+    if constexpr (sizeof(R) == 4) {
+      // single precision: the FP32 pipe is fast enough that issue slots, not FMAs, bound the
+      // loop, so all 16 blocks run, with operands kept in registers across the block row
 #pragma unroll
-    for (int kk = 0; kk < GK; ++kk) {
-      R ar[4], ai[4], as[4], br[4], bi[4], bs[4];
+      for (int kk = 0; kk < GK; ++kk) {
+        R ar[4], ai[4], as[4], br[4], bi[4], bs[4];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        ar[a] = Ar[kk][ty + 16 * a];
-        ai[a] = Ai[kk][ty + 16 * a];
-        as[a] = As[kk][ty + 16 * a];
-      }
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        br[b] = Br[kk][tx + 16 * b];
-        bi[b] = Bi[kk][tx + 16 * b];
-        bs[b] = Bs[kk][tx + 16 * b];
-      }
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < 4; ++a) {
+          ar[a] = Ar[kk][ty + 16 * a];
+          ai[a] = Ai[kk][ty + 16 * a];
+          as[a] = As[kk][ty + 16 * a];
+        }
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-          t1[a][b] = fma(ar[a], br[b], t1[a][b]);
-          t2[a][b] = fma(ai[a], bi[b], t2[a][b]);
-          t3[a][b] = fma(as[a], bs[b], t3[a][b]);
+          br[b] = Br[kk][tx + 16 * b];
+          bi[b] = Bi[kk][tx + 16 * b];
+          bs[b] = Bs[kk][tx + 16 * b];
         }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            t1[a][b] = fma(ar[a], br[b], t1[a][b]);
+            t2[a][b] = fma(ai[a], bi[b], t2[a][b]);
+            t3[a][b] = fma(as[a], bs[b], t3[a][b]);
+          }
+      }
+      __syncthreads();
+      continue;
+    }
+    // double precision (2 DFMA per clock per SM): only the 16 x 16 blocks (a, b) of the tile that
+    // carry work in this k-chunk run: rows and columns inside the task, the lower triangle of a
+    // diagonal tile, the non-zero part of a triangular B.  The tests are uniform over the CTA, so
+    // skipped blocks cost no FP64 issue slots.
+    bool bact[4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      bool on = 16 * b < tk.n;
+      if (tk.flags & GF_B_UNIT_LOWER_NT) on = on && (k0 + tk.kg0 <= 16 * b + 15 + tk.ng0);
+      if (tk.flags & GF_B_UNIT_LOWER_NN) on = on && (k0 + GK - 1 + tk.kg0 >= 16 * b + tk.ng0);
+      bact[b] = on;
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      if (16 * a >= tk.m) continue;
+#pragma unroll
+      for (int kk = 0; kk < GK; ++kk) {
+        const R ar = Ar[kk][ty + 16 * a], ai = Ai[kk][ty + 16 * a], as = As[kk][ty + 16 * a];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          if (!bact[b] || (lower && b > a)) continue;
+          const R br = Br[kk][tx + 16 * b], bi = Bi[kk][tx + 16 * b], bs = Bs[kk][tx + 16 * b];
+          t1[a][b] = fma(ar, br, t1[a][b]);
+          t2[a][b] = fma(ai, bi, t2[a][b]);
+          t3[a][b] = fma(as, bs, t3[a][b]);
+        }
+      }
     }
     __syncthreads();
   }
-  const bool neg = tk.flags & GF_NEG, beta0 = tk.flags & GF_BETA0, lower = tk.flags & GF_C_LOWER;
+  const bool neg = tk.flags & GF_NEG, beta0 = tk.flags & GF_BETA0;
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
     const int i = ty + 16 * a;
@@ -247,6 +283,22 @@ __global__ void __launch_bounds__(256) k_copy_linv(const FrontTask<T>* __restric
       ft.G[(int64_t)c * ld + r] = ft.W[(int64_t)c * ft.s + r];
 }
 
+// ZD = Z D^{-1}, column by column, once per front: the Schur update and the M_BL product then
+// read plain operands in every tile instead of dividing each element by its pivot again
+template <typename T>
+__global__ void __launch_bounds__(256) k_scale_zd(const FrontTask<T>* __restrict__ fronts,
+                                                  const ColTask* __restrict__ tasks) {
+  const ColTask tk = tasks[blockIdx.x];
+  const FrontTask<T> ft = fronts[tk.front];
+  const int ld = ft.s + ft.u;
+  for (int c = tk.c0; c < tk.c1; ++c) {
+    const T dinv = cdiv(CplxTraits<T>::one(), ft.G[(int64_t)c * (ld + 1)]);
+    const T* z = ft.Z + (int64_t)c * ft.u;
+    T* zd = ft.ZD + (int64_t)c * ft.u;
+    for (int r = threadIdx.x; r < ft.u; r += blockDim.x) zd[r] = cmul(z[r], dinv);
+  }
+}
+
 template <typename T>
 void launch_diag_ldlt(const FrontTask<T>* fronts, const int* list, int nlist, int kb, double tiny, int* status,
                       cudaStream_t st) {
@@ -268,13 +320,18 @@ template <typename T>
 void launch_copy_linv(const FrontTask<T>* fronts, const ColTask* tasks, int ntasks, cudaStream_t st) {
   if (ntasks > 0) k_copy_linv<T><<<ntasks, 256, 0, st>>>(fronts, tasks);
 }
+template <typename T>
+void launch_scale_zd(const FrontTask<T>* fronts, const ColTask* tasks, int ntasks, cudaStream_t st) {
+  if (ntasks > 0) k_scale_zd<T><<<ntasks, 256, 0, st>>>(fronts, tasks);
+}
 
 #define PSP_INST(T)                                                                                           \
   template void launch_diag_ldlt<T>(const FrontTask<T>*, const int*, int, int, double, int*, cudaStream_t);    \
   template void launch_panel_right<T>(const FrontTask<T>*, const ColTask*, int, int, cudaStream_t);            \
   template void launch_panel_left<T>(const FrontTask<T>*, const ColTask*, int, int, cudaStream_t);             \
   template void launch_gemm<T>(const GemmTask<T>*, int, cudaStream_t);                                         \
-  template void launch_copy_linv<T>(const FrontTask<T>*, const ColTask*, int, cudaStream_t);
+  template void launch_copy_linv<T>(const FrontTask<T>*, const ColTask*, int, cudaStream_t);                 \
+  template void launch_scale_zd<T>(const FrontTask<T>*, const ColTask*, int, cudaStream_t);
 PSP_INST(double2)
 PSP_INST(float2)
 #undef PSP_INST

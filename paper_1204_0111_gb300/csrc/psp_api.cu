@@ -315,8 +315,8 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
   auto packed_elems = [&](int64_t s_, int64_t u_) {   // F_BL, Z D^-1, Z (u x s) and two inv(L) (s x s)
     return TBLK * (3 * nrb(u_) * nkb16(s_) + 2 * nrb(s_) * nkb16(s_));
   };
-  auto front_temp = [&](int64_t s_, int64_t u_) {     // W (s x s), Z (u x s), packed operands
-    return pad16(s_ * s_) + pad16(u_ * s_) + (use_tc(s_, u_) ? packed_elems(s_, u_) : 0);
+  auto front_temp = [&](int64_t s_, int64_t u_) {     // W (s x s), Z (u x s), Z D^-1 or packed operands
+    return pad16(s_ * s_) + pad16(u_ * s_) + (use_tc(s_, u_) ? packed_elems(s_, u_) : pad16(u_ * s_));
   };
   int64_t arena[2] = {0, 0}, temp_level_max = 0, temp_front_max = 16;
   for (int lv = 0; lv < L; ++lv) {
@@ -396,7 +396,7 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
   std::vector<unsigned char*> packs;     // per front: base of its packed operands (tensor-core fronts)
   std::vector<TcPackTask> ptasks;
   std::vector<TcGemmTask> ttasks;
-  enum Kind { ASSEMBLE, DIAG, PRIGHT, PLEFT, GEMM, COPY, TCGEMM, TCPACK };
+  enum Kind { ASSEMBLE, DIAG, PRIGHT, PLEFT, GEMM, COPY, TCGEMM, TCPACK, SCALE };
   struct Launch {
     Kind kind;
     int64_t front_off;
@@ -440,15 +440,28 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
       toff += pad16((int64_t)ft.s * ft.s);
       ft.Z = tbase + toff;
       toff += pad16((int64_t)ft.u * ft.s);
-      fronts.push_back(ft);
+      ft.ZD = nullptr;
       packs.push_back(nullptr);
       if (use_tc(ft.s, ft.u)) {
         packs.back() = reinterpret_cast<unsigned char*>(tbase + toff);
         toff += packed_elems(ft.s, ft.u);
+      } else {
+        ft.ZD = tbase + toff;
+        toff += pad16((int64_t)ft.u * ft.s);
       }
+      fronts.push_back(ft);
       smax = std::max(smax, ft.s);
     }
     const int nf = (int)(fronts.size() - f0);
+    // GEMM tiles are emitted largest front first: a launch's tiles start in order, one CTA per SM,
+    // so the long tiles start early and the short ones fill the tail
+    std::vector<int> ord(nf);
+    for (int f = 0; f < nf; ++f) ord[f] = f;
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
+      const auto& a = fronts[f0 + x];
+      const auto& b = fronts[f0 + y];
+      return (double)a.s * (a.s + a.u) * (a.s + a.u) > (double)b.s * (b.s + b.u) * (b.s + b.u);
+    });
     // assembly: column chunks of 32 over the full front width
     {
       const int64_t c0 = (int64_t)ctasks.size();
@@ -512,7 +525,7 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
       }
       launches.push_back(lp);
       const int64_t g0 = (int64_t)gtasks.size();
-      for (int f = 0; f < nf; ++f) {
+      for (int f : ord) {
         const auto& ft = fronts[f0 + f];
         if (ft.s <= o + nb) continue;
         const int ld = ft.s + ft.u;
@@ -547,7 +560,9 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
             g.m = std::min(64, ft.s - ti);
             g.n = std::min(64, cend - tj);
             g.k = bs;
-            g.flags = GF_NEG | GF_B_NN;
+            g.kg0 = o;              // W is unit lower: B(n, k) = W[o + k, tj + n] vanishes for o + k < tj + n
+            g.ng0 = tj;
+            g.flags = GF_NEG | GF_B_NN | GF_B_UNIT_LOWER_NN;
             gtasks.push_back(g);
           }
       }
@@ -597,16 +612,14 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
           GemmTask<T> g{};
           g.C = ft.U + (int64_t)tj * ft.u + ti;
           g.ldc = ft.u;
-          g.A = ft.Z + ti;
+          g.A = ft.ZD + ti;
           g.lda = ft.u;
           g.B = ft.Z + tj;
           g.ldb = ft.u;
-          g.d = ft.G;
-          g.ldd = ld + 1;
           g.m = std::min(64, ft.u - ti);
           g.n = std::min(64, ft.u - tj);
           g.k = ft.s;
-          g.flags = GF_D_DIV | GF_NEG | (ti == tj ? GF_C_LOWER : 0);
+          g.flags = GF_NEG | (ti == tj ? GF_C_LOWER : 0);
           gtasks.push_back(g);
         }
       for (int tj = 0; tj < ft.s; tj += 64)
@@ -614,10 +627,8 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
           GemmTask<T> g{};
           g.C = ft.G + (int64_t)tj * ld + ft.s + ti;
           g.ldc = ld;
-          g.A = ft.Z + (int64_t)tj * ft.u + ti;   // A(i, k) = Z[ti + i, tj + k]
+          g.A = ft.ZD + (int64_t)tj * ft.u + ti;  // A(i, k) = (Z D^-1)[ti + i, tj + k]
           g.lda = ft.u;
-          g.d = ft.G + (int64_t)tj * (ld + 1);
-          g.ldd = ld + 1;
           g.B = ft.G + (int64_t)tj * ld + tj;     // B(n, k) = Linv[tj + k, tj + n]
           g.ldb = ld;
           g.m = std::min(64, ft.u - ti);
@@ -625,7 +636,7 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
           g.k = ft.s - tj;
           g.kg0 = tj;
           g.ng0 = tj;
-          g.flags = GF_BETA0 | GF_D_DIV | GF_B_NN | GF_B_UNIT_LOWER_NN;
+          g.flags = GF_BETA0 | GF_B_NN | GF_B_UNIT_LOWER_NN;
           gtasks.push_back(g);
         }
     };
@@ -662,10 +673,23 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
       (void)fl;
     };
     for (int phase = 0; phase < 2; ++phase) {
+      if (phase == 1) {
+        // Z D^{-1} of the CUDA-core fronts, once per front
+        const int64_t c0 = (int64_t)ctasks.size();
+        Launch ls{SCALE, f0, c0, 0, 0};
+        for (int f : ord) {
+          const auto& ft = fronts[f0 + f];
+          if (ft.u == 0 || packs[f0 + f]) continue;
+          for (int c = 0; c < ft.s; c += 16) ctasks.push_back({f, c, std::min(c + 16, ft.s)});
+          ls.bytes += 2.0 * es * ft.u * ft.s;
+        }
+        ls.count = (int)(ctasks.size() - c0);
+        if (ls.count > 0) launches.push_back(ls);
+      }
       // CUDA-core fronts
       {
         const int64_t g0 = (int64_t)gtasks.size();
-        for (int f = 0; f < nf; ++f) {
+        for (int f : ord) {
           const auto& ft = fronts[f0 + f];
           if (ft.u == 0 || packs[f0 + f]) continue;
           if (phase == 0) emit_z(ft);
@@ -680,7 +704,7 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
       // tensor-core fronts: pack, then tiles
       const int64_t p0 = (int64_t)ptasks.size(), t0 = (int64_t)ttasks.size();
       double tflops = 0;
-      for (int f = 0; f < nf; ++f) {
+      for (int f : ord) {
         const auto& ft = fronts[f0 + f];
         if (ft.u == 0 || !packs[f0 + f]) continue;
         const int ld = ft.s + ft.u;
@@ -778,7 +802,7 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
   int* status = X->d_status.as<int>();
   PSP_CK(cudaMemsetAsync(status, 0, 4 * sizeof(int), st));
   static const char* names[] = {"k_assemble", "k_diag_ldlt", "k_panel_right", "k_panel_left", "k_gemm", "k_copy_linv",
-                                "k_tc_gemm", "k_tc_pack"};
+                                "k_tc_gemm", "k_tc_pack", "k_scale_zd"};
   for (const auto& l : launches) {
     if (l.count <= 0) continue;
     X->stats.run(names[l.kind], st, 1, l.flops, l.bytes, [&] {
@@ -794,6 +818,7 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
         case COPY: launch_copy_linv<T>(F + l.front_off, CT + l.off, l.count, st); break;
         case TCGEMM: launch_tc_gemm(d_ttasks.as<TcGemmTask>() + l.off, l.count, status, st); break;
         case TCPACK: launch_tc_pack(d_ptasks.as<TcPackTask>() + l.off, l.count, st); break;
+        case SCALE: launch_scale_zd<T>(F + l.front_off, CT + l.off, l.count, st); break;
       }
     }, true);
   }
@@ -1647,8 +1672,8 @@ static void init_options(psp_ctx_s* X, const psp_options& o) {
   X->stats.mode = o.collect_stats;
   X->use_tc = o.tensor_cores != 0;
   X->tc_min_dim = o.tc_min_dim > 0 ? o.tc_min_dim : 64;
-  // measured on lens100: complex64 sweeps are fastest at >= 608 tasks per level, complex128 at 304
-  X->sweep_level_tasks = o.sweep_level_tasks > 0 ? o.sweep_level_tasks : (o.precision == PSP_PREC_C64 ? 608 : 304);
+  // measured on lens100: both precisions' sweeps are fastest at about 608 tasks per level
+  X->sweep_level_tasks = o.sweep_level_tasks > 0 ? o.sweep_level_tasks : 608;
   X->sweep_ctas_per_sm = o.sweep_ctas_per_sm > 0 ? o.sweep_ctas_per_sm : 8;
   X->sweep_rhs_group = o.sweep_rhs_group > 0 ? o.sweep_rhs_group : 0;
   X->temp_budget_elems = o.setup_temp_mb > 0 ? ((int64_t)o.setup_temp_mb << 20) / (o.precision == PSP_PREC_C64 ? 8 : 16) : 0;

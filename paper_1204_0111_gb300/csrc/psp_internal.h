@@ -130,6 +130,7 @@ struct FrontTask {
   T* U;        // u x u update (F_BR), ld = u; nullptr for the root
   T* W;        // s x s work: inv(L_TL) under construction
   T* Z;        // u x s work: F_BL L^{-T}
+  T* ZD;       // u x s work: Z D^{-1} (fronts whose products run on CUDA cores; else nullptr)
   int s, u;
   int panel, sn;
   int64_t gfid;
@@ -185,6 +186,8 @@ int64_t tc_block_bytes();
 int tc_gemm_tile();
 template <typename T>
 void launch_copy_linv(const FrontTask<T>* fronts, const ColTask* tasks, int ntasks, cudaStream_t st);
+template <typename T>
+void launch_scale_zd(const FrontTask<T>* fronts, const ColTask* tasks, int ntasks, cudaStream_t st);
 
 // ---- multifrontal solve of one panel (Alg. 1.3 inside Alg. 1.5) ----
 struct SolveTask {  // rows [r0, r1) of front sn (forward) or columns [r0, r1) of S (backward)
