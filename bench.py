@@ -272,9 +272,12 @@ def gpu_main(a):
     u_dev = torch.zeros_like(f_dev)
     stream = torch.cuda.current_stream(dev)
 
+    sched = {}
+
     def step(precision="c128", stats=0):
         P = psp.SweepingPreconditioner(c_dev, w.h, w.omega, w.gamma, w.panel_depth, pad=w.pad, leaf=w.leaf,
-                                       pml_C=w.pml_C, alpha=w.alpha, precision=precision, collect_stats=stats)
+                                       pml_C=w.pml_C, alpha=w.alpha, precision=precision, collect_stats=stats,
+                                       **sched.get(precision, {}))
         info = P.solve(f_dev, u_dev, tol=w.tol, k=w.k, maxit=400)
         st = P.stats() if stats else None
         fb = P.info()["factor_bytes"]
@@ -285,6 +288,16 @@ def gpu_main(a):
         if world > 1:
             dist.barrier()
 
+    # sweep schedule from the library's autotuner, once per precision, before any timed work
+    tuning = {}
+    for prec in ("c128",) + (() if a.no_mixed else ("c64",)):
+        P = psp.SweepingPreconditioner(c_dev, w.h, w.omega, w.gamma, w.panel_depth, pad=w.pad, leaf=w.leaf,
+                                       pml_C=w.pml_C, alpha=w.alpha, precision=prec)
+        t = P.tune_sweep(nrhs=nrhs, reps=3)
+        P.close()
+        tuning[prec] = t
+        sched[prec] = {"sweep_level_tasks": t["sweep_level_tasks"], "sweep_ctas_per_sm": t["sweep_ctas_per_sm"],
+                       "sweep_rhs_group": t["sweep_rhs_group"]}
     for _ in range(a.warmup):
         step()
     torch.cuda.synchronize()
@@ -330,7 +343,7 @@ def gpu_main(a):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         P = psp.SweepingPreconditioner(c_pin, w.h, w.omega, w.gamma, w.panel_depth, pad=w.pad, leaf=w.leaf,
-                                       pml_C=w.pml_C, alpha=w.alpha)
+                                       pml_C=w.pml_C, alpha=w.alpha, **sched["c128"])
         P.solve(f_pin, u_pin, tol=w.tol, k=w.k, maxit=400)
         P.close()
     torch.cuda.synchronize()
@@ -396,7 +409,7 @@ def gpu_main(a):
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": config_dict(w, nrhs, {"parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches // a.steps,
-                "clocks": clk, "detail": detail, "mixed": mixed}
+                "clocks": clk, "detail": dict(detail, sweep_tuning=tuning), "mixed": mixed}
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -457,8 +470,14 @@ def batch_main(a):
     u_dev = torch.zeros_like(f_dev)
     stream = torch.cuda.current_stream(dev)
 
+    B = psp.SweepingPreconditionerBatch(prs, precision="c64")
+    tuning = B.tune_sweep(nrhs=nrhs, reps=2)     # the library's autotuner, before any timed work
+    B.close()
+    sched = {"sweep_level_tasks": tuning["sweep_level_tasks"], "sweep_ctas_per_sm": tuning["sweep_ctas_per_sm"],
+             "sweep_rhs_group": tuning["sweep_rhs_group"]}
+
     def step(stats=0, problems=prs, f=f_dev, u=u_dev):
-        B = psp.SweepingPreconditionerBatch(problems, precision="c64", collect_stats=stats)
+        B = psp.SweepingPreconditionerBatch(problems, precision="c64", collect_stats=stats, **sched)
         info = B.solve(f, u, tol=1e-5, k=20, maxit=400)
         st = B.stats() if stats else None
         fb = B.info()["factor_bytes"]
@@ -518,7 +537,7 @@ def batch_main(a):
                     "d2h_bytes_per_step": int(u_pin.numel() * 16)},
             "gpu_launches": int(sum(v["launches"] for v in agg.values()) // a.steps), "clocks": clk,
             "detail": {"gmres_iters": infos[-1]["iterations"], "relres": max(i["relres_max"] for i in infos),
-                       "applies": infos[-1]["applies"], "factor_bytes": fbytes,
+                       "applies": infos[-1]["applies"], "factor_bytes": fbytes, "sweep_tuning": tuning,
                        "host_setup_ms": {k[5:]: v["total_ms"] for k, v in full_st.items() if k.startswith("host:")},
                        "kernels": kernel_table(full)}}
     print(json.dumps(line))

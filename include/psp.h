@@ -244,6 +244,31 @@ typedef struct {
 
 psp_status psp_stats(psp_handle h, psp_kernel_stat* out, int capacity, int* count, int reset);
 
+/*
+ * psp_tune_sweep - the paper has no counterpart: an autotuner for the schedule of the persistent
+ * sweep (the GPU's counterpart of the paper's choice of process grids, §2.1).  On this handle it
+ * times psp_apply with nrhs right-hand sides (per problem of a batch) under candidate schedules
+ * and keeps the fastest: the tasks a tree level is split into (152 .. 2432), the resident CTAs per
+ * SM (2, 4, 8) and, for nrhs > 1, the right-hand sides per CTA pass (1 .. 8).  It searches one
+ * coordinate at a time, starting from the handle's current schedule, timing `reps` applications
+ * (CUDA events on `stream`) per candidate after one untimed one.  Results do not change beyond
+ * rounding (the schedule only regroups the same sums).  The work vectors are the handle's own; the
+ * call allocates one N x nrhs block for its input and synchronises the stream.
+ *   out   receives the chosen schedule and the times (may be NULL)
+ * Errors: PSP_ERR_ARG (nrhs < 1, reps < 1), PSP_ERR_STATE (no factorisation), PSP_ERR_CUDA.
+ */
+typedef struct {
+  int sweep_level_tasks;
+  int sweep_ctas_per_sm;
+  int sweep_rhs_group;    /* 0: the default grouping */
+  int candidates;         /* schedules timed */
+  double initial_ms;      /* one application under the schedule the handle had */
+  double best_ms;         /* one application under the chosen schedule */
+  int reserved[4];
+} psp_sweep_tuning;
+
+psp_status psp_tune_sweep(psp_handle h, int nrhs, int reps, void* stream, psp_sweep_tuning* out);
+
 psp_status psp_destroy(psp_handle h);
 const char* psp_status_string(psp_status s);
 const char* psp_last_error(void);

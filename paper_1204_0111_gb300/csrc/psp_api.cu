@@ -1922,6 +1922,85 @@ psp_status psp_stats(psp_handle X, psp_kernel_stat* out, int capacity, int* coun
   PSP_CATCH
 }
 
+psp_status psp_tune_sweep(psp_handle X, int nrhs, int reps, void* stream, psp_sweep_tuning* out) {
+  if (!X || nrhs < 1 || reps < 1) return fail(PSP_ERR_ARG, "bad tuning arguments");
+  if (!X->d_factor.p) return fail(PSP_ERR_STATE, "handle has no factorisation");
+  PSP_TRY
+  cudaStream_t st = (cudaStream_t)stream;
+  DevBuf u;
+  const size_t bytes = (size_t)X->N * nrhs * sizeof(double2);
+  u.alloc(bytes);
+  PSP_CK(cudaMemsetAsync(u.p, 0x3f, bytes, st));   // a fixed, finite, normal pattern
+  cudaEvent_t e0, e1;
+  PSP_CK(cudaEventCreate(&e0));
+  PSP_CK(cudaEventCreate(&e1));
+  struct Sched { int lt, cps, rg; };
+  int timed = 0;
+  auto time_one = [&](const Sched& c) {
+    if (c.lt != X->sweep_level_tasks) {
+      X->sweep_level_tasks = c.lt;
+      plan_solve(X);
+    }
+    X->sweep_ctas_per_sm = c.cps;
+    X->sweep_rhs_group = c.rg;
+    apply_dispatch(X, u.as<double2>(), nrhs, st);
+    PSP_CK(cudaEventRecord(e0, st));
+    for (int r = 0; r < reps; ++r) apply_dispatch(X, u.as<double2>(), nrhs, st);
+    PSP_CK(cudaEventRecord(e1, st));
+    PSP_CK(cudaEventSynchronize(e1));
+    float ms = 0;
+    PSP_CK(cudaEventElapsedTime(&ms, e0, e1));
+    ++timed;
+    return (double)ms / reps;
+  };
+  const bool was_timing = X->stats.timing;
+  X->stats.timing = false;
+  Sched best{X->sweep_level_tasks, X->sweep_ctas_per_sm, X->sweep_rhs_group};
+  double best_ms = 0, initial_ms = 0;
+  try {
+    best_ms = initial_ms = time_one(best);
+    auto consider = [&](Sched c) {
+      const double ms = time_one(c);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = c;
+      }
+    };
+    for (int lt : {152, 304, 608, 1216, 2432})
+      if (lt != best.lt) consider({lt, best.cps, best.rg});
+    for (int cps : {2, 4, 8})
+      if (cps != best.cps) consider({best.lt, cps, best.rg});
+    if (nrhs > 1)
+      for (int rg : {1, 2, 4, 8})
+        if (rg <= nrhs && rg != best.rg) consider({best.lt, best.cps, rg});
+  } catch (...) {
+    X->stats.timing = was_timing;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    throw;
+  }
+  X->stats.timing = was_timing;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best.lt != X->sweep_level_tasks) {
+    X->sweep_level_tasks = best.lt;
+    plan_solve(X);
+  }
+  X->sweep_ctas_per_sm = best.cps;
+  X->sweep_rhs_group = best.rg;
+  if (out) {
+    std::memset(out, 0, sizeof(*out));
+    out->sweep_level_tasks = best.lt;
+    out->sweep_ctas_per_sm = best.cps;
+    out->sweep_rhs_group = best.rg;
+    out->candidates = timed;
+    out->initial_ms = initial_ms;
+    out->best_ms = best_ms;
+  }
+  return PSP_OK;
+  PSP_CATCH
+}
+
 psp_status psp_destroy(psp_handle X) {
   if (!X) return PSP_OK;
   delete X;

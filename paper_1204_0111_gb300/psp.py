@@ -52,6 +52,15 @@ class SolveInfo(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
+class SweepTuning(ctypes.Structure):
+    _fields_ = [("sweep_level_tasks", ctypes.c_int), ("sweep_ctas_per_sm", ctypes.c_int),
+                ("sweep_rhs_group", ctypes.c_int), ("candidates", ctypes.c_int), ("initial_ms", ctypes.c_double),
+                ("best_ms", ctypes.c_double), ("reserved", ctypes.c_int * 4)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
 class PSPError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -93,6 +102,7 @@ def lib():
         "psp_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
         "psp_export_front": (_I, [_P, _I, _I, _P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
         "psp_stats": (_I, [_P, ctypes.POINTER(KernelStat), _I, ctypes.POINTER(_I), _I]),
+        "psp_tune_sweep": (_I, [_P, _I, _I, _P, ctypes.POINTER(SweepTuning)]),
         "psp_destroy": (_I, [_P]),
         "psp_status_string": (ctypes.c_char_p, [_I]),
         "psp_last_error": (ctypes.c_char_p, []),
@@ -221,6 +231,12 @@ class SweepingPreconditioner:
         _check(lib().psp_stats(self._h, buf, n.value, ctypes.byref(n), 1 if reset else 0))
         return {buf[i].name.decode(): {"launches": buf[i].launches, "total_ms": buf[i].total_ms,
                                        "flops": buf[i].flops, "bytes": buf[i].bytes} for i in range(n.value)}
+
+    def tune_sweep(self, nrhs=1, reps=3, stream=None):
+        """psp_tune_sweep: time candidate sweep schedules on this handle, keep the fastest."""
+        t = SweepTuning()
+        _check(lib().psp_tune_sweep(self._h, int(nrhs), int(reps), _stream(stream), ctypes.byref(t)))
+        return t.as_dict()
 
     def symbolic(self, panel):
         n = ctypes.c_size_t()

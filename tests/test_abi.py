@@ -70,3 +70,7 @@ def test_batch_arguments_are_rejected_before_any_device_call(L):
     assert L.psp_setup_batch(2, grids, None, om, ga, de, None, None, ctypes.byref(h)) == 1
     n = ctypes.c_int()
     assert L.psp_batch_layout(None, ctypes.byref(n), None, 0) == 1
+
+
+def test_tune_sweep_rejects_bad_arguments(L):
+    assert L.psp_tune_sweep(None, 1, 1, None, None) == 1

@@ -219,3 +219,17 @@ def test_tensor_core_fronts_complex64(case):
     assert worst_cc < 1e-3 and worst_tc < 1e-3 and worst_diff < 1e-3, (worst_tc, worst_cc, worst_diff)
     st = Ptc.stats()
     assert (st.get("k_tc_gemm", {}).get("launches", 0) > 0) == big
+
+
+def test_sweep_autotuner_keeps_results():
+    case = CASES[2]
+    P = gpu_for(case)
+    O = oracle_for(case)
+    t = P.tune_sweep(nrhs=2, reps=1)
+    assert t["sweep_level_tasks"] in (152, 304, 608, 1216, 2432)
+    assert t["sweep_ctas_per_sm"] in (2, 4, 8) and t["sweep_rhs_group"] in (0, 1, 2)
+    assert t["candidates"] >= 8 and 0 < t["best_ms"] <= t["initial_ms"]
+    r = wl.random_vector(case.N, 2, seed=44)
+    out = np.zeros_like(r)
+    P.apply(r, out)
+    assert rel(out, O.apply(r)) < 1e-10
