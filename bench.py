@@ -290,7 +290,7 @@ def gpu_main(a):
 
     # sweep schedule from the library's autotuner, once per precision, before any timed work
     tuning = {}
-    for prec in ("c128",) + (() if a.no_mixed else ("c64",)):
+    for prec in () if a.no_tune else ("c128",) + (() if a.no_mixed else ("c64",)):
         P = psp.SweepingPreconditioner(c_dev, w.h, w.omega, w.gamma, w.panel_depth, pad=w.pad, leaf=w.leaf,
                                        pml_C=w.pml_C, alpha=w.alpha, precision=prec)
         t = P.tune_sweep(nrhs=nrhs, reps=3)
@@ -343,7 +343,7 @@ def gpu_main(a):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         P = psp.SweepingPreconditioner(c_pin, w.h, w.omega, w.gamma, w.panel_depth, pad=w.pad, leaf=w.leaf,
-                                       pml_C=w.pml_C, alpha=w.alpha, **sched["c128"])
+                                       pml_C=w.pml_C, alpha=w.alpha, **sched.get("c128", {}))
         P.solve(f_pin, u_pin, tol=w.tol, k=w.k, maxit=400)
         P.close()
     torch.cuda.synchronize()
@@ -580,6 +580,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the sweep autotuner (library defaults); keeps the "
+                    "first timed step the first launches of the run, for launch-list captures")
     ap.add_argument("--ref-iters", type=int, default=18, help="GMRES iterations assumed by the reference arm")
     ap.add_argument("--n", type=int, default=100, help="grid points per axis (100 = the benchmark workload; "
                     "smaller sizes are for profiling captures)")
