@@ -249,6 +249,35 @@ __device__ __forceinline__ bool wait_count(const unsigned* p, unsigned target, i
   return true;
 }
 
+// Warm L2 with the factor lines a task will stream, while its dependencies are still being
+// waited for (the lines do not depend on them): up the tree rows [r0, r1) of the columns
+// j < min(r1, s), down the tree columns [c0, c1) from below their diagonal to the end.
+template <typename T>
+__device__ __forceinline__ void prefetch_task(const SolveTask tk, const int dir, const SolveCtx<T>& cx) {
+  const int sn = tk.sn;
+  const int s = cx.sh.s[sn], ld = s + cx.sh.u[sn];
+  const char* G = reinterpret_cast<const char*>(cx.G + cx.sh.g_off[sn]);
+  constexpr int kLine = 128;
+  if (dir == 0) {
+    const int ncol = min(tk.r1, s);
+    const int64_t seg = (int64_t)(tk.r1 - tk.r0) * sizeof(T);
+    const int lines = (int)((seg + kLine - 1) / kLine) + 1;   // the segment may straddle one more line
+    for (int w = threadIdx.x; w < ncol * lines; w += blockDim.x) {
+      const int j = w / lines, l = w % lines;
+      const char* col = G + ((int64_t)j * ld + tk.r0) * sizeof(T);
+      const char* a = col + (int64_t)l * kLine;
+      if (a < col + seg) asm volatile("prefetch.L2 [%0];" ::"l"(a));
+    }
+  } else {
+    for (int c = tk.r0; c < tk.r1; ++c) {
+      const char* col = G + ((int64_t)c * ld + c + 1) * sizeof(T);
+      const int64_t seg = (int64_t)(ld - c - 1) * sizeof(T);
+      for (int64_t off = (int64_t)threadIdx.x * kLine; off < seg; off += (int64_t)blockDim.x * kLine)
+        asm volatile("prefetch.L2 [%0];" ::"l"(col + off));
+    }
+  }
+}
+
 constexpr int kMaxSweepShapes = 4, kMaxSweepSteps = 512, kMaxSweepPanels = 256;
 constexpr int kSweepThreads = 256;
 
@@ -309,7 +338,18 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs<T> a) {
         cx.upd = a.cx.upd + (int64_t)sp.prob * a.cx.upd_ld * a.cx.nrhs;
       }
       const SolveTask tk = a.tasks[e.task];
-      const int fb = a.front_base[pi.shape];
+      s_tk = tk;
+      s_dir = e.dir;
+      s_R = e.R;
+    }
+    __syncthreads();
+    prefetch_task<T>(s_tk, s_dir, s_cx);
+    if (threadIdx.x == 0) {
+      const QueueEntry e = a.queue[idx];
+      const SolveTask tk = s_tk;
+      const SolveCtx<T>& cx = s_cx;
+      const int shape = tab_smem ? s_panel[s_step[e.step].panel].shape : a.panels[a.steps[e.step].panel].shape;
+      const int fb = a.front_base[shape];
       const unsigned* up = a.done_up + a.step_front_base[e.step];
       const unsigned* down = a.done_down + a.step_front_base[e.step];
       bool ok = true;
@@ -326,9 +366,6 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs<T> a) {
                       : wait_count(up + tk.sn, (unsigned)a.ntask_up[fb + tk.sn], a.status);
       }
       __threadfence();
-      s_tk = tk;
-      s_dir = e.dir;
-      s_R = e.R;
       s_ok = ok;
     }
     __syncthreads();
