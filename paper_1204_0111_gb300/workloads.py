@@ -117,8 +117,12 @@ class Workload:
     def N(self):
         return self.n ** 3
 
+    forcing: np.ndarray | None = None
+
     def rhs(self) -> np.ndarray:
-        """(nrhs, N) Gaussian shots."""
+        """(nrhs, N) right-hand sides: the explicit forcing if set, else Gaussian shots."""
+        if self.forcing is not None:
+            return self.forcing
         return np.stack([gaussian_source(self.n, self.n, self.n, self.h, s) for s in self.sources])
 
 
@@ -174,3 +178,68 @@ def cube_salt(n=256, gamma=12, panel_depth=8, pad=8, ppw=8.0, leaf=64, shots=(8,
     c = velocity_salt(n, n, n, h)
     return Workload(f"salt{n}", n, c, h, omega_for_ppw(float(c.min()), ppw, h), gamma, panel_depth,
                     gamma if pad is None else pad, leaf, sources=top_shots(n, h, gamma, *shots), k=30)
+
+
+# ---------------------------------------------------------------------------------------------
+# The paper's analytic models and forcing functions (§3), on the unit cube, any n
+# ---------------------------------------------------------------------------------------------
+def velocity_barrier(nx, ny, nz, h, high=1e10):
+    """c = 1 with a slab x1 in [0, 1], x2 in [0.25, 0.3], x3 in [0, 0.75] at c = 1e10."""
+    x, y, z = coords(nx, ny, nz, h)
+    slab = (y >= 0.25) & (y <= 0.3) & (z <= 0.75)
+    return np.where(slab, high, 1.0)
+
+
+def velocity_wedge(nx, ny, nz, h):
+    """c = 2 below x3 = 0.4 + 0.1 x2, else 1.5 below x3 = 0.8 - 0.2 x2, else 3."""
+    x, y, z = coords(nx, ny, nz, h)
+    return np.where(z <= 0.4 + 0.1 * y, 2.0, np.where(z <= 0.8 - 0.2 * y, 1.5, 3.0))
+
+
+def velocity_two_layer(nx, ny, nz, h):
+    """c = 4 for x2 < 0.5, else 1."""
+    x, y, z = coords(nx, ny, nz, h)
+    return np.where(y < 0.5, 4.0, 1.0)
+
+
+def velocity_waveguide(nx, ny, nz, h):
+    """c = 1.25 (1 - 0.4 exp(-32 ((x1 - 0.5)^2 + (x2 - 0.5)^2)))."""
+    x, y, z = coords(nx, ny, nz, h)
+    return 1.25 * (1.0 - 0.4 * np.exp(-32.0 * ((x - 0.5) ** 2 + (y - 0.5) ** 2)))
+
+
+PAPER_SHOTS = ((0.5, 0.5, 0.1), (0.25, 0.25, 0.1), (0.75, 0.75, 0.5))   # x0, x1, x2 of §3
+PAPER_DIRECTION = (1.0 / math.sqrt(3.0), 1.0 / math.sqrt(3.0), -1.0 / math.sqrt(3.0))
+
+
+def paper_forcing(n, h, omega):
+    """The four right-hand sides of §3 on an n^3 grid, shape (4, N) complex:
+    f0 one shot n exp(-10 n |x - x0|^2); f1 the shots at x0, x1, x2 summed; f2 a Gaussian beam
+    exp(i omega x.d) exp(-4 omega |x - x2|^2); f3 a plane wave exp(i omega x.d)."""
+    x, y, z = coords(n, n, n, h)
+    shot = [n * np.exp(-10.0 * n * ((x - p[0]) ** 2 + (y - p[1]) ** 2 + (z - p[2]) ** 2)) for p in PAPER_SHOTS]
+    d = PAPER_DIRECTION
+    phase = np.exp(1j * omega * (x * d[0] + y * d[1] + z * d[2]))
+    x2 = PAPER_SHOTS[2]
+    beam = phase * np.exp(-4.0 * omega * ((x - x2[0]) ** 2 + (y - x2[1]) ** 2 + (z - x2[2]) ** 2))
+    f = [shot[0], shot[0] + shot[1] + shot[2], beam, phase]
+    return np.stack([np.asarray(v, dtype=np.complex128).ravel() for v in f])
+
+
+# model -> (velocity, PML amplitude of the paper's table)
+PAPER_MODELS = {"barrier": (velocity_barrier, 3.0), "wedge": (velocity_wedge, 4.0),
+                "two_layer": (velocity_two_layer, 4.0), "waveguide": (velocity_waveguide, 2.0)}
+
+
+def cube_paper(model, n, gamma=5, panel_depth=4, pad=None, ppw=10.0, leaf=64, alpha=7.0):
+    """One of the paper's analytic models on n^3 with its settings (§3): gamma = 5 PML points,
+    4 planes per panel, damping 7, the tabulated PML amplitude, 10 points per shortest wavelength;
+    rhs() gives its four forcing functions."""
+    vel, C = PAPER_MODELS[model]
+    h = 1.0 / (n + 1)
+    c = vel(n, n, n, h)
+    omega = omega_for_ppw(float(c.min()), ppw, h)
+    w = Workload(f"{model}{n}", n, c, h, omega, gamma, panel_depth, gamma if pad is None else pad, leaf,
+                 pml_C=C, alpha=alpha)
+    w.forcing = paper_forcing(n, h, omega)
+    return w
