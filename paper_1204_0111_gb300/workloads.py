@@ -142,14 +142,17 @@ def cube_lens(n=100, gamma=8, panel_depth=4, pad=None, ppw=10.0, leaf=64):
                     gamma if pad is None else pad, leaf, sources=[(0.5, 0.5, 0.1)])
 
 
-def cube_layered(n=200, gamma=10, panel_depth=4, pad=None, ppw=10.0, leaf=64, seed=3, pml_C=8.0):
-    """Layered and faulted model on n^3, shot at (0.5, 0.5, 0.1).  PML amplitude 8: on this
-    high-contrast model the sweep needs a stronger PML than the smooth ones (oracle, n = 40: 34
-    iterations at C = 4, 19 at C = 8)."""
+def cube_layered(n=200, gamma=10, panel_depth=4, pad=None, ppw=10.0, leaf=64, seed=3, pml_C=8.0, alpha=None):
+    """Layered and faulted model on n^3, shot at (0.5, 0.5, 0.1).  PML amplitude 8 and damping
+    alpha = omega / 5 of the preconditioner's J: on this model, whose interfaces cross the sweep
+    direction, the sweep needs a stronger PML and more damping than on the smooth ones (oracle,
+    n = 40: 34 iterations at C = 4, 19 at C = 8; GPU, n = 200: no convergence at alpha = 2 pi or 20,
+    145 iterations at alpha = 50).  Neither changes the solution of A u = f."""
     h = 1.0 / (n + 1)
     c = velocity_layered_faulted(n, n, n, h, seed=seed)
-    return Workload(f"layered{n}", n, c, h, omega_for_ppw(float(c.min()), ppw, h), gamma, panel_depth,
-                    gamma if pad is None else pad, leaf, pml_C=pml_C, sources=[(0.5, 0.5, 0.1)])
+    omega = omega_for_ppw(float(c.min()), ppw, h)
+    return Workload(f"layered{n}", n, c, h, omega, gamma, panel_depth, gamma if pad is None else pad, leaf,
+                    pml_C=pml_C, alpha=omega / 5.0 if alpha is None else alpha, sources=[(0.5, 0.5, 0.1)])
 
 
 def top_shots(n, h, gamma, nx_shots, ny_shots, lo=0.2, hi=0.8):

@@ -131,11 +131,10 @@ def test_layered30_matches_oracle_iterations():
         assert abs(info["iterations"] - it_oracle) <= 1, (precision, info["iterations"], it_oracle)
 
 
-def test_layered200_complex64_setup_and_apply_properties():
+def test_layered200_complex64_solve_to_tolerance():
     # the 200^3 layered and faulted model, gamma 10, complex64 fronts (116 GB of factors, level
-    # groups under the temporary budget).  GMRES(20) does not converge on this model at this
-    # frequency (nor in complex128 at 150^3), so the checks are the ones that hold at any size:
-    # the application is complex symmetric and a GMRES cycle does not increase the true residual.
+    # groups under the temporary budget), FP64 GMRES(20) to 1e-5; the application is complex
+    # symmetric and the solution's true residual is measured with the oracle's operator
     w = wl.cube_layered(200)
     P = handle(w, precision="c64")
     asym, _ = bilinear_asymmetry(P, w.N, 51)
@@ -143,5 +142,7 @@ def test_layered200_complex64_setup_and_apply_properties():
     f = w.rhs()
     fd = torch.from_numpy(f).cuda()
     ud = torch.zeros_like(fd)
-    info = P.solve(fd, ud, tol=w.tol, k=w.k, maxit=w.k, raise_on_nonconvergence=False)
-    assert info["iterations"] == w.k and info["relres_max"] <= 1.0 + 1e-12
+    info = P.solve(fd, ud, tol=w.tol, k=w.k, maxit=400)
+    assert info["converged"] == 1
+    A = dz.operator_A(dz.Helmholtz(w.c, w.h, w.omega, w.gamma, w.pml_C, w.alpha))
+    assert true_residual(A, w, f, ud.cpu().numpy()) < w.tol
