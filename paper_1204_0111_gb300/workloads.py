@@ -142,17 +142,25 @@ def cube_lens(n=100, gamma=8, panel_depth=4, pad=None, ppw=10.0, leaf=64):
                     gamma if pad is None else pad, leaf, sources=[(0.5, 0.5, 0.1)])
 
 
-def cube_layered(n=200, gamma=10, panel_depth=4, pad=None, ppw=10.0, leaf=64, seed=3, pml_C=8.0, alpha=None):
-    """Layered and faulted model on n^3, shot at (0.5, 0.5, 0.1).  PML amplitude 8 and damping
-    alpha = omega / 5 of the preconditioner's J: on this model, whose interfaces cross the sweep
-    direction, the sweep needs a stronger PML and more damping than on the smooth ones (oracle,
-    n = 40: 34 iterations at C = 4, 19 at C = 8; GPU, n = 200: no convergence at alpha = 2 pi or 20,
-    145 iterations at alpha = 50).  Neither changes the solution of A u = f."""
+def cube_layered(n=200, gamma=10, panel_depth=4, pad=None, ppw=10.0, leaf=64, seed=3, pml_C=None, alpha=2.0 * math.pi):
+    """Layered and faulted model on n^3, shot at (0.5, 0.5, 0.1).  PML amplitude 4 relative to the
+    fastest wave speed: pml_C = 4 c_max (see pml_amplitude)."""
     h = 1.0 / (n + 1)
     c = velocity_layered_faulted(n, n, n, h, seed=seed)
     omega = omega_for_ppw(float(c.min()), ppw, h)
+    C = pml_amplitude(4.0, float(c.max())) if pml_C is None else pml_C
     return Workload(f"layered{n}", n, c, h, omega, gamma, panel_depth, gamma if pad is None else pad, leaf,
-                    pml_C=pml_C, alpha=omega / 5.0 if alpha is None else alpha, sources=[(0.5, 0.5, 0.1)])
+                    pml_C=C, alpha=alpha, sources=[(0.5, 0.5, 0.1)])
+
+
+def pml_amplitude(C_rel, c_ref):
+    """The stretch's amplitude for a PML amplitude C_rel given relative to the wave speed c_ref.
+
+    With s = 1 + i sigma / omega and sigma = (C / eta) t^2, a wave of speed c crossing the layer
+    decays by exp(-C / (3 c)): the same C absorbs less where waves are faster.  The amplitudes the
+    paper reports (2-4, sec. 3) behave, on its models, like amplitudes relative to the fastest
+    propagating speed, so a workload passes C = C_rel * c_ref."""
+    return C_rel * c_ref
 
 
 def top_shots(n, h, gamma, nx_shots, ny_shots, lo=0.2, hi=0.8):
@@ -229,20 +237,22 @@ def paper_forcing(n, h, omega):
     return np.stack([np.asarray(v, dtype=np.complex128).ravel() for v in f])
 
 
-# model -> (velocity, PML amplitude of the paper's table)
-PAPER_MODELS = {"barrier": (velocity_barrier, 3.0), "wedge": (velocity_wedge, 4.0),
-                "two_layer": (velocity_two_layer, 4.0), "waveguide": (velocity_waveguide, 2.0)}
+# model -> (velocity, PML amplitude of the paper's table, fastest propagating wave speed; the
+# barrier's slab at c = 1e10 is an obstacle, not a propagating medium)
+PAPER_MODELS = {"barrier": (velocity_barrier, 3.0, 1.0), "wedge": (velocity_wedge, 4.0, 3.0),
+                "two_layer": (velocity_two_layer, 4.0, 4.0), "waveguide": (velocity_waveguide, 2.0, 1.25)}
 
 
 def cube_paper(model, n, gamma=5, panel_depth=4, pad=None, ppw=10.0, leaf=64, alpha=7.0):
     """One of the paper's analytic models on n^3 with its settings (§3): gamma = 5 PML points,
-    4 planes per panel, damping 7, the tabulated PML amplitude, 10 points per shortest wavelength;
-    rhs() gives its four forcing functions."""
-    vel, C = PAPER_MODELS[model]
+    4 planes per panel, damping 7, the tabulated PML amplitude (relative to the fastest propagating
+    speed, see pml_amplitude), 10 points per shortest wavelength; rhs() gives its four forcing
+    functions."""
+    vel, C, c_ref = PAPER_MODELS[model]
     h = 1.0 / (n + 1)
     c = vel(n, n, n, h)
     omega = omega_for_ppw(float(c.min()), ppw, h)
     w = Workload(f"{model}{n}", n, c, h, omega, gamma, panel_depth, gamma if pad is None else pad, leaf,
-                 pml_C=C, alpha=alpha)
+                 pml_C=pml_amplitude(C, c_ref), alpha=alpha)
     w.forcing = paper_forcing(n, h, omega)
     return w
