@@ -470,11 +470,12 @@ def batch_main(a):
     u_dev = torch.zeros_like(f_dev)
     stream = torch.cuda.current_stream(dev)
 
-    B = psp.SweepingPreconditionerBatch(prs, precision="c64")
+    pml_C = ws[0].pml_C        # one PML amplitude for the whole batch (the same for every problem)
+    B = psp.SweepingPreconditionerBatch(prs, precision="c64", pml_C=pml_C)
     tuning = B.tune_sweep(nrhs=nrhs, reps=2)     # the library's autotuner, before any timed work
     B.close()
     sched = {"sweep_level_tasks": tuning["sweep_level_tasks"], "sweep_ctas_per_sm": tuning["sweep_ctas_per_sm"],
-             "sweep_rhs_group": tuning["sweep_rhs_group"]}
+             "sweep_rhs_group": tuning["sweep_rhs_group"], "pml_C": pml_C}
 
     def step(stats=0, problems=prs, f=f_dev, u=u_dev):
         B = psp.SweepingPreconditionerBatch(problems, precision="c64", collect_stats=stats, **sched)
@@ -527,8 +528,9 @@ def batch_main(a):
             "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c64 fronts/sweeps, f64 GMRES", "data": "synthetic",
             "config": {"workload": "batch16: 16 independent problems n = 40 + 8 (k mod 11), smooth random velocity "
-                                   "c = 2 + 0.5 tanh(g), gamma 8, panels of 4 + pad 8, leaf 64, 8 shots each below "
-                                   "the top PML, GMRES(20) to 1e-05, complex64 fronts",
+                                   "c = 2 + 0.5 tanh(g), gamma 8, PML amplitude 10 (4 relative to c < 2.5), panels of "
+                                   "4 + pad 8, leaf 64, 8 shots each below the top PML, GMRES(20) to 1e-05, complex64 "
+                                   "fronts",
                        "sizes": sizes, "nrhs_per_problem": nrhs, "points": int(sum(w.N for w in ws)),
                        "l2": "inputs larger than L2", "parallelism": "single GPU, one batched handle"},
             "roofline": roof, "cpu_baseline": None,

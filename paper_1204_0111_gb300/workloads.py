@@ -179,7 +179,8 @@ def cube_smooth(k, gamma=8, panel_depth=4, pad=None, ppw=10.0, leaf=64, base_see
     h = 1.0 / (n + 1)
     c = velocity_smooth_random(n, n, n, h, seed=base_seed + k)
     return Workload(f"smooth{n}_k{k}", n, c, h, omega_for_ppw(float(c.min()), ppw, h), gamma, panel_depth,
-                    gamma if pad is None else pad, leaf, sources=top_shots(n, h, gamma, 4, 2))
+                    gamma if pad is None else pad, leaf, pml_C=pml_amplitude(4.0, 2.5),   # c < 2.5
+                    sources=top_shots(n, h, gamma, 4, 2))
 
 
 def cube_salt(n=256, gamma=12, panel_depth=8, pad=8, ppw=8.0, leaf=64, shots=(8, 4)):
@@ -188,7 +189,8 @@ def cube_salt(n=256, gamma=12, panel_depth=8, pad=8, ppw=8.0, leaf=64, shots=(8,
     h = 1.0 / (n + 1)
     c = velocity_salt(n, n, n, h)
     return Workload(f"salt{n}", n, c, h, omega_for_ppw(float(c.min()), ppw, h), gamma, panel_depth,
-                    gamma if pad is None else pad, leaf, sources=top_shots(n, h, gamma, *shots), k=30)
+                    gamma if pad is None else pad, leaf, pml_C=pml_amplitude(4.0, float(c.max())),
+                    sources=top_shots(n, h, gamma, *shots), k=30)
 
 
 # ---------------------------------------------------------------------------------------------

@@ -158,7 +158,7 @@ def test_batch16_uneven_problems_eight_shots_complex64():
     # a true relative residual of 1e-5, and the two smallest problems equal to their own handles
     ws = [wl.cube_smooth(k) for k in range(16)]
     prs = [dict(c=w.c, h=w.h, omega=w.omega, gamma=w.gamma, panel_depth=w.panel_depth) for w in ws]
-    B = batched(prs, precision="c64")
+    B = batched(prs, precision="c64", pml_C=ws[0].pml_C)   # one amplitude for the whole batch
     nrhs = 8
     fs = [w.rhs() for w in ws]
     fd = torch.from_numpy(B.pack(fs)).cuda()
@@ -175,11 +175,11 @@ def test_batch16_uneven_problems_eight_shots_complex64():
     B.close()
     del fd, ud
     small = [0, 11]   # n = 40 twice (seeds 400 and 411)
-    Bs = batched([prs[q] for q in small], precision="c64")
+    Bs = batched([prs[q] for q in small], precision="c64", pml_C=ws[0].pml_C)
     flat = np.zeros(Bs.N * nrhs, dtype=np.complex128)
     Bs.solve(Bs.pack([fs[q] for q in small]), flat, tol=1e-5, k=20, maxit=400)
     for i, q in enumerate(small):
-        P = single(prs[q], precision="c64")
+        P = single(prs[q], precision="c64", pml_C=ws[0].pml_C)
         u = np.zeros_like(fs[q])
         P.solve(fs[q], u, tol=1e-5, k=20, maxit=400)
         assert np.array_equal(Bs.unpack(flat, nrhs)[i], u)
