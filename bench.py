@@ -7,8 +7,13 @@ planes, nested-dissection leaf 64, one Gaussian shot (sigma = 2h) at (0.5, 0.5, 
 a relative residual of 1e-5, complex128 on the GPU.  One step = the whole hot path on one problem:
 setup (factor every panel) + GMRES solve to 1e-5 (all preconditioner applications and matvecs).
 
-One JSON line is printed by rank 0.  `--impl reference` times the complex128 CPU oracle on a
-bounded sample of the same workload instead (see `reference_main`).
+One JSON line is printed by rank 0.  Before the timed region the library's sweep autotuner picks
+the sweep schedule once per precision (`--no-tune` keeps the defaults).  The line also carries
+the complex64 path on the same workload (`mixed`; `--no-mixed` skips it) and the CPU oracle's
+extrapolated time (`cpu_baseline`; `--no-cpu-baseline` skips it).  `--workload batch16` prints the
+same kind of line for 16 independent problems of uneven size in one batched handle instead.
+`--impl reference` times the complex128 CPU oracle on a bounded sample of the default workload
+(see `reference_main`).
 """
 from __future__ import annotations
 

@@ -278,6 +278,8 @@ __device__ __forceinline__ void prefetch_task(const SolveTask tk, const int dir,
   }
 }
 
+// tables cached in shared memory when they fit (a single problem: at most 3-4 shapes; batches
+// and very deep sweeps read them from global memory instead)
 constexpr int kMaxSweepShapes = 4, kMaxSweepSteps = 512, kMaxSweepPanels = 256;
 constexpr int kSweepThreads = 256;
 

@@ -251,7 +251,8 @@ struct QueueEntry {
 };
 template <typename T>
 struct SweepArgs {
-  SolveCtx<T> cx;               // fields common to every panel (vectors, sizes, coupling tables)
+  SolveCtx<T> cx;               // fields common to every panel (vectors, sizes, coupling tables); for a batch
+                                // (nprobs > 1) the vector and work-vector bases, offset per problem
   int nshapes, nsteps, npanels; // sizes of the three tables below (kept in shared memory)
   const SweepStep* steps;
   const PanelSweep* panels;
