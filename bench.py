@@ -192,6 +192,22 @@ SETUP_KERNELS = ("k_assemble", "k_diag_ldlt", "k_panel_right", "k_panel_left", "
 SWEEP_KERNELS = ("k_sweep", "k_solve_fwd", "k_solve_bwd")
 
 
+def max_over_ranks(x, device=None):
+    """The largest value of a per-rank float over all ranks (the slowest rank's time); the value
+    itself when no process group is running."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_rank, seconds_max):
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / seconds_max
+
+
 def _agg(stat_list):
     agg = {}
     for st in stat_list:
@@ -329,11 +345,8 @@ def gpu_main(a):
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * a.steps / (ms_max / 1e3)
+    ms_max = max_over_ranks(ms, dev)
+    value = job_rate(world, a.steps, ms_max / 1e3)
 
     _, full_st, _ = step(stats=1)       # one extra step, every launch timed, after the timed region
     roofline, detail, launches = summarize(stats_all, full_st, infos, fbytes, a.steps)
@@ -353,10 +366,7 @@ def gpu_main(a):
         P.close()
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    tt = torch.tensor([t1 - t0], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-    e2e = {"value": world * e2e_steps / float(tt.item()), "unit": UNIT,
+    e2e = {"value": job_rate(world, e2e_steps, max_over_ranks(t1 - t0, dev)), "unit": UNIT,
            "h2d_bytes_per_step": int(c_pin.numel() * 8 + f_pin.numel() * 16),
            "d2h_bytes_per_step": int(u_pin.numel() * 16)}
 
