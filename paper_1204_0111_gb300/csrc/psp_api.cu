@@ -6,6 +6,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <memory>
 #include <new>
@@ -65,6 +66,13 @@ template <typename U>
 static void upload(DevBuf& d, const std::vector<U>& h) {
   d.alloc(std::max<size_t>(h.size() * sizeof(U), 16));
   if (!h.empty()) PSP_CK(cudaMemcpy(d.p, h.data(), h.size() * sizeof(U), cudaMemcpyHostToDevice));
+}
+// Stream-ordered upload: the copy from pageable memory is staged before the call returns, and it
+// does not wait for work already queued on the stream.
+template <typename U>
+static void upload_async(DevBuf& d, const std::vector<U>& h, cudaStream_t st) {
+  d.alloc(std::max<size_t>(h.size() * sizeof(U), 16));
+  if (!h.empty()) PSP_CK(cudaMemcpyAsync(d.p, h.data(), h.size() * sizeof(U), cudaMemcpyHostToDevice, st));
 }
 
 static bool is_device_pointer(const void* p) {
@@ -280,8 +288,9 @@ static double ms_since(std::chrono::steady_clock::time_point t0) {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
 
+// `while_device_runs` is host work done after the last launch is enqueued, before waiting for them.
 template <typename T>
-static void factor_all(psp_ctx_s* X, cudaStream_t st) {
+static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()>& while_device_runs) {
   auto tp = std::chrono::steady_clock::now();
   const int nb = 32;
   const double tiny = sizeof(T) == 16 ? 1e-300 : 1e-30;
@@ -422,7 +431,76 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
       for (int ti = tj; ti < M; ti += 64) emit(C, ldc, ti, tj, std::min(64, M - ti), std::min(64, M - tj));
   };
 
+  // Each group's tasks are uploaded and its launches enqueued as soon as the group is planned, so
+  // the host plans the next group while the device factors this one.  Task arrays go to
+  // stream-ordered device chunks, one per group and array, freed after the final synchronisation.
+  int* status = X->d_status.as<int>();
+  PSP_CK(cudaMemsetAsync(status, 0, 4 * sizeof(int), st));
+  static const char* names[] = {"k_assemble", "k_diag_ldlt", "k_panel_right", "k_panel_left", "k_gemm", "k_copy_linv",
+                                "k_tc_gemm", "k_tc_pack", "k_scale_zd"};
+  std::vector<void*> chunks;
+  struct ChunkGuard {
+    std::vector<void*>& c;
+    cudaStream_t s;
+    ~ChunkGuard() {
+      for (void* p : c) cudaFreeAsync(p, s);
+    }
+  } chunk_guard{chunks, st};
+  // copies v[done, size) to a new device chunk (the copy from pageable memory is staged before the
+  // call returns, so the vector may grow afterwards); returns the chunk and advances done
+  auto upload_tail = [&](const auto& v, size_t& done) {
+    using E = typename std::decay_t<decltype(v)>::value_type;
+    const size_t n = v.size() - done;
+    E* d = nullptr;
+    if (n > 0) {
+      PSP_CK(cudaMallocAsync(reinterpret_cast<void**>(&d), n * sizeof(E), st));
+      chunks.push_back(d);
+      PSP_CK(cudaMemcpyAsync(d, v.data() + done, n * sizeof(E), cudaMemcpyHostToDevice, st));
+    }
+    return d;
+  };
+  size_t up_f = 0, up_c = 0, up_d = 0, up_g = 0, up_p = 0, up_t = 0;
+  double plan_ms = 0, enqueue_ms = 0;
+  auto enqueue_group = [&](size_t lb) {
+    const size_t f0 = up_f, c0 = up_c, d0 = up_d, g0 = up_g, p0 = up_p, t0 = up_t;
+    const FrontTask<T>* F = upload_tail(fronts, up_f);
+    const ColTask* CT = upload_tail(ctasks, up_c);
+    const int* DL = upload_tail(dlist, up_d);
+    const GemmTask<T>* GT = upload_tail(gtasks, up_g);
+    const TcPackTask* PT = upload_tail(ptasks, up_p);
+    const TcGemmTask* TT = upload_tail(ttasks, up_t);
+    up_f = fronts.size();
+    up_c = ctasks.size();
+    up_d = dlist.size();
+    up_g = gtasks.size();
+    up_p = ptasks.size();
+    up_t = ttasks.size();
+    for (size_t li = lb; li < launches.size(); ++li) {
+      const Launch& l = launches[li];
+      if (l.count <= 0) continue;
+      const FrontTask<T>* Fl = F + (l.front_off - (int64_t)f0);
+      X->stats.run(names[l.kind], st, 1, l.flops, l.bytes, [&] {
+        switch (l.kind) {
+          case ASSEMBLE:
+            launch_assemble_impl<T>(Fl, CT + (l.off - (int64_t)c0), l.count, X->d_shapes.as<ShapeDev>(),
+                                    X->d_boxops.as<BoxOp>(), d_upd_ptr.as<T*>(), X->d_panel_shape.as<int32_t>(), st);
+            break;
+          case DIAG: launch_diag_ldlt<T>(Fl, DL + (l.off - (int64_t)d0), l.count, l.kb, tiny, status, st); break;
+          case PRIGHT: launch_panel_right<T>(Fl, CT + (l.off - (int64_t)c0), l.count, l.kb, st); break;
+          case PLEFT: launch_panel_left<T>(Fl, CT + (l.off - (int64_t)c0), l.count, l.kb, st); break;
+          case GEMM: launch_gemm<T>(GT + (l.off - (int64_t)g0), l.count, st); break;
+          case COPY: launch_copy_linv<T>(Fl, CT + (l.off - (int64_t)c0), l.count, st); break;
+          case TCGEMM: launch_tc_gemm(TT + (l.off - (int64_t)t0), l.count, status, st); break;
+          case TCPACK: launch_tc_pack(PT + (l.off - (int64_t)p0), l.count, st); break;
+          case SCALE: launch_scale_zd<T>(Fl, CT + (l.off - (int64_t)c0), l.count, st); break;
+        }
+      }, true);
+    }
+    PSP_CK(cudaGetLastError());
+  };
+
   for (const auto& grp : groups) {
+    const size_t lb = launches.size();
     const int64_t f0 = (int64_t)fronts.size();
     int smax = 0;
     int64_t toff = 0;
@@ -782,48 +860,16 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
         launches.push_back(lt);
       }
     }
+    plan_ms += ms_since(tp);
+    tp = std::chrono::steady_clock::now();
+    enqueue_group(lb);
+    enqueue_ms += ms_since(tp);
+    tp = std::chrono::steady_clock::now();
   }
 
-  X->stats.host("plan_tasks", ms_since(tp));
-  tp = std::chrono::steady_clock::now();
-  DevBuf d_fronts, d_ctasks, d_dlist, d_gtasks, d_ptasks, d_ttasks;
-  upload(d_ptasks, ptasks);
-  upload(d_ttasks, ttasks);
-  upload(d_fronts, fronts);
-  upload(d_ctasks, ctasks);
-  upload(d_dlist, dlist);
-  upload(d_gtasks, gtasks);
-  const FrontTask<T>* F = d_fronts.as<FrontTask<T>>();
-  const ColTask* CT = d_ctasks.as<ColTask>();
-  const int* DL = d_dlist.as<int>();
-  const GemmTask<T>* GT = d_gtasks.as<GemmTask<T>>();
-  X->stats.host("upload_tasks", ms_since(tp));
-  tp = std::chrono::steady_clock::now();
-  int* status = X->d_status.as<int>();
-  PSP_CK(cudaMemsetAsync(status, 0, 4 * sizeof(int), st));
-  static const char* names[] = {"k_assemble", "k_diag_ldlt", "k_panel_right", "k_panel_left", "k_gemm", "k_copy_linv",
-                                "k_tc_gemm", "k_tc_pack", "k_scale_zd"};
-  for (const auto& l : launches) {
-    if (l.count <= 0) continue;
-    X->stats.run(names[l.kind], st, 1, l.flops, l.bytes, [&] {
-      switch (l.kind) {
-        case ASSEMBLE:
-          launch_assemble_impl<T>(F + l.front_off, CT + l.off, l.count, X->d_shapes.as<ShapeDev>(),
-                                  X->d_boxops.as<BoxOp>(), d_upd_ptr.as<T*>(), X->d_panel_shape.as<int32_t>(), st);
-          break;
-        case DIAG: launch_diag_ldlt<T>(F + l.front_off, DL + l.off, l.count, l.kb, tiny, status, st); break;
-        case PRIGHT: launch_panel_right<T>(F + l.front_off, CT + l.off, l.count, l.kb, st); break;
-        case PLEFT: launch_panel_left<T>(F + l.front_off, CT + l.off, l.count, l.kb, st); break;
-        case GEMM: launch_gemm<T>(GT + l.off, l.count, st); break;
-        case COPY: launch_copy_linv<T>(F + l.front_off, CT + l.off, l.count, st); break;
-        case TCGEMM: launch_tc_gemm(d_ttasks.as<TcGemmTask>() + l.off, l.count, status, st); break;
-        case TCPACK: launch_tc_pack(d_ptasks.as<TcPackTask>() + l.off, l.count, st); break;
-        case SCALE: launch_scale_zd<T>(F + l.front_off, CT + l.off, l.count, st); break;
-      }
-    }, true);
-  }
-  PSP_CK(cudaGetLastError());
-  X->stats.host("enqueue_setup", ms_since(tp));
+  X->stats.host("plan_tasks", plan_ms);
+  X->stats.host("enqueue_setup", enqueue_ms);
+  while_device_runs();
   tp = std::chrono::steady_clock::now();
   PSP_CK(cudaStreamSynchronize(st));
   X->stats.host("wait_setup", ms_since(tp));
@@ -839,7 +885,7 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 // Solve plan: per shape and level, forward row tasks and backward column tasks.
 // ---------------------------------------------------------------------------
-static void plan_solve(psp_ctx_s* X) {
+static void plan_solve(psp_ctx_s* X, cudaStream_t st) {
   std::vector<SolveTask> tasks;
   X->splan.assign(X->shapes.size(), {});
   for (size_t si = 0; si < X->shapes.size(); ++si) {
@@ -874,7 +920,7 @@ static void plan_solve(psp_ctx_s* X) {
       P.nbwd = (int)(tasks.size() - P.bwd_off);
     }
   }
-  upload(X->d_stasks, tasks);
+  upload_async(X->d_stasks, tasks, st);
 
   // persistent sweep: panel solves in Alg. 1.5 order and one task queue in topological order.  The
   // chains of a batch's problems are interleaved step by step; each step follows the previous step
@@ -940,8 +986,8 @@ static void plan_solve(psp_ctx_s* X) {
   X->sweep_rhs_bytes = per_rhs;
   X->sweep_nsteps = (int)steps.size();
   X->sweep_nqueue = (int)queue.size();
-  upload(X->d_sweep_steps, steps);
-  upload(X->d_sweep_queue, queue);
+  upload_async(X->d_sweep_steps, steps, st);
+  upload_async(X->d_sweep_queue, queue, st);
   // metadata: front_base | ntask_up | ntask_down | step_front | step_tasks
   std::vector<int> meta;
   meta.insert(meta.end(), front_base.begin(), front_base.end());
@@ -956,7 +1002,7 @@ static void plan_solve(psp_ctx_s* X) {
   X->meta_step_prev = (int64_t)meta.size();
   meta.insert(meta.end(), step_prev.begin(), step_prev.end());
   X->meta_front_base = o_up;
-  upload(X->d_sweep_meta, meta);
+  upload_async(X->d_sweep_meta, meta, st);
   std::vector<ProblemSweep> pss;
   for (const auto& pr : X->probs) {
     ProblemSweep p{};
@@ -969,11 +1015,11 @@ static void plan_solve(psp_ctx_s* X) {
     p.nz = pr.nz;
     pss.push_back(p);
   }
-  upload(X->d_sweep_probs, pss);
+  upload_async(X->d_sweep_probs, pss, st);
   // counters zeroed before every sweep: head | status[4] | step_done[nsteps] | done_up | done_down
   X->sweep_sync_words = 1 + 4 + steps.size() + 2 * (size_t)step_front[steps.size()];
   X->d_sweep_sync.alloc(X->sweep_sync_words * 4);
-  PSP_CK(cudaMemset(X->d_sweep_sync.p, 0, X->sweep_sync_words * 4));
+  PSP_CK(cudaMemsetAsync(X->d_sweep_sync.p, 0, X->sweep_sync_words * 4, st));
 }
 
 // work vectors of one sweep: per problem (a batch's chains run side by side) a box vector pair of
@@ -1380,11 +1426,15 @@ static void finish_setup(psp_ctx_s* X, cudaStream_t st) {
   X->d_factor.alloc((size_t)fe * X->elem_bytes);
   X->d_status.alloc(4 * sizeof(int));
   X->stats.host("alloc_factors", ms_since(ta));
-  ta = std::chrono::steady_clock::now();
-  plan_solve(X);
-  X->stats.host("plan_solve", ms_since(ta));
-  if (X->prec == PSP_PREC_C64) factor_all<float2>(X, st);
-  else factor_all<double2>(X, st);
+  // the sweep's plan is host work the device does not need for the factorisation: it runs while
+  // the device factors
+  auto planner = [X, st] {
+    auto t0 = std::chrono::steady_clock::now();
+    plan_solve(X, st);
+    X->stats.host("plan_solve", ms_since(t0));
+  };
+  if (X->prec == PSP_PREC_C64) factor_all<float2>(X, st, planner);
+  else factor_all<double2>(X, st, planner);
 }
 
 static void setup_impl(psp_ctx_s* X, const double* c, cudaStream_t st) {
@@ -1939,7 +1989,7 @@ psp_status psp_tune_sweep(psp_handle X, int nrhs, int reps, void* stream, psp_sw
   auto time_one = [&](const Sched& c) {
     if (c.lt != X->sweep_level_tasks) {
       X->sweep_level_tasks = c.lt;
-      plan_solve(X);
+      plan_solve(X, st);
     }
     X->sweep_ctas_per_sm = c.cps;
     X->sweep_rhs_group = c.rg;
@@ -1984,7 +2034,7 @@ psp_status psp_tune_sweep(psp_handle X, int nrhs, int reps, void* stream, psp_sw
   cudaEventDestroy(e1);
   if (best.lt != X->sweep_level_tasks) {
     X->sweep_level_tasks = best.lt;
-    plan_solve(X);
+    plan_solve(X, st);
   }
   X->sweep_ctas_per_sm = best.cps;
   X->sweep_rhs_group = best.rg;
