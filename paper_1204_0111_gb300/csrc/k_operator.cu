@@ -90,6 +90,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_assemble(const FrontTask<T>* __restrict__ fronts,
                                                   const ColTask* __restrict__ tasks, const ShapeDev* __restrict__ shapes,
                                                   const BoxOp* __restrict__ boxops, T* const* __restrict__ upd_ptr,
+                                                  const int32_t* __restrict__ upd_tile,
                                                   const int32_t* __restrict__ panel_shape) {
   const ColTask tk = tasks[blockIdx.x];
   const FrontTask<T> ft = fronts[tk.front];
@@ -109,8 +110,8 @@ __global__ void __launch_bounds__(256) k_assemble(const FrontTask<T>* __restrict
       T* wc = ft.W + (int64_t)c * s;
       for (int r = threadIdx.x; r < s; r += blockDim.x) wc[r] = (r == c) ? CplxTraits<T>::one() : zero;
     } else {
-      T* col = ft.U + (int64_t)(c - s) * u;
-      for (int r = threadIdx.x; r < u; r += blockDim.x) col[r] = zero;
+      // the lower part of column c - s of the packed update matrix
+      for (int r = c - s + threadIdx.x; r < u; r += blockDim.x) ft.U[upd_index(r, c - s, u, ft.ut)] = zero;
     }
   }
   __syncthreads();
@@ -168,6 +169,7 @@ __global__ void __launch_bounds__(256) k_assemble(const FrontTask<T>* __restrict
     const int uc = sh.u[ch];
     const int32_t* rel = sh.rel + sh.struct_ptr[ch];
     const T* Uc = upd_ptr[ft.gfid - ft.sn + ch];
+    const int utc = upd_tile[ft.gfid - ft.sn + ch];
     // child columns b whose target column rel[b] lies in [c0, c1): a contiguous range
     int b0 = 0, b1 = uc;
     {
@@ -180,15 +182,14 @@ __global__ void __launch_bounds__(256) k_assemble(const FrontTask<T>* __restrict
     }
     for (int b = b0; b < b1; ++b) {
       const int tc = rel[b];
-      const T* src = Uc + (int64_t)b * uc;
       if (tc < s) {
         T* dst = ft.G + (int64_t)tc * ld;
-        for (int a = b + threadIdx.x; a < uc; a += blockDim.x) dst[rel[a]] = cadd(dst[rel[a]], src[a]);
+        for (int a = b + threadIdx.x; a < uc; a += blockDim.x)
+          dst[rel[a]] = cadd(dst[rel[a]], Uc[upd_index(a, b, uc, utc)]);
       } else {
-        T* dst = ft.U + (int64_t)(tc - s) * u;
         for (int a = b + threadIdx.x; a < uc; a += blockDim.x) {
-          const int tr = rel[a] - s;
-          dst[tr] = cadd(dst[tr], src[a]);
+          T* d = ft.U + upd_index(rel[a] - s, tc - s, u, ft.ut);
+          *d = cadd(*d, Uc[upd_index(a, b, uc, utc)]);
         }
       }
     }
@@ -198,14 +199,17 @@ __global__ void __launch_bounds__(256) k_assemble(const FrontTask<T>* __restrict
 
 template <typename T>
 void launch_assemble_impl(const FrontTask<T>* fronts, const ColTask* tasks, int ntasks, const ShapeDev* shapes,
-                          const BoxOp* boxops, T* const* upd_ptr, const int32_t* panel_shape, cudaStream_t st) {
+                          const BoxOp* boxops, T* const* upd_ptr, const int32_t* upd_tile, const int32_t* panel_shape,
+                          cudaStream_t st) {
   if (ntasks <= 0) return;
-  k_assemble<T><<<ntasks, 256, 0, st>>>(fronts, tasks, shapes, boxops, upd_ptr, panel_shape);
+  k_assemble<T><<<ntasks, 256, 0, st>>>(fronts, tasks, shapes, boxops, upd_ptr, upd_tile, panel_shape);
 }
 
 template void launch_assemble_impl<double2>(const FrontTask<double2>*, const ColTask*, int, const ShapeDev*,
-                                            const BoxOp*, double2* const*, const int32_t*, cudaStream_t);
+                                            const BoxOp*, double2* const*, const int32_t*, const int32_t*,
+                                            cudaStream_t);
 template void launch_assemble_impl<float2>(const FrontTask<float2>*, const ColTask*, int, const ShapeDev*,
-                                           const BoxOp*, float2* const*, const int32_t*, cudaStream_t);
+                                           const BoxOp*, float2* const*, const int32_t*, const int32_t*,
+                                           cudaStream_t);
 
 }  // namespace psp

@@ -335,7 +335,7 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
       const int64_t s = sh.s[sn], u = sh.u[sn];
       if (u > 0) {
         uoff[X->sn_base[p] + sn] = slab;
-        slab += pad16(u * u);
+        slab += pad16(upd_packed_elems((int)u, use_tc(s, u) ? 128 : 64));
       }
       const int64_t t = front_temp(s, u);
       tsum += t;
@@ -392,10 +392,17 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
   T* tbase = d_temp.as<T>();
   T* fbase = X->d_factor.as<T>();
   std::vector<T*> upd_ptr(X->nfronts, nullptr);
+  std::vector<int32_t> upd_tile(X->nfronts, 64);   // tile size of each front's packed update matrix
   for (int64_t i = 0; i < X->nfronts; ++i)
     if (uoff[i] >= 0) upd_ptr[i] = ubase + uoff[i];
-  DevBuf d_upd_ptr;
+  for (int p = 0; p < X->m; ++p) {
+    const Shape& sh = X->shapes[X->shape_of[p]];
+    for (int sn = 0; sn < sh.nsn; ++sn)
+      if (use_tc(sh.s[sn], sh.u[sn])) upd_tile[X->sn_base[p] + sn] = 128;
+  }
+  DevBuf d_upd_ptr, d_upd_tile;
   upload(d_upd_ptr, upd_ptr);
+  upload(d_upd_tile, upd_tile);
 
   // --- task lists ---
   std::vector<FrontTask<T>> fronts;
@@ -483,7 +490,8 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
         switch (l.kind) {
           case ASSEMBLE:
             launch_assemble_impl<T>(Fl, CT + (l.off - (int64_t)c0), l.count, X->d_shapes.as<ShapeDev>(),
-                                    X->d_boxops.as<BoxOp>(), d_upd_ptr.as<T*>(), X->d_panel_shape.as<int32_t>(), st);
+                                    X->d_boxops.as<BoxOp>(), d_upd_ptr.as<T*>(), d_upd_tile.as<int32_t>(),
+                                    X->d_panel_shape.as<int32_t>(), st);
             break;
           case DIAG: launch_diag_ldlt<T>(Fl, DL + (l.off - (int64_t)d0), l.count, l.kb, tiny, status, st); break;
           case PRIGHT: launch_panel_right<T>(Fl, CT + (l.off - (int64_t)c0), l.count, l.kb, st); break;
@@ -514,6 +522,7 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
       ft.gfid = X->sn_base[p] + sn;
       ft.G = fbase + X->panel_fbase[p] + sh.g_off[sn];
       ft.U = upd_ptr[ft.gfid];
+      ft.ut = upd_tile[ft.gfid];
       ft.W = tbase + toff;
       toff += pad16((int64_t)ft.s * ft.s);
       ft.Z = tbase + toff;
@@ -688,8 +697,8 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
       for (int tj = 0; tj < ft.u; tj += 64)
         for (int ti = tj; ti < ft.u; ti += 64) {
           GemmTask<T> g{};
-          g.C = ft.U + (int64_t)tj * ft.u + ti;
-          g.ldc = ft.u;
+          g.C = ft.U + upd_index(ti, tj, ft.u, 64);   // the packed 64 x 64 tile (ti, tj)
+          g.ldc = 64;
           g.A = ft.ZD + ti;
           g.lda = ft.u;
           g.B = ft.Z + tj;
@@ -818,8 +827,8 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
               TcGemmTask t{};
               t.A = P.zd + (int64_t)(ti / 128) * P.ku * bb;
               t.B = P.z + (int64_t)(tj / 128) * P.ku * bb;
-              t.C = reinterpret_cast<float2*>(ft.U + (int64_t)tj * ft.u + ti);
-              t.ldc = ft.u;
+              t.C = reinterpret_cast<float2*>(ft.U + upd_index(ti, tj, ft.u, 128));   // packed 128 x 128 tile
+              t.ldc = 128;
               t.m = std::min(128, ft.u - ti);
               t.n = std::min(128, ft.u - tj);
               t.kb0 = 0;

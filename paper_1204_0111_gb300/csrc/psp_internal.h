@@ -123,17 +123,34 @@ struct GemmTask {
   int pad_;
 };
 
+// Update matrices F_BR (u x u, symmetric) keep only their lower tiles: tiles of ut x ut (ut = 64 for
+// fronts whose products run on CUDA cores, 128 for tensor-core fronts), tile (I, J), I >= J, stored
+// column of tiles after column of tiles, each tile column-major with leading dimension ut.
+__host__ __device__ __forceinline__ int64_t upd_tile_offset(int64_t I, int64_t J, int64_t ntiles, int ut) {
+  return (J * ntiles - J * (J - 1) / 2 + (I - J)) * (int64_t)ut * ut;
+}
+__host__ __device__ __forceinline__ int64_t upd_index(int r, int c, int u, int ut) {   // r >= c; ut 64 or 128
+  const int sh = ut == 128 ? 7 : 6;
+  const int nt = (u + ut - 1) >> sh;
+  return upd_tile_offset(r >> sh, c >> sh, nt, ut) + ((int64_t)(c & (ut - 1)) << sh) + (r & (ut - 1));
+}
+__host__ __device__ __forceinline__ int64_t upd_packed_elems(int u, int ut) {
+  const int64_t nt = (u + ut - 1) / ut;
+  return nt * (nt + 1) / 2 * (int64_t)ut * ut;
+}
+
 // A front in a level batch.
 template <typename T>
 struct FrontTask {
   T* G;        // (s+u) x s, ld = s+u
-  T* U;        // u x u update (F_BR), ld = u; nullptr for the root
+  T* U;        // u x u update (F_BR) in lower tiles of ut x ut (upd_index); nullptr for the root
   T* W;        // s x s work: inv(L_TL) under construction
   T* Z;        // u x s work: F_BL L^{-T}
   T* ZD;       // u x s work: Z D^{-1} (fronts whose products run on CUDA cores; else nullptr)
   int s, u;
   int panel, sn;
   int64_t gfid;
+  int ut, pad_;   // tile size of U
 };
 
 struct ColTask {   // a chunk of columns / rows of one front
@@ -149,7 +166,8 @@ void launch_scale_rhs(const BoxOp& op, const double2* f, double2* b, int nrhs, i
 
 template <typename T>
 void launch_assemble_impl(const FrontTask<T>* fronts, const ColTask* tasks, int ntasks, const ShapeDev* shapes,
-                          const BoxOp* boxops, T* const* upd_ptr, const int32_t* panel_shape, cudaStream_t st);
+                          const BoxOp* boxops, T* const* upd_ptr, const int32_t* upd_tile, const int32_t* panel_shape,
+                          cudaStream_t st);
 template <typename T>
 void launch_diag_ldlt(const FrontTask<T>* fronts, const int* list, int nlist, int kb, double tiny, int* status,
                       cudaStream_t st);
