@@ -91,7 +91,9 @@ typedef struct {
                           to 80 % of the device memory left after the factors and update matrices */
   int sweep_rhs_group; /* sweep schedule: most right-hand sides (1, 2, 4 or 8) one CTA carries through a
                           pass over a factor block; <= 0: as many as keep its shared memory within 64 KB */
-  int reserved[2];
+  int solve_rhs_group; /* psp_solve: most right-hand sides per GMRES run; <= 0: as many as fit the free
+                          device memory (single-problem handles) */
+  int reserved[1];
 } psp_options;
 
 /* Per-solve report filled by psp_solve (host struct). */
@@ -103,7 +105,9 @@ typedef struct {
   double relres_max;   /* max over rhs of the true ||b - A_s u|| / ||b||, b = s1 s2 s3 f */
   double solve_ms;     /* wall time of the solve (host clock, stream synchronised) */
   int status_front;    /* front id of a zero pivot, -1 if none */
-  int reserved[7];
+  int groups;          /* GMRES runs the right-hand sides were solved in (1 unless their Krylov bases
+                          did not fit the free device memory together) */
+  int reserved[6];
 } psp_solve_info;
 
 void psp_default_options(psp_options* opt);

@@ -236,7 +236,7 @@ struct psp_ctx_s {
   int zero_pivot_front = -1;
   bool use_tc = true;
   int tc_min_dim = 64;
-  int sweep_level_tasks = 608, sweep_ctas_per_sm = 8, sweep_rhs_group = 0;
+  int sweep_level_tasks = 608, sweep_ctas_per_sm = 8, sweep_rhs_group = 0, solve_rhs_group = 0;
   bool persistent_sweep = true;
   int64_t upd_arena_elems = 0;
   int64_t temp_budget_elems = 0;   // cap on setup temporaries per level group (0: what the device has free)
@@ -1735,6 +1735,7 @@ static void init_options(psp_ctx_s* X, const psp_options& o) {
   X->sweep_level_tasks = o.sweep_level_tasks > 0 ? o.sweep_level_tasks : 608;
   X->sweep_ctas_per_sm = o.sweep_ctas_per_sm > 0 ? o.sweep_ctas_per_sm : 8;
   X->sweep_rhs_group = o.sweep_rhs_group > 0 ? o.sweep_rhs_group : 0;
+  X->solve_rhs_group = o.solve_rhs_group > 0 ? o.solve_rhs_group : 0;
   X->temp_budget_elems = o.setup_temp_mb > 0 ? ((int64_t)o.setup_temp_mb << 20) / (o.precision == PSP_PREC_C64 ? 8 : 16) : 0;
 }
 
@@ -1887,13 +1888,45 @@ psp_status psp_solve(psp_handle X, const double* f, double* u, int nrhs, double 
     X->stage_out.ensure(bytes);
     ud = X->stage_out.as<double2>();
   }
-  psp_status rs = PSP_OK;
-  try {
-    solve_impl(X, fd, ud, nrhs, tol, k, maxit, info, st);
-  } catch (const Error& e) {
-    if (e.st != PSP_ERR_NOT_CONVERGED) throw;
-    rs = fail(e.st, e.msg);
+  // Right-hand sides per GMRES run: all of them when their Krylov bases (V and Z, 2k + 1 vectors)
+  // fit the free device memory, else groups that do.  The columns iterate independently, so the
+  // groups give the same result.  (Batches keep one run: their columns interleave problems.)
+  int group = nrhs;
+  if (X->probs.size() == 1) {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+      const double per_rhs = (2.0 * k + 6) * (double)X->N * sizeof(double2) +
+                             (2.0 * X->max_nloc + X->max_upd) * (double)X->elem_bytes;
+      const double held = (double)X->gm.bytes + X->ws_xf.bytes + X->ws_xb.bytes + X->ws_upd.bytes;
+      const double avail = (double)free_b + held - 2.0e9;
+      group = std::max(1, std::min(nrhs, (int)(avail / per_rhs)));
+    } else {
+      cudaGetLastError();
+    }
+    if (X->solve_rhs_group > 0) group = std::min(group, X->solve_rhs_group);
   }
+  psp_status rs = PSP_OK;
+  psp_solve_info agg{};
+  agg.converged = 1;
+  agg.status_front = -1;
+  for (int r0 = 0; r0 < nrhs; r0 += group) {
+    const int ng = std::min(group, nrhs - r0);
+    psp_solve_info gi{};
+    try {
+      solve_impl(X, fd + (int64_t)r0 * X->N, ud + (int64_t)r0 * X->N, ng, tol, k, maxit, &gi, st);
+    } catch (const Error& e) {
+      if (e.st != PSP_ERR_NOT_CONVERGED) throw;
+      rs = fail(e.st, e.msg);
+    }
+    agg.iterations = std::max(agg.iterations, gi.iterations);
+    agg.restarts = std::max(agg.restarts, gi.restarts);
+    agg.converged = agg.converged && gi.converged;
+    agg.applies += gi.applies;
+    agg.relres_max = std::max(agg.relres_max, gi.relres_max);
+    agg.solve_ms += gi.solve_ms;
+    agg.groups += 1;
+  }
+  if (info) *info = agg;
   if (!dev_out) {
     PSP_CK(cudaMemcpyAsync(u, ud, bytes, cudaMemcpyDeviceToHost, st));
     PSP_CK(cudaStreamSynchronize(st));

@@ -35,7 +35,7 @@ class Options(ctypes.Structure):
                 ("tc_min_dim", ctypes.c_int),
                 ("sweep_level_tasks", ctypes.c_int), ("sweep_ctas_per_sm", ctypes.c_int),
                 ("setup_temp_mb", ctypes.c_int), ("sweep_rhs_group", ctypes.c_int),
-                ("reserved", ctypes.c_int * 2)]
+                ("solve_rhs_group", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
 
 
 class KernelStat(ctypes.Structure):
@@ -46,7 +46,7 @@ class KernelStat(ctypes.Structure):
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int), ("converged", ctypes.c_int),
                 ("applies", ctypes.c_int), ("relres_max", ctypes.c_double), ("solve_ms", ctypes.c_double),
-                ("status_front", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+                ("status_front", ctypes.c_int), ("groups", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -154,14 +154,15 @@ class SweepingPreconditioner:
 
     def __init__(self, c, h, omega, gamma, panel_depth, pad=None, leaf=64, pml_C=4.0, alpha=2 * math.pi,
                  precision="c128", faces=63, mode="moving", stream=None, collect_stats=0, tensor_cores=True,
-                 tc_min_dim=0, sweep_level_tasks=0, sweep_ctas_per_sm=0, setup_temp_mb=0, sweep_rhs_group=0):
+                 tc_min_dim=0, sweep_level_tasks=0, sweep_ctas_per_sm=0, setup_temp_mb=0, sweep_rhs_group=0,
+                 solve_rhs_group=0):
         nz, ny, nx = c.shape
         self.nx, self.ny, self.nz = nx, ny, nz
         self.N = nx * ny * nz
         self.points = [self.N]
         g = Grid(nx, ny, nz, float(h))
         o = _options(pad, leaf, pml_C, alpha, precision, faces, mode, collect_stats, tensor_cores, tc_min_dim,
-                     sweep_level_tasks, sweep_ctas_per_sm, setup_temp_mb, sweep_rhs_group)
+                     sweep_level_tasks, sweep_ctas_per_sm, setup_temp_mb, sweep_rhs_group, solve_rhs_group)
         cp, n = _ptr_and_len(c, complex_=False)
         if n != self.N:
             raise ValueError("c has the wrong size")
@@ -263,7 +264,7 @@ class SweepingPreconditionerBatch(SweepingPreconditioner):
 
     def __init__(self, problems, pad=None, leaf=64, pml_C=4.0, alpha=2 * math.pi, precision="c128", faces=63,
                  mode="moving", stream=None, collect_stats=0, tensor_cores=True, tc_min_dim=0, sweep_level_tasks=0,
-                 sweep_ctas_per_sm=0, setup_temp_mb=0, sweep_rhs_group=0):
+                 sweep_ctas_per_sm=0, setup_temp_mb=0, sweep_rhs_group=0, solve_rhs_group=0):
         n = len(problems)
         grids = (Grid * n)()
         cs = (_P * n)()
@@ -287,7 +288,7 @@ class SweepingPreconditionerBatch(SweepingPreconditioner):
             self.points.append(nx * ny * nz)
         self.N = sum(self.points)
         o = _options(pad, leaf, pml_C, alpha, precision, faces, mode, collect_stats, tensor_cores, tc_min_dim,
-                     sweep_level_tasks, sweep_ctas_per_sm, setup_temp_mb, sweep_rhs_group)
+                     sweep_level_tasks, sweep_ctas_per_sm, setup_temp_mb, sweep_rhs_group, solve_rhs_group)
         h_ = _P()
         st = lib().psp_setup_batch(n, grids, cs, om, ga, de, ctypes.byref(o), _stream(stream), ctypes.byref(h_))
         self._finish(h_, st)
@@ -321,7 +322,7 @@ class SweepingPreconditionerBatch(SweepingPreconditioner):
 
 
 def _options(pad, leaf, pml_C, alpha, precision, faces, mode, collect_stats, tensor_cores, tc_min_dim,
-             sweep_level_tasks, sweep_ctas_per_sm, setup_temp_mb, sweep_rhs_group=0):
+             sweep_level_tasks, sweep_ctas_per_sm, setup_temp_mb, sweep_rhs_group=0, solve_rhs_group=0):
     o = Options()
     lib().psp_default_options(ctypes.byref(o))
     o.pml_C = float(pml_C)
@@ -338,6 +339,7 @@ def _options(pad, leaf, pml_C, alpha, precision, faces, mode, collect_stats, ten
     o.sweep_ctas_per_sm = int(sweep_ctas_per_sm)
     o.setup_temp_mb = int(setup_temp_mb)
     o.sweep_rhs_group = int(sweep_rhs_group)
+    o.solve_rhs_group = int(solve_rhs_group)
     return o
 
 

@@ -233,3 +233,22 @@ def test_sweep_autotuner_keeps_results():
     out = np.zeros_like(r)
     P.apply(r, out)
     assert rel(out, O.apply(r)) < 1e-10
+
+
+def test_solve_in_groups_of_right_hand_sides_equals_one_run():
+    # psp_solve may split the right-hand sides into several GMRES runs (when their bases do not fit
+    # in memory together); every column iterates independently, so the solutions are the same
+    case = CASES[0]
+    f = np.stack([wl.gaussian_source(case.nx, case.ny, case.nz, case.h, s)
+                  for s in ((0.5, 0.5, 0.5), (0.3, 0.6, 0.2), (0.7, 0.2, 0.8))])
+    P = gpu_for(case)
+    u1 = np.zeros_like(f)
+    i1 = P.solve(f, u1, tol=1e-6, k=10, maxit=300)
+    c = torch.from_numpy(case.c).cuda()
+    Q = psp.SweepingPreconditioner(c, case.h, case.omega, case.gamma, case.depth, pad=case.pad, leaf=case.leaf,
+                                   pml_C=case.C, alpha=case.alpha, faces=case.faces, solve_rhs_group=1)
+    u3 = np.zeros_like(f)
+    i3 = Q.solve(f, u3, tol=1e-6, k=10, maxit=300)
+    assert i1["groups"] == 1 and i3["groups"] == 3
+    assert np.array_equal(u1, u3)
+    assert i3["iterations"] == i1["iterations"] and i3["converged"] == 1
