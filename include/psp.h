@@ -93,7 +93,9 @@ typedef struct {
                           pass over a factor block; <= 0: as many as keep its shared memory within 64 KB */
   int solve_rhs_group; /* psp_solve: most right-hand sides per GMRES run; <= 0: as many as fit the free
                           device memory (single-problem handles) */
-  int reserved[1];
+  int test_sweep_stall; /* tests only: 1 makes one dependency of the persistent sweep impossible to
+                           meet, so its bounded wait (about 2 s) gives up; psp_solve then returns
+                           PSP_ERR_TIMEOUT and the device stays usable.  0 (default): off */
 } psp_options;
 
 /* Per-solve report filled by psp_solve (host struct). */

@@ -234,13 +234,15 @@ static int pick_rg(int nrhs, size_t per_rhs_bytes) {
 // wait is bounded anyway: a CTA that gives up sets status[2] and stops; the others then give up
 // at their next wait.
 // ---------------------------------------------------------------------------
-constexpr long long kWaitSpins = 20000000;   // x ~64 ns sleep: about a second
+constexpr long long kWaitCycles = 4000000000LL;   // SM clock cycles: about two seconds at 2 GHz
+constexpr long long kWaitSpins = 400000000LL;     // and a hard cap on polls, whatever the clock does
 
 __device__ __forceinline__ bool wait_count(const unsigned* p, unsigned target, int* status) {
+  const long long t0 = clock64();
   long long it = 0;
   while (*(volatile const unsigned*)p < target) {
     if (*(volatile int*)(status + 2) != 0) return false;
-    if (++it > kWaitSpins) {
+    if (++it > kWaitSpins || clock64() - t0 > kWaitCycles) {
       atomicExch(status + 2, 1);
       return false;
     }

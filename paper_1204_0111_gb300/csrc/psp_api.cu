@@ -237,6 +237,7 @@ struct psp_ctx_s {
   bool use_tc = true;
   int tc_min_dim = 64;
   int sweep_level_tasks = 608, sweep_ctas_per_sm = 8, sweep_rhs_group = 0, solve_rhs_group = 0;
+  bool test_sweep_stall = false;
   bool persistent_sweep = true;
   int64_t upd_arena_elems = 0;
   int64_t temp_budget_elems = 0;   // cap on setup temporaries per level group (0: what the device has free)
@@ -1008,6 +1009,7 @@ static void plan_solve(psp_ctx_s* X, cudaStream_t st) {
   meta.insert(meta.end(), step_front.begin(), step_front.end());
   X->meta_step_tasks = (int64_t)meta.size();
   meta.insert(meta.end(), step_tasks.begin(), step_tasks.end());
+  if (X->test_sweep_stall && steps.size() > 1) meta[X->meta_step_tasks] += 1;   // step 0 never "completes"
   X->meta_step_prev = (int64_t)meta.size();
   meta.insert(meta.end(), step_prev.begin(), step_prev.end());
   X->meta_front_base = o_up;
@@ -1736,6 +1738,7 @@ static void init_options(psp_ctx_s* X, const psp_options& o) {
   X->sweep_ctas_per_sm = o.sweep_ctas_per_sm > 0 ? o.sweep_ctas_per_sm : 8;
   X->sweep_rhs_group = o.sweep_rhs_group > 0 ? o.sweep_rhs_group : 0;
   X->solve_rhs_group = o.solve_rhs_group > 0 ? o.solve_rhs_group : 0;
+  X->test_sweep_stall = o.test_sweep_stall == 1;
   X->temp_budget_elems = o.setup_temp_mb > 0 ? ((int64_t)o.setup_temp_mb << 20) / (o.precision == PSP_PREC_C64 ? 8 : 16) : 0;
 }
 

@@ -252,3 +252,22 @@ def test_solve_in_groups_of_right_hand_sides_equals_one_run():
     assert i1["groups"] == 1 and i3["groups"] == 3
     assert np.array_equal(u1, u3)
     assert i3["iterations"] == i1["iterations"] and i3["converged"] == 1
+
+
+def test_sweep_wait_gives_up_and_the_device_stays_usable():
+    # a dependency of the persistent sweep that can never be met (test option): its bounded wait
+    # gives up after about two seconds, psp_solve reports PSP_ERR_TIMEOUT, and a normal handle
+    # solves afterwards on the same device
+    case = CASES[0]
+    c = torch.from_numpy(case.c).cuda()
+    f = wl.gaussian_source(case.nx, case.ny, case.nz, case.h, (0.5, 0.5, 0.5))[None, :].copy()
+    P = psp.SweepingPreconditioner(c, case.h, case.omega, case.gamma, case.depth, pad=case.pad, leaf=case.leaf,
+                                   pml_C=case.C, alpha=case.alpha, faces=case.faces, test_sweep_stall=1)
+    u = np.zeros_like(f)
+    with pytest.raises(psp.PSPError) as e:
+        P.solve(f, u, tol=1e-6, k=10, maxit=50)
+    assert e.value.name == "PSP_ERR_TIMEOUT"
+    P.close()
+    Q = gpu_for(case)
+    u = np.zeros_like(f)
+    assert Q.solve(f, u, tol=1e-6, k=10, maxit=300)["converged"] == 1
