@@ -567,7 +567,7 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
           ea += uc * (uc + 1) / 2;
         }
         la.flops += 2.0 * ea;
-        la.bytes += es * (2.0 * ea + (double)(ft.s + ft.u) * ft.s + (double)ft.s * ft.s + (double)ft.u * ft.u);
+        la.bytes += es * (2.0 * ea + (double)(ft.s + ft.u) * ft.s + (double)ft.s * ft.s + 0.5 * ft.u * (ft.u + 1.0));
       }
       launches.push_back(la);
     }
