@@ -2063,7 +2063,7 @@ psp_status psp_tune_sweep(psp_handle X, int nrhs, int reps, void* stream, psp_sw
     };
     for (int lt : {152, 304, 608, 1216, 2432})
       if (lt != best.lt) consider({lt, best.cps, best.rg});
-    for (int cps : {2, 4, 8})
+    for (int cps : {2, 3, 4, 6, 8})
       if (cps != best.cps) consider({best.lt, cps, best.rg});
     if (nrhs > 1)
       for (int rg : {1, 2, 4, 8})

@@ -227,8 +227,8 @@ def test_sweep_autotuner_keeps_results():
     O = oracle_for(case)
     t = P.tune_sweep(nrhs=2, reps=1)
     assert t["sweep_level_tasks"] in (152, 304, 608, 1216, 2432)
-    assert t["sweep_ctas_per_sm"] in (2, 4, 8) and t["sweep_rhs_group"] in (0, 1, 2)
-    assert t["candidates"] >= 8 and 0 < t["best_ms"] <= t["initial_ms"]
+    assert t["sweep_ctas_per_sm"] in (2, 3, 4, 6, 8) and t["sweep_rhs_group"] in (0, 1, 2)
+    assert t["candidates"] >= 10 and 0 < t["best_ms"] <= t["initial_ms"]
     r = wl.random_vector(case.N, 2, seed=44)
     out = np.zeros_like(r)
     P.apply(r, out)
