@@ -308,15 +308,30 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs<T> a) {
   }
   __syncthreads();
   const int nrg = (a.cx.nrhs + RG - 1) / RG;
+  // thread 0 only: the current task's queue entry, task, front base and step counter base.  They
+  // are loaded for the next task while this one signals its completion, so a task's dependency
+  // check starts without a chain of dependent global loads.
+  QueueEntry ce{};
+  SolveTask ctk{};
+  int c_fb = 0, c_sfb = 0, c_idx = -1;
+  auto fetch = [&](int i) {
+    ce = a.queue[i];
+    ctk = a.tasks[ce.task];
+    const int panel = tab_smem ? s_step[ce.step].panel : a.steps[ce.step].panel;
+    const int shape = tab_smem ? s_panel[panel].shape : a.panels[panel].shape;
+    c_fb = a.front_base[shape];
+    c_sfb = a.step_front_base[ce.step];
+    c_idx = i;
+  };
   for (;;) {
     if (threadIdx.x == 0) s_idx = s_next;
     __syncthreads();
     const int idx = s_idx;
     if (idx >= a.nqueue) break;
     if (threadIdx.x == 0) {
+      if (c_idx != idx) fetch(idx);
       s_next = (int)atomicAdd(a.queue_head, 1u);   // next task, fetched while this one runs
-      const QueueEntry e = a.queue[idx];
-      const SweepStep sp = tab_smem ? s_step[e.step] : a.steps[e.step];
+      const SweepStep sp = tab_smem ? s_step[ce.step] : a.steps[ce.step];
       const PanelSweep pi = tab_smem ? s_panel[sp.panel] : a.panels[sp.panel];
       SolveCtx<T>& cx = s_cx;
       cx.sh = tab_smem ? s_shape[pi.shape] : a.shapes[pi.shape];
@@ -341,33 +356,28 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs<T> a) {
         cx.xb = a.cx.xb + (int64_t)sp.prob * a.cx.n_loc * a.cx.nrhs;
         cx.upd = a.cx.upd + (int64_t)sp.prob * a.cx.upd_ld * a.cx.nrhs;
       }
-      const SolveTask tk = a.tasks[e.task];
-      s_tk = tk;
-      s_dir = e.dir;
-      s_R = e.R;
+      s_tk = ctk;
+      s_dir = ce.dir;
+      s_R = ce.R;
     }
     __syncthreads();
     prefetch_task<T>(s_tk, s_dir, s_cx);
     if (threadIdx.x == 0) {
-      const QueueEntry e = a.queue[idx];
-      const SolveTask tk = s_tk;
       const SolveCtx<T>& cx = s_cx;
-      const int shape = tab_smem ? s_panel[s_step[e.step].panel].shape : a.panels[a.steps[e.step].panel].shape;
-      const int fb = a.front_base[shape];
-      const unsigned* up = a.done_up + a.step_front_base[e.step];
-      const unsigned* down = a.done_down + a.step_front_base[e.step];
+      const unsigned* up = a.done_up + c_sfb;
+      const unsigned* down = a.done_down + c_sfb;
       bool ok = true;
-      if (e.dir == 0) {
-        const int prev = a.step_prev ? a.step_prev[e.step] : e.step - 1;
+      if (ce.dir == 0) {
+        const int prev = a.step_prev ? a.step_prev[ce.step] : ce.step - 1;
         if (prev >= 0) ok = wait_count(a.step_done + prev, (unsigned)a.step_tasks[prev], a.status);
-        for (int c = cx.sh.child_ptr[tk.sn]; ok && c < cx.sh.child_ptr[tk.sn + 1]; ++c) {
+        for (int c = cx.sh.child_ptr[ctk.sn]; ok && c < cx.sh.child_ptr[ctk.sn + 1]; ++c) {
           const int ch = cx.sh.child_idx[c];
-          ok = wait_count(up + ch, (unsigned)a.ntask_up[fb + ch], a.status);
+          ok = wait_count(up + ch, (unsigned)a.ntask_up[c_fb + ch], a.status);
         }
       } else {
-        const int par = cx.sh.parent[tk.sn];
-        ok = par >= 0 ? wait_count(down + par, (unsigned)a.ntask_down[fb + par], a.status)
-                      : wait_count(up + tk.sn, (unsigned)a.ntask_up[fb + tk.sn], a.status);
+        const int par = cx.sh.parent[ctk.sn];
+        ok = par >= 0 ? wait_count(down + par, (unsigned)a.ntask_down[c_fb + par], a.status)
+                      : wait_count(up + ctk.sn, (unsigned)a.ntask_up[c_fb + ctk.sn], a.status);
       }
       __threadfence();
       s_ok = ok;
@@ -382,12 +392,12 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs<T> a) {
       __syncthreads();
     }
     if (threadIdx.x == 0) {
-      // completion counters of this task's step and front (the queue entry is re-read: cheap)
-      const QueueEntry e = a.queue[idx];
-      const int front0 = a.step_front_base[e.step];
+      // completion counters of this task's step and front, then the next task's tables
       __threadfence();
-      atomicAdd((dir == 0 ? a.done_up : a.done_down) + front0 + tk.sn, 1u);
-      atomicAdd(a.step_done + e.step, 1u);
+      atomicAdd((dir == 0 ? a.done_up : a.done_down) + c_sfb + tk.sn, 1u);
+      atomicAdd(a.step_done + ce.step, 1u);
+      const int nx = s_next;
+      if (nx < a.nqueue) fetch(nx);
     }
   }
 }
