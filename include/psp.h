@@ -69,7 +69,9 @@ typedef enum {
 
 /* Options; psp_default_options() fills the defaults shown. */
 typedef struct {
-  double pml_C;       /* PML amplitude "C" (§3), default 4.0 */
+  double pml_C;       /* PML amplitude "C" (§3) of the stretch sigma = (C / (gamma h)) t^2, default 4.0;
+                         a wave of speed c decays by exp(-C / (3 c)) across the layer, so in media
+                         faster than 1 pass the amplitude times the fastest speed */
   double alpha;       /* damping of Eq. (1.5), default 2*pi */
   int pad_depth;      /* artificial PML planes prefixed to each panel (Alg. 1.4); -1 = pml_gamma */
   int leaf_size;      /* nested-dissection leaf: boxes with nx*ny*depth <= leaf are leaves; default 64 */
