@@ -998,7 +998,7 @@ static void plan_solve(psp_ctx_s* X, cudaStream_t st) {
   X->sweep_nqueue = (int)queue.size();
   upload_async(X->d_sweep_steps, steps, st);
   upload_async(X->d_sweep_queue, queue, st);
-  // metadata: front_base | ntask_up | ntask_down | step_front | step_tasks
+  // metadata: front_base | ntask_up | ntask_down | step_front | step_tasks | step_prev
   std::vector<int> meta;
   meta.insert(meta.end(), front_base.begin(), front_base.end());
   const int64_t o_up = (int64_t)meta.size();
