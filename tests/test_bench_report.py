@@ -52,3 +52,22 @@ def test_gpu_main_uses_only_defined_names(bench):
     names = {ins.argval for ins in dis.get_instructions(code) if ins.opname in ("LOAD_GLOBAL",)}
     for n in names:
         assert hasattr(bench, n) or n in dir(__builtins__) or n in __builtins__, n
+
+
+def test_roofline_generic_bounds_and_rates(bench):
+    # the sweep against HBM: algorithmic bytes over event time
+    r = bench.roofline_generic("k_sweep", rec(27, 1000.0, 1e12, 5e11), 0.9, "t")
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert abs(r["achieved"] - 500.0) < 1e-9 and abs(r["frac"] - 500.0 / r["peak"]) < 1e-12
+    # the tensor-core GEMM against the TF32 peak derived from the bf16 one
+    t = bench.roofline_generic("k_tc_gemm", rec(16, 100.0, 1e13, 1e10), 0.1, "t")
+    assert t["bound"] == "tensor" and abs(t["achieved"] - 100.0) < 1e-9
+    pk, _ = bench._peaks()
+    assert abs(t["peak"] - pk["bf16_tflops"] * 1.1 / 2.25) < 1e-9
+    # a CUDA-core kernel against the FP32 ALU peak
+    g = bench.roofline_generic("k_gemm", rec(10, 10.0, 1e11, 1e9), 0.05, "t")
+    assert g["bound"] == "alu" and abs(g["peak"] - 152 * 128 * 2 * 2.07e9 / 1e12) < 1e-9
+
+
+def test_job_rate_counts_every_rank(bench):
+    assert bench.job_rate(4, 5, 2.0) == 10.0
