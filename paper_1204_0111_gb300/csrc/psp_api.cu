@@ -11,6 +11,7 @@
 #include <memory>
 #include <new>
 #include <stdexcept>
+#include <thread>
 #include <tuple>
 #include <type_traits>
 #include <string>
@@ -1247,6 +1248,7 @@ static void build_problem(psp_ctx_s* X, const double* c, cudaStream_t st) {
   std::vector<int32_t> cplane_all;
   std::vector<int64_t> p_s3n(X->m), p_s3h(X->m), p_cpl(X->m);
   std::map<std::tuple<int, int, int>, int> shape_idx;
+  std::vector<int> shape_depth;   // box depth of each distinct shape
   X->shape_of.assign(X->m, 0);
   for (int i = 0; i < X->m; ++i) {
     const int z0 = X->z0[i], z1 = X->z1[i];
@@ -1287,11 +1289,23 @@ static void build_problem(psp_ctx_s* X, const double* c, cudaStream_t st) {
       const int idx = (int)X->shapes.size();
       shape_idx[key] = idx;
       X->shapes.emplace_back();
-      build_shape(X->shapes.back(), nx, ny, D, X->leaf);
+      shape_depth.push_back(D);
       X->shape_of[i] = idx;
     } else {
       X->shape_of[i] = it->second;
     }
+  }
+  // the distinct shapes' symbolic analyses are independent: build them on a few host threads
+  {
+    const int ns = (int)X->shapes.size();
+    const int nthreads = std::max(1, std::min(ns, 8));
+    auto worker = [&](int t) {
+      for (int si = t; si < ns; si += nthreads) build_shape(X->shapes[si], nx, ny, shape_depth[si], X->leaf);
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nthreads; ++t) pool.emplace_back(worker, t);
+    worker(0);
+    for (auto& th : pool) th.join();
   }
   // global plane map (identity) for the full-domain operators
   const int64_t gcpl = (int64_t)cplane_all.size();
