@@ -28,6 +28,14 @@
  *    psp_last_error() returns a thread-local message for the last failure.
  *    A handle stays destroyable after any error.
  *  - A handle must not be used from two host threads at once.
+ *  - A handle belongs to the CUDA device that was current when it was set up: every later call
+ *    must run with that device current and pass device pointers of that device (or host
+ *    pointers); otherwise it returns PSP_ERR_ARG.
+ *  - The sweep's dependency waits are bounded (about two seconds).  A wait that gives up leaves
+ *    that application's output incomplete and raises a flag that stays set until it is reported:
+ *    by psp_apply with a host `out` (which synchronises), by psp_solve, or by psp_check_status.
+ *    Calls that only enqueue work on device pointers return before the sweep has run and cannot
+ *    report it themselves.
  */
 #ifndef PSP_H
 #define PSP_H
@@ -170,6 +178,9 @@ psp_status psp_batch_layout(psp_handle h, int* nprob, int64_t* points, int capac
  * with T_i the Alg. 1.3 application of the factored H_i (extend by zero over the
  * pad, multifrontal solve, keep the panel's planes).  rhs and out are nrhs
  * complex vectors of length N (host or device); out may alias rhs.
+ * With a host `out` the call synchronises the stream and returns PSP_ERR_TIMEOUT if a dependency
+ * wait of the sweep gave up; with a device `out` it returns once the work is enqueued, and a give-up
+ * is reported by the next psp_solve or psp_check_status.
  */
 psp_status psp_apply(psp_handle h, const double* rhs, double* out, int nrhs, void* stream);
 
@@ -185,10 +196,14 @@ psp_status psp_apply(psp_handle h, const double* rhs, double* out, int nrhs, voi
  *    live in one file-scope device array of 16 MiB that every GPU context loading the library
  *    reserves until the process exits.  When a problem needs more for the given nrhs the call
  *    returns PSP_ERR_ARG with the size it needs; use psp_apply then.
- *  - rhs and out are DEVICE pointers (N x nrhs, as for psp_apply; out may alias rhs).  Host
- *    pointers are rejected with PSP_ERR_ARG: staging them would need an allocation.
- *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
- *    device current; make that first call before any stream capture.
+ *  - rhs and out are DEVICE pointers of the handle's device (N x nrhs, as for psp_apply; out may
+ *    alias rhs).  Host pointers are rejected with PSP_ERR_ARG: staging them would need an allocation.
+ *  - The first call in a CUDA context of a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; a context created anew on the device (after
+ *    cudaDeviceReset, for instance) gets its first call too.  Make that first call before any stream
+ *    capture.
+ *  - Like psp_apply with device pointers, the call only enqueues the sweep: a dependency wait that
+ *    gives up is reported by the next psp_solve or psp_check_status.
  *  - Every call shares the one array, which keeps the last call's contents.  Nothing in it has to
  *    start at zero: the sweep writes each work entry before it reads it.  Calls that overlap on the
  *    GPU (other streams, handles or host threads) race on the array and give wrong results.
@@ -276,6 +291,13 @@ typedef struct {
 } psp_sweep_tuning;
 
 psp_status psp_tune_sweep(psp_handle h, int nrhs, int reps, void* stream, psp_sweep_tuning* out);
+
+/*
+ * psp_check_status - the paper has no counterpart: synchronises `stream` and reports whether a
+ * bounded dependency wait of any sweep on this handle gave up since setup or the last report
+ * (PSP_ERR_TIMEOUT, after which the flag is cleared), else PSP_OK.  The device stays usable.
+ */
+psp_status psp_check_status(psp_handle h, void* stream);
 
 psp_status psp_destroy(psp_handle h);
 const char* psp_status_string(psp_status s);

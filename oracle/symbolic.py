@@ -118,12 +118,3 @@ def nested_dissection(nx: int, ny: int, nz: int, leaf: int) -> Symbolic:
         e = np.sort(e[outside])
         sn.struct = order[e]
     return Symbolic(nx, ny, nz, leaf, sns, elim, order)
-
-
-def tree_levels(sym: Symbolic) -> np.ndarray:
-    """Height of every supernode (leaves 0, parent = 1 + max child height)."""
-    lev = np.zeros(len(sym.supernodes), dtype=np.int64)
-    for f, sn in enumerate(sym.supernodes):
-        if sn.children:
-            lev[f] = 1 + max(lev[c] for c in sn.children)
-    return lev

@@ -237,13 +237,16 @@ static int pick_rg(int nrhs, size_t per_rhs_bytes) {
 constexpr long long kWaitCycles = 4000000000LL;   // SM clock cycles: about two seconds at 2 GHz
 constexpr long long kWaitSpins = 400000000LL;     // and a hard cap on polls, whatever the clock does
 
-__device__ __forceinline__ bool wait_count(const unsigned* p, unsigned target, int* status) {
+// a wait that gives up sets status[2] (cleared before every sweep) and the handle's sticky flag
+// (cleared only when the host reads it)
+__device__ __forceinline__ bool wait_count(const unsigned* p, unsigned target, int* status, int* sticky) {
   const long long t0 = clock64();
   long long it = 0;
   while (*(volatile const unsigned*)p < target) {
     if (*(volatile int*)(status + 2) != 0) return false;
     if (++it > kWaitSpins || clock64() - t0 > kWaitCycles) {
       atomicExch(status + 2, 1);
+      if (sticky) atomicExch(sticky, 1);
       return false;
     }
     __nanosleep(32);
@@ -369,15 +372,15 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs<T> a) {
       bool ok = true;
       if (ce.dir == 0) {
         const int prev = a.step_prev ? a.step_prev[ce.step] : ce.step - 1;
-        if (prev >= 0) ok = wait_count(a.step_done + prev, (unsigned)a.step_tasks[prev], a.status);
+        if (prev >= 0) ok = wait_count(a.step_done + prev, (unsigned)a.step_tasks[prev], a.status, a.sticky);
         for (int c = cx.sh.child_ptr[ctk.sn]; ok && c < cx.sh.child_ptr[ctk.sn + 1]; ++c) {
           const int ch = cx.sh.child_idx[c];
-          ok = wait_count(up + ch, (unsigned)a.ntask_up[c_fb + ch], a.status);
+          ok = wait_count(up + ch, (unsigned)a.ntask_up[c_fb + ch], a.status, a.sticky);
         }
       } else {
         const int par = cx.sh.parent[ctk.sn];
-        ok = par >= 0 ? wait_count(down + par, (unsigned)a.ntask_down[c_fb + par], a.status)
-                      : wait_count(up + ctk.sn, (unsigned)a.ntask_up[c_fb + ctk.sn], a.status);
+        ok = par >= 0 ? wait_count(down + par, (unsigned)a.ntask_down[c_fb + par], a.status, a.sticky)
+                      : wait_count(up + ctk.sn, (unsigned)a.ntask_up[c_fb + ctk.sn], a.status, a.sticky);
       }
       __threadfence();
       s_ok = ok;

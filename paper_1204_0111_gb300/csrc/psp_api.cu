@@ -76,12 +76,21 @@ static void upload_async(DevBuf& d, const std::vector<U>& h, cudaStream_t st) {
   if (!h.empty()) PSP_CK(cudaMemcpyAsync(d.p, h.data(), h.size() * sizeof(U), cudaMemcpyHostToDevice, st));
 }
 
+// true for device (or managed) memory, false for host memory; device memory of a device other than
+// the current one is an argument error
 static bool is_device_pointer(const void* p) {
   cudaPointerAttributes a;
   cudaError_t e = cudaPointerGetAttributes(&a, p);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return false;
+  }
+  if (a.type == cudaMemoryTypeDevice) {
+    int cur = -1;
+    PSP_CK(cudaGetDevice(&cur));
+    if (a.device != cur)
+      throw Error{PSP_ERR_ARG, "a pointer is memory of device " + std::to_string(a.device) + ", not of the current device " +
+                                   std::to_string(cur)};
   }
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
@@ -235,6 +244,7 @@ struct psp_ctx_s {
   DevBuf gm;
   int gm_nrhs = 0, gm_k = 0;
   int zero_pivot_front = -1;
+  int device = -1;          // CUDA device current at setup; every later call must run with it current
   bool use_tc = true;
   int tc_min_dim = 64;
   int sweep_level_tasks = 608, sweep_ctas_per_sm = 8, sweep_rhs_group = 0, solve_rhs_group = 0;
@@ -1131,6 +1141,7 @@ static void apply_core(psp_ctx_s* X, double2* u, int nrhs, T* xf, T* xb, T* upd,
     const int64_t nfront_steps = ((int64_t)X->sweep_sync_words - 5 - X->sweep_nsteps) / 2;
     sa.queue_head = sync;
     sa.status = reinterpret_cast<int*>(sync + 1);
+    sa.sticky = X->d_status.as<int>() + 2;
     sa.step_done = sync + 5;
     sa.done_up = sync + 5 + X->sweep_nsteps;
     sa.done_down = sa.done_up + nfront_steps;
@@ -1198,6 +1209,25 @@ psp_status set_error(psp_status s, const char* msg) {
 }
 
 int64_t handle_points(const psp_ctx_s* X) { return X->d_factor.p ? X->N : -1; }
+int handle_device(const psp_ctx_s* X) { return X->device; }
+
+// the handle's device must be current (its factors and tables live there)
+static void check_device(const psp_ctx_s* X) {
+  int cur = -1;
+  PSP_CK(cudaGetDevice(&cur));
+  if (cur != X->device)
+    throw Error{PSP_ERR_ARG, "the handle was set up on device " + std::to_string(X->device) + ", but device " +
+                                 std::to_string(cur) + " is current"};
+}
+
+// reads and clears the handle's sticky flag of a sweep wait that gave up (the stream is synchronised)
+static bool sweep_gave_up(psp_ctx_s* X, cudaStream_t st) {
+  int flag = 0;
+  PSP_CK(cudaMemcpyAsync(&flag, X->d_status.as<int>() + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PSP_CK(cudaStreamSynchronize(st));
+  if (flag) PSP_CK(cudaMemsetAsync(X->d_status.as<int>() + 2, 0, sizeof(int), st));
+  return flag != 0;
+}
 
 static void apply_dispatch(psp_ctx_s* X, double2* u, int nrhs, cudaStream_t st) {
   if (X->prec == PSP_PREC_C64) apply_impl<float2>(X, u, nrhs, st);
@@ -1248,7 +1278,8 @@ static void build_problem(psp_ctx_s* X, const double* c, cudaStream_t st) {
   std::vector<int32_t> cplane_all;
   std::vector<int64_t> p_s3n(X->m), p_s3h(X->m), p_cpl(X->m);
   std::map<std::tuple<int, int, int>, int> shape_idx;
-  std::vector<int> shape_depth;   // box depth of each distinct shape
+  std::vector<int> shape_depth;   // box depth of each distinct shape (same index as X->shapes)
+  X->shapes.clear();
   X->shape_of.assign(X->m, 0);
   for (int i = 0; i < X->m; ++i) {
     const int z0 = X->z0[i], z1 = X->z1[i];
@@ -1295,17 +1326,31 @@ static void build_problem(psp_ctx_s* X, const double* c, cudaStream_t st) {
       X->shape_of[i] = it->second;
     }
   }
-  // the distinct shapes' symbolic analyses are independent: build them on a few host threads
+  // the distinct shapes' symbolic analyses are independent: build them on a few host threads.  A
+  // worker catches what build_shape throws (a consistency error, bad_alloc); the first one is
+  // rethrown here after every thread has joined, so it reaches the ABI as a status.
   {
     const int ns = (int)X->shapes.size();
     const int nthreads = std::max(1, std::min(ns, 8));
+    std::vector<std::exception_ptr> errs(nthreads);
     auto worker = [&](int t) {
-      for (int si = t; si < ns; si += nthreads) build_shape(X->shapes[si], nx, ny, shape_depth[si], X->leaf);
+      try {
+        for (int si = t; si < ns; si += nthreads) build_shape(X->shapes[si], nx, ny, shape_depth[si], X->leaf);
+      } catch (...) {
+        errs[t] = std::current_exception();
+      }
     };
     std::vector<std::thread> pool;
-    for (int t = 1; t < nthreads; ++t) pool.emplace_back(worker, t);
+    try {
+      for (int t = 1; t < nthreads; ++t) pool.emplace_back(worker, t);
+    } catch (...) {
+      for (auto& th : pool) th.join();
+      throw;
+    }
     worker(0);
     for (auto& th : pool) th.join();
+    for (auto& e : errs)
+      if (e) std::rethrow_exception(e);
   }
   // global plane map (identity) for the full-domain operators
   const int64_t gcpl = (int64_t)cplane_all.size();
@@ -1623,10 +1668,7 @@ static void solve_impl(psp_ctx_s* X, const double2* f, double2* x, int nrhs_in, 
       small("k_arnoldi_step", [&] { launch_arnoldi_step(Ls, j, h1, h2, nrm, st); });
       axpby(w, V + (int64_t)(j + 1) * ldv_vec, scl, 0);
       PSP_CK(cudaMemcpyAsync(hres.data(), resid, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
-      int sweep_status = 0;
-      PSP_CK(cudaMemcpyAsync(&sweep_status, X->d_sweep_sync.as<unsigned>() + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
-      PSP_CK(cudaStreamSynchronize(st));
-      if (sweep_status != 0) throw Error{PSP_ERR_TIMEOUT, "a dependency wait of the sweep gave up"};
+      if (sweep_gave_up(X, st)) throw Error{PSP_ERR_TIMEOUT, "a dependency wait of the sweep gave up"};
       ++total_it;
       bool all_done = true;
       for (int r = 0; r < nrhs; ++r) {
@@ -1783,6 +1825,7 @@ psp_status psp_setup(const psp_grid* g, const double* c, double omega, int pml_g
   init_problem(X, g, omega, pml_gamma, panel_depth, o);
   *out = X;
   PSP_TRY
+  PSP_CK(cudaGetDevice(&X->device));
   setup_impl(X, c, (cudaStream_t)stream);
   return PSP_OK;
   PSP_CATCH
@@ -1818,6 +1861,7 @@ psp_status psp_setup_batch(int nprob, const psp_grid* grids, const double* const
   init_problem(B, grids, omega[0], pml_gamma[0], panel_depth[0], o);
   *out = B;
   PSP_TRY
+  PSP_CK(cudaGetDevice(&B->device));
   setup_batch_impl(B, nprob, c, (cudaStream_t)stream);
   return PSP_OK;
   PSP_CATCH
@@ -1834,9 +1878,11 @@ psp_status psp_apply(psp_handle X, const double* rhs, double* out, int nrhs, voi
   if (!X || !rhs || !out || nrhs < 1) return fail(PSP_ERR_ARG, "bad apply arguments");
   if (!X->d_factor.p) return fail(PSP_ERR_STATE, "handle has no factorisation");
   PSP_TRY
+  check_device(X);
   cudaStream_t st = (cudaStream_t)stream;
   const size_t bytes = (size_t)X->N * nrhs * sizeof(double2);
   const bool dev_out = is_device_pointer(out);
+  (void)is_device_pointer(rhs);
   double2* u;
   if (dev_out) {
     u = reinterpret_cast<double2*>(out);
@@ -1849,6 +1895,7 @@ psp_status psp_apply(psp_handle X, const double* rhs, double* out, int nrhs, voi
   if (!dev_out) {
     PSP_CK(cudaMemcpyAsync(out, u, bytes, cudaMemcpyDeviceToHost, st));
     PSP_CK(cudaStreamSynchronize(st));
+    if (sweep_gave_up(X, st)) return fail(PSP_ERR_TIMEOUT, "a dependency wait of the sweep gave up; out is incomplete");
   }
   return PSP_OK;
   PSP_CATCH
@@ -1857,6 +1904,7 @@ psp_status psp_apply(psp_handle X, const double* rhs, double* out, int nrhs, voi
 psp_status psp_matvec(psp_handle X, int which, const double* x, double* y, int nrhs, void* stream) {
   if (!X || !x || !y || nrhs < 1 || (which != 0 && which != 1)) return fail(PSP_ERR_ARG, "bad matvec arguments");
   PSP_TRY
+  check_device(X);
   cudaStream_t st = (cudaStream_t)stream;
   const size_t bytes = (size_t)X->N * nrhs * sizeof(double2);
   const double2* xd = reinterpret_cast<const double2*>(x);
@@ -1891,6 +1939,7 @@ psp_status psp_solve(psp_handle X, const double* f, double* u, int nrhs, double 
   if (!X || !f || !u || nrhs < 1 || !(tol > 0) || k < 1 || maxit < 1) return fail(PSP_ERR_ARG, "bad solve arguments");
   if (!X->d_factor.p) return fail(PSP_ERR_STATE, "handle has no factorisation");
   PSP_TRY
+  check_device(X);
   cudaStream_t st = (cudaStream_t)stream;
   const size_t bytes = (size_t)X->N * nrhs * sizeof(double2);
   const double2* fd = reinterpret_cast<const double2*>(f);
@@ -1991,6 +2040,7 @@ psp_status psp_export_front(psp_handle X, int panel, int sn, double* buf, int* s
   if (u) *u = sh.u[sn];
   if (!buf) return PSP_OK;
   PSP_TRY
+  check_device(X);
   const int64_t n = (int64_t)(sh.s[sn] + sh.u[sn]) * sh.s[sn];
   const char* src = X->d_factor.as<char>() + (X->panel_fbase[panel] + sh.g_off[sn]) * (int64_t)X->elem_bytes;
   if (X->elem_bytes == 16) {
@@ -2035,6 +2085,7 @@ psp_status psp_tune_sweep(psp_handle X, int nrhs, int reps, void* stream, psp_sw
   if (!X || nrhs < 1 || reps < 1) return fail(PSP_ERR_ARG, "bad tuning arguments");
   if (!X->d_factor.p) return fail(PSP_ERR_STATE, "handle has no factorisation");
   PSP_TRY
+  check_device(X);
   cudaStream_t st = (cudaStream_t)stream;
   DevBuf u;
   const size_t bytes = (size_t)X->N * nrhs * sizeof(double2);
@@ -2106,6 +2157,17 @@ psp_status psp_tune_sweep(psp_handle X, int nrhs, int reps, void* stream, psp_sw
     out->initial_ms = initial_ms;
     out->best_ms = best_ms;
   }
+  return PSP_OK;
+  PSP_CATCH
+}
+
+psp_status psp_check_status(psp_handle X, void* stream) {
+  if (!X) return fail(PSP_ERR_ARG, "NULL handle");
+  if (!X->d_status.p) return PSP_OK;
+  PSP_TRY
+  check_device(X);
+  if (sweep_gave_up(X, (cudaStream_t)stream))
+    return fail(PSP_ERR_TIMEOUT, "a dependency wait of a sweep gave up since the last check");
   return PSP_OK;
   PSP_CATCH
 }

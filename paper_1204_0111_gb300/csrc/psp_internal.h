@@ -16,6 +16,7 @@ namespace psp {
 size_t apply_workspace_bytes(const psp_ctx_s* X, int nrhs);
 psp_status apply_with_workspace(psp_ctx_s* X, double2* u, int nrhs, void* ws, cudaStream_t st);
 int64_t handle_points(const psp_ctx_s* X);   // N, or -1 when the handle has no factorisation
+int handle_device(const psp_ctx_s* X);       // CUDA device the handle was set up on
 psp_status set_error(psp_status s, const char* msg);
 
 // ---------------------------------------------------------------------------
@@ -289,6 +290,7 @@ struct SweepArgs {
   unsigned* done_down;
   unsigned* step_done;          // per step completed tasks (zeroed per sweep)
   int* status;                  // status[2] set when a wait gave up
+  int* sticky;                  // also set then; kept until the host reads it (psp_check_status)
   // batches of independent problems (nprobs > 1): each problem's steps form their own chain
   int nprobs;
   const ProblemSweep* probs;    // per problem; cx's vectors and work vectors are offset per problem

@@ -6,6 +6,8 @@
 // cudaMalloc would synchronise the device.  psp_apply grows its work vectors on demand; this entry
 // point instead uses one file-scope __device__ array, so it never calls cudaMalloc, cudaFree or any
 // other allocating routine.
+#include <cuda.h>
+
 #include <mutex>
 #include <string>
 
@@ -22,33 +24,58 @@ namespace {
 
 std::mutex g_scratch_mu;
 constexpr int kMaxDevices = 128;
-void* g_scratch_addr[kMaxDevices] = {};  // device address of psp_apply_scratch, per device ordinal
+// device address of psp_apply_scratch per device ordinal, and the context it was resolved in: a
+// context created anew on that device (after cudaDeviceReset, say) loads the module again, and the
+// address is then resolved again
+void* g_scratch_addr[kMaxDevices] = {};
+CUcontext g_scratch_ctx[kMaxDevices] = {};
 
-// Once per device, with that device current: resolve the array's device address.
-psp_status scratch_address(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return psp::set_error(PSP_ERR_CUDA, cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return psp::set_error(PSP_ERR_CUDA, "device ordinal out of range");
-  std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
+using CtxGetCurrent = CUresult (*)(CUcontext*);
+
+// cuCtxGetCurrent through the runtime's driver entry-point table (the library does not link libcuda)
+CtxGetCurrent ctx_get_current() {
+  static CtxGetCurrent fn = [] {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, psp_apply_scratch);
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    return reinterpret_cast<CtxGetCurrent>(p);
+  }();
+  return fn;
+}
+
+// With the handle's device current: the array's device address in the current context, resolved on
+// the first call in that context.
+psp_status scratch_address(int dev, void** out) {
+  if (dev < 0 || dev >= kMaxDevices) return psp::set_error(PSP_ERR_CUDA, "device ordinal out of range");
+  CtxGetCurrent get = ctx_get_current();
+  if (!get) return psp::set_error(PSP_ERR_CUDA, "cuCtxGetCurrent is not available");
+  CUcontext ctx = nullptr;
+  if (get(&ctx) != CUDA_SUCCESS || !ctx) return psp::set_error(PSP_ERR_CUDA, "no current CUDA context");
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_addr[dev] || g_scratch_ctx[dev] != ctx) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, psp_apply_scratch);
     if (e != cudaSuccess || !p)
       return psp::set_error(PSP_ERR_CUDA, (std::string("cudaGetSymbolAddress failed: ") + cudaGetErrorString(e)).c_str());
     g_scratch_addr[dev] = p;
+    g_scratch_ctx[dev] = ctx;
   }
   *out = g_scratch_addr[dev];
   return PSP_OK;
 }
 
-bool is_device(const void* p) {
+// device memory of device `dev` (memory of another device is not accepted)
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
 }
 
 }  // namespace
@@ -57,8 +84,14 @@ extern "C" psp_status psp_apply_noalloc(psp_handle h, const double* rhs, double*
   if (!h || !rhs || !out || nrhs < 1) return psp::set_error(PSP_ERR_ARG, "bad apply arguments");
   const int64_t N = psp::handle_points(h);
   if (N < 0) return psp::set_error(PSP_ERR_STATE, "handle has no factorisation");
-  if (!is_device(rhs) || !is_device(out))
-    return psp::set_error(PSP_ERR_ARG, "psp_apply_noalloc needs device pointers for rhs and out");
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return psp::set_error(PSP_ERR_CUDA, cudaGetErrorString(e));
+  if (dev != psp::handle_device(h))
+    return psp::set_error(PSP_ERR_ARG, ("the handle was set up on device " + std::to_string(psp::handle_device(h)) +
+                                        ", but device " + std::to_string(dev) + " is current").c_str());
+  if (!on_device(rhs, dev) || !on_device(out, dev))
+    return psp::set_error(PSP_ERR_ARG, "psp_apply_noalloc needs device pointers of the handle's device for rhs and out");
   const size_t need = psp::apply_workspace_bytes(h, nrhs);
   if (need > kNoAllocScratchBytes)
     return psp::set_error(PSP_ERR_ARG, ("psp_apply_noalloc needs " + std::to_string(need) +
@@ -66,11 +99,11 @@ extern "C" psp_status psp_apply_noalloc(psp_handle h, const double* rhs, double*
                                         std::to_string(kNoAllocScratchBytes) + "; use psp_apply")
                                            .c_str());
   void* ws = nullptr;
-  psp_status st = scratch_address(&ws);
+  psp_status st = scratch_address(dev, &ws);
   if (st != PSP_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   if ((const void*)rhs != (const void*)out) {
-    cudaError_t e = cudaMemcpyAsync(out, rhs, (size_t)N * nrhs * sizeof(double2), cudaMemcpyDeviceToDevice, s);
+    e = cudaMemcpyAsync(out, rhs, (size_t)N * nrhs * sizeof(double2), cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return psp::set_error(PSP_ERR_CUDA, cudaGetErrorString(e));
   }
   return psp::apply_with_workspace(h, reinterpret_cast<double2*>(out), nrhs, ws, s);

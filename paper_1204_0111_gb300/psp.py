@@ -103,6 +103,7 @@ def lib():
         "psp_export_front": (_I, [_P, _I, _I, _P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
         "psp_stats": (_I, [_P, ctypes.POINTER(KernelStat), _I, ctypes.POINTER(_I), _I]),
         "psp_tune_sweep": (_I, [_P, _I, _I, _P, ctypes.POINTER(SweepTuning)]),
+        "psp_check_status": (_I, [_P, _P]),
         "psp_destroy": (_I, [_P]),
         "psp_status_string": (ctypes.c_char_p, [_I]),
         "psp_last_error": (ctypes.c_char_p, []),
@@ -217,6 +218,10 @@ class SweepingPreconditioner:
         if st != 0 and (raise_on_nonconvergence or st != 5):
             _check(st)
         return info.as_dict()
+
+    def check_status(self, stream=None):
+        """psp_check_status: raise PSPError(PSP_ERR_TIMEOUT) if a sweep wait gave up since the last check."""
+        _check(lib().psp_check_status(self._h, _stream(stream)))
 
     def info(self):
         m = _I()

@@ -267,6 +267,18 @@ def test_sweep_wait_gives_up_and_the_device_stays_usable():
     with pytest.raises(psp.PSPError) as e:
         P.solve(f, u, tol=1e-6, k=10, maxit=50)
     assert e.value.name == "PSP_ERR_TIMEOUT"
+    P.check_status()                       # psp_solve reported the give-up and cleared the flag
+    # psp_apply with a host output synchronises and reports the give-up itself
+    with pytest.raises(psp.PSPError) as e:
+        P.apply(f, np.zeros_like(f))
+    assert e.value.name == "PSP_ERR_TIMEOUT"
+    # with device pointers it only enqueues; psp_check_status reports it once
+    fd = torch.from_numpy(f).cuda()
+    P.apply(fd, torch.empty_like(fd))
+    with pytest.raises(psp.PSPError) as e:
+        P.check_status()
+    assert e.value.name == "PSP_ERR_TIMEOUT"
+    P.check_status()
     P.close()
     Q = gpu_for(case)
     u = np.zeros_like(f)

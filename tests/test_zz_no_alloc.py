@@ -25,10 +25,10 @@ from paper_1204_0111_gb300 import psp  # noqa: E402
 TOL = 1e-10  # the apply parity tolerance of the other GPU tests
 
 
-def _make(case):
+def _make(case, precision="c128"):
     c = torch.from_numpy(case.c).cuda()
     return psp.SweepingPreconditioner(c, case.h, case.omega, case.gamma, case.depth, pad=case.pad, leaf=case.leaf,
-                                      pml_C=case.C, alpha=case.alpha, faces=case.faces)
+                                      pml_C=case.C, alpha=case.alpha, faces=case.faces, precision=precision)
 
 
 def _noalloc(P, rhs, out):
@@ -87,3 +87,36 @@ def test_noalloc_rejects_host_pointers_and_oversize_requests():
     st = _noalloc(P, big, big)
     assert st == 1 and b"use psp_apply" in L.psp_last_error()
     P.close()
+
+
+def test_noalloc_complex64_handle_matches_apply():
+    # complex64 fronts and work vectors (8-byte elements in the shared array)
+    case = small_cases()[2]
+    P = _make(case, precision="c64")
+    r = torch.from_numpy(wl.random_vector(case.N, 3, seed=5)).cuda()
+    ref = torch.empty_like(r)
+    P.apply(r, ref)
+    for call in range(2):
+        out = torch.from_numpy(wl.random_vector(case.N, 3, seed=60 + call)).cuda()
+        assert _noalloc(P, r, out) == 0, psp.lib().psp_last_error()
+        torch.cuda.synchronize()
+        assert _rel(out, ref) < TOL, call      # same kernels and schedule as psp_apply
+    P.close()
+
+
+def test_noalloc_batch_of_two_problems_matches_apply():
+    # a batch handle: each problem's work vectors sit at their own offset inside the shared array
+    cases = small_cases()[:2]
+    probs = [dict(c=torch.from_numpy(cs.c).cuda(), h=cs.h, omega=cs.omega, gamma=cs.gamma, panel_depth=cs.depth)
+             for cs in cases]
+    B = psp.SweepingPreconditionerBatch(probs, leaf=16)
+    nrhs = 2
+    r = torch.from_numpy(wl.random_vector(B.N * nrhs, 1, seed=9).reshape(-1)).cuda()
+    ref = torch.empty_like(r)
+    B.apply(r, ref)
+    for call in range(2):
+        out = torch.zeros_like(r)
+        assert _noalloc(B, r, out) == 0, psp.lib().psp_last_error()
+        torch.cuda.synchronize()
+        assert _rel(out, ref) < TOL, call
+    B.close()
