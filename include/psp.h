@@ -252,8 +252,10 @@ psp_status psp_export_front(psp_handle h, int panel, int supernode, double* buf,
  * Per-kernel accounting of one handle (setup, applies, matvecs and solves issued through it).
  * Launch counts and algorithmic work are always kept; total_ms is filled for the kernels that the
  * handle's collect_stats selects (CUDA events around each such launch, on the launch stream).
- * flops: useful real floating-point operations (a complex multiply-add counts 8); bytes: the
- * algorithmic HBM bytes (matrix entries read once, vectors read/written once).
+ * flops: useful real floating-point operations (a complex multiply-add counts 8) of the plain
+ * multifrontal method (LDL^T of F_TL, F_BL L^{-T}, the Schur update, the solves); extra_flops: the
+ * further flops the kernel executes for selective inversion (inv(L_TL) and M_BL = L_BL inv(L_TL),
+ * §2.2); bytes: the algorithmic HBM bytes (matrix entries read once, vectors read/written once).
  * Copies min(capacity, kinds) records into out, sets *count to the number of kernel kinds,
  * synchronises the device, and zeroes the counters when reset != 0.
  */
@@ -263,6 +265,7 @@ typedef struct {
   double total_ms;
   double flops;
   double bytes;
+  double extra_flops;
 } psp_kernel_stat;
 
 psp_status psp_stats(psp_handle h, psp_kernel_stat* out, int capacity, int* count, int reset);

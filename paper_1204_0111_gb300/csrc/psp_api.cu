@@ -119,6 +119,7 @@ static double2 inv_stretch(double sig, double omega) { return cinv(stretch(sig, 
 struct KStat {
   int64_t launches = 0;
   double flops = 0, bytes = 0, ms = 0;
+  double extra = 0;   // executed flops beyond the algorithmic count (selective inversion)
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
 };
 struct Stats {
@@ -138,11 +139,13 @@ struct Stats {
     return e;
   }
   template <class F>
-  void run(const char* name, cudaStream_t st, int nlaunch, double flops, double bytes, F&& launch, bool setup = false) {
+  void run(const char* name, cudaStream_t st, int nlaunch, double flops, double bytes, F&& launch, bool setup = false,
+           double extra = 0) {
     KStat& s = k[name];
     s.launches += nlaunch;
     s.flops += flops;
     s.bytes += bytes;
+    s.extra += extra;
     if (!timing || mode == 0 || (mode == 2 && !setup)) {
       launch();
       return;
@@ -432,15 +435,17 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
     int count;
     int kb;
     double flops = 0, bytes = 0;
+    double extra = 0;   // selective-inversion flops (not part of the algorithmic count)
   };
   std::vector<Launch> launches;
   const double es = sizeof(T);
-  // work of the gemm tasks [g0, end)
-  auto gemm_work = [&](int64_t g0, double& fl, double& by) {
+  // work of the gemm tasks [g0, end): algorithmic flops, selective-inversion flops, bytes
+  auto gemm_work = [&](int64_t g0, double& fl, double& ex, double& by) {
     fl = 0;
+    ex = 0;
     by = 0;
     for (size_t i = g0; i < gtasks.size(); ++i) {
-      fl += 8.0 * gemm_cmacs(gtasks[i]);
+      (gtasks[i].flags & GF_SI ? ex : fl) += 8.0 * gemm_cmacs(gtasks[i]);
       by += es * ((double)gtasks[i].m * gtasks[i].k + (double)gtasks[i].n * gtasks[i].k + 2.0 * gtasks[i].m * gtasks[i].n);
     }
   };
@@ -514,7 +519,7 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
           case TCPACK: launch_tc_pack(PT + (l.off - (int64_t)p0), l.count, st); break;
           case SCALE: launch_scale_zd<T>(Fl, CT + (l.off - (int64_t)c0), l.count, st); break;
         }
-      }, true);
+      }, true, l.extra);
     }
     PSP_CK(cudaGetLastError());
   };
@@ -619,7 +624,7 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
       Launch lp{PLEFT, f0, pl0, (int)(ctasks.size() - pl0), kb};
       for (int64_t t = pl0; t < (int64_t)ctasks.size(); ++t) {
         const double cols = ctasks[t].c1 - ctasks[t].c0, bs = std::min(nb, fronts[f0 + ctasks[t].front].s - o);
-        lp.flops += 8.0 * cols * bs * (bs - 1) / 2;
+        lp.extra += 8.0 * cols * bs * (bs - 1) / 2;   // block row of inv(L): selective inversion
         lp.bytes += es * 2 * cols * bs;
       }
       launches.push_back(lp);
@@ -661,12 +666,12 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
             g.k = bs;
             g.kg0 = o;              // W is unit lower: B(n, k) = W[o + k, tj + n] vanishes for o + k < tj + n
             g.ng0 = tj;
-            g.flags = GF_NEG | GF_B_NN | GF_B_UNIT_LOWER_NN;
+            g.flags = GF_NEG | GF_B_NN | GF_B_UNIT_LOWER_NN | GF_SI;
             gtasks.push_back(g);
           }
       }
       Launch lg{GEMM, f0, g0, (int)(gtasks.size() - g0), kb};
-      gemm_work(g0, lg.flops, lg.bytes);
+      gemm_work(g0, lg.flops, lg.extra, lg.bytes);
       launches.push_back(lg);
     }
     // inv(L_TL) into F_TL's strict lower part
@@ -735,7 +740,7 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
           g.k = ft.s - tj;
           g.kg0 = tj;
           g.ng0 = tj;
-          g.flags = GF_BETA0 | GF_B_NN | GF_B_UNIT_LOWER_NN;
+          g.flags = GF_BETA0 | GF_B_NN | GF_B_UNIT_LOWER_NN | GF_SI;   // M_BL = Z D^-1 inv(L)
           gtasks.push_back(g);
         }
     };
@@ -796,13 +801,13 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
         }
         if ((int64_t)gtasks.size() > g0) {
           Launch lg{GEMM, f0, g0, (int)(gtasks.size() - g0), -1};
-          gemm_work(g0, lg.flops, lg.bytes);
+          gemm_work(g0, lg.flops, lg.extra, lg.bytes);
           launches.push_back(lg);
         }
       }
       // tensor-core fronts: pack, then tiles
       const int64_t p0 = (int64_t)ptasks.size(), t0 = (int64_t)ttasks.size();
-      double tflops = 0;
+      double tflops = 0, tflops_si = 0;
       for (int f : ord) {
         const auto& ft = fronts[f0 + f];
         if (ft.u == 0 || !packs[f0 + f]) continue;
@@ -866,7 +871,7 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
               ttasks.push_back(t);
               GemmTask<T> sh{};
               sh.m = t.m; sh.n = t.n; sh.k = ft.s - tj; sh.kg0 = tj; sh.ng0 = tj; sh.flags = GF_B_UNIT_LOWER_NN;
-              tflops += 8.0 * gemm_cmacs(sh);
+              tflops_si += 8.0 * gemm_cmacs(sh);   // M_BL: selective inversion
             }
         }
       }
@@ -878,6 +883,7 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
         double fl_unused = 0;
         tc_work(fl_unused, lt.bytes, t0);
         lt.flops = tflops;
+        lt.extra = tflops_si;
         launches.push_back(lt);
       }
     }
@@ -2068,6 +2074,7 @@ psp_status psp_stats(psp_handle X, psp_kernel_stat* out, int capacity, int* coun
       r.total_ms = kv.second.ms;
       r.flops = kv.second.flops;
       r.bytes = kv.second.bytes;
+      r.extra_flops = kv.second.extra;
     }
     ++i;
   }
@@ -2075,7 +2082,7 @@ psp_status psp_stats(psp_handle X, psp_kernel_stat* out, int capacity, int* coun
   if (reset)
     for (auto& kv : X->stats.k) {
       kv.second.launches = 0;
-      kv.second.ms = kv.second.flops = kv.second.bytes = 0;
+      kv.second.ms = kv.second.flops = kv.second.bytes = kv.second.extra = 0;
     }
   return PSP_OK;
   PSP_CATCH

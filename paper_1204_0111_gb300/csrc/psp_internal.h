@@ -107,7 +107,8 @@ enum GemmFlags : int {
   GF_B_UNIT_LOWER_NN = 16,// B(n,k) is T[k,n] of a unit lower T stored with D on its diagonal
   GF_D_MUL = 32,          // scale A(:,k) by d(k)
   GF_D_DIV = 64,          // scale A(:,k) by 1/d(k)
-  GF_NEG = 128            // alpha = -1 (else +1)
+  GF_NEG = 128,           // alpha = -1 (else +1)
+  GF_SI = 256             // selective-inversion work (inv(L_TL), M_BL): host accounting only, kernels ignore it
 };
 
 // C(m x n) (+)= alpha * A(m x k) * diag(d)^{+-1} * B(n x k)^T ; pointers already offset.

@@ -40,7 +40,7 @@ class Options(ctypes.Structure):
 
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
-                ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double), ("extra_flops", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -237,7 +237,8 @@ class SweepingPreconditioner:
         buf = (KernelStat * max(n.value, 1))()
         _check(lib().psp_stats(self._h, buf, n.value, ctypes.byref(n), 1 if reset else 0))
         return {buf[i].name.decode(): {"launches": buf[i].launches, "total_ms": buf[i].total_ms,
-                                       "flops": buf[i].flops, "bytes": buf[i].bytes} for i in range(n.value)}
+                                       "flops": buf[i].flops, "bytes": buf[i].bytes,
+                                       "extra_flops": buf[i].extra_flops} for i in range(n.value)}
 
     def tune_sweep(self, nrhs=1, reps=3, stream=None):
         """psp_tune_sweep: time candidate sweep schedules on this handle, keep the fastest."""

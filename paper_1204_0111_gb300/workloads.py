@@ -83,11 +83,11 @@ def velocity_salt(nx, ny, nz, h):
 
 
 def gaussian_source(nx, ny, nz, h, center, sigma=None):
-    """f = exp(-|x - x0|^2 / (2 sigma^2)), sigma = 2h by default; flat (N,) complex."""
+    """f = exp(-|x - x0|^2 / (2 sigma^2)), sigma = 2h by default; flat (N,) complex.  Built as the
+    outer product of its three 1-D factors (the Gaussian is separable)."""
     sigma = 2.0 * h if sigma is None else sigma
-    x, y, z = coords(nx, ny, nz, h)
-    r2 = (x - center[0]) ** 2 + (y - center[1]) ** 2 + (z - center[2]) ** 2
-    return np.exp(-r2 / (2.0 * sigma * sigma)).ravel().astype(np.complex128)
+    g = [np.exp(-((np.arange(n) + 1) * h - x0) ** 2 / (2.0 * sigma * sigma)) for n, x0 in zip((nx, ny, nz), center)]
+    return (g[2][:, None, None] * (g[1][:, None] * g[0][None, :])[None, :, :]).ravel().astype(np.complex128)
 
 
 def random_vector(N, nrhs=1, seed=0):

@@ -15,8 +15,8 @@ def bench():
     return mod
 
 
-def rec(launches, ms, flops, bytes_):
-    return {"launches": launches, "total_ms": ms, "flops": flops, "bytes": bytes_}
+def rec(launches, ms, flops, bytes_, extra=0.0):
+    return {"launches": launches, "total_ms": ms, "flops": flops, "bytes": bytes_, "extra_flops": extra}
 
 
 def test_summarize_picks_dominant_kernel_and_computes_rates(bench):
@@ -28,7 +28,7 @@ def test_summarize_picks_dominant_kernel_and_computes_rates(bench):
     roof, detail, launches = bench.summarize(timed, full, infos, 16e9, 2)
     assert roof["kernel"] == "k_gemm"
     assert roof["achieved"] == pytest.approx(1.0)              # 2e12 flop / 2 s
-    assert roof["frac"] == pytest.approx(1.0 / bench.FP64_PEAK_TFLOPS)
+    assert roof["frac"] == pytest.approx(1.0 / bench.FP64_DERIVED_TFLOPS)
     assert roof["kernel_share"] == pytest.approx(1000.0 / 1450.0)
     assert launches == 2 * 129
     assert detail["apply_ms"] == pytest.approx(400.0 / 19)
@@ -71,3 +71,38 @@ def test_roofline_generic_bounds_and_rates(bench):
 
 def test_job_rate_counts_every_rank(bench):
     assert bench.job_rate(4, 5, 2.0) == 10.0
+
+
+def test_summarize_counts_algorithmic_flops_and_reports_si_beside(bench):
+    timed = [{"k_gemm": rec(10, 1000.0, 1e12, 0, extra=2.5e11)}]
+    full = {"k_gemm": rec(10, 1000.0, 1e12, 0, extra=2.5e11)}
+    infos = [{"iterations": 3, "relres_max": 1e-6, "solve_ms": 1.0, "applies": 4}]
+    roof, _, _ = bench.summarize(timed, full, infos, 1, 1, fp64_peak=1.25, fp64_source="x")
+    assert roof["achieved"] == pytest.approx(1.0) and roof["frac"] == pytest.approx(0.8)
+    assert roof["achieved_incl_si"] == pytest.approx(1.25)
+
+
+def test_rooflines_cover_the_metric_families(bench):
+    full128 = {"k_gemm": rec(10, 2000.0, 2e12, 1e9, extra=5e11), "k_sweep": rec(19, 1000.0, 4e11, 3e11)}
+    full64 = {"k_gemm": rec(10, 60.0, 5e11, 1e9), "k_tc_gemm": rec(16, 30.0, 2.5e12, 1e10, extra=5e11),
+              "k_assemble": rec(12, 40.0, 1e9, 4e10), "k_sweep": rec(19, 300.0, 5e11, 5e11)}
+    alu = {"fp64_tflops": 1.2, "fp64_source": "m", "fp32_tflops": 70.0, "fp32_source": "m"}
+    out = {(r["path"], r["kernel"]): r for r in bench.rooflines(full128, full64, alu)}
+    g = out[("c128", "k_gemm")]
+    assert g["achieved"] == pytest.approx(1.0) and g["frac"] == pytest.approx(1.0 / 1.2)
+    assert g["achieved_incl_si"] == pytest.approx(1.25)
+    s64 = out[("c64", "k_sweep")]
+    assert s64["bound"] == "hbm" and s64["achieved"] == pytest.approx(5e11 / 0.3 / 1e9)
+    fp = out[("c64", "front phase (all setup kernels)")]
+    assert fp["bound"] == "tensor" and fp["setup_kernel_ms"] == pytest.approx(130.0)
+    assert fp["achieved"] == pytest.approx((5e11 + 2.5e12 + 1e9) / 0.13 / 1e12)
+    assert fp["tensor_executed"] == pytest.approx(3e12 * 18 / 8 / 0.13 / 1e12)
+    tc = out[("c64", "k_tc_gemm")]
+    assert tc["executed"] == pytest.approx(3e12 * 18 / 8 / 0.03 / 1e12)
+
+
+def test_oracle_extrapolation_formula(bench):
+    s = {"t_batch": 10.0, "t_T": 0.2, "t_matvec": 0.01}
+    total, formula = bench.oracle_extrapolate(s, m=23, cores=16, iters=18, k=20)
+    expect = 2 * 10.0 + 18 * (45 * 0.2 + 0.01) + 1 * 0.01 + 18 * 19 / 8 * 0.01
+    assert total == pytest.approx(expect) and "cores = 16" in formula
