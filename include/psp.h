@@ -106,6 +106,13 @@ typedef struct {
   int test_sweep_stall; /* tests only: 1 makes one dependency of the persistent sweep impossible to
                            meet, so its bounded wait (about 2 s) gives up; psp_solve then returns
                            PSP_ERR_TIMEOUT and the device stays usable.  0 (default): off */
+  int gmres_basis;      /* psp_solve: 1 keeps z_j = M^{-1} v_j for every Krylov vector (2k + 1 vectors per
+                           right-hand side); 2 keeps V only and forms x += M^{-1}(V y) with one more
+                           application per restart cycle (k + 2 vectors); 0 (default): 1 when every
+                           right-hand side fits in one run, else whichever needs fewer runs */
+  int factor_every_panel; /* 0 (default): panels whose auxiliary problems are identical (same depth and
+                             pad, bitwise the same x3-stretch and wave speed on every plane, as in a
+                             model invariant along x3, §3) share one factorisation; 1: factor each */
 } psp_options;
 
 /* Per-solve report filled by psp_solve (host struct). */
@@ -237,7 +244,8 @@ psp_status psp_solve(psp_handle h, const double* f, double* u, int nrhs, double 
  */
 psp_status psp_symbolic_export(psp_handle h, int panel, int32_t* buf, size_t* len);
 
-/* Number of panels m, total fronts, and bytes of factor storage (any pointer may be NULL). */
+/* Number of panels m, fronts factored (panels that share a factorisation count once), and bytes of
+   factor storage (any pointer may be NULL). */
 psp_status psp_info(psp_handle h, int* panels, int64_t* fronts, int64_t* factor_bytes);
 
 /*

@@ -206,6 +206,12 @@ struct psp_ctx_s {
   std::vector<int> z0, z1, lead, shape_of;
   std::vector<int64_t> sn_base;
   int64_t nfronts = 0;
+  // panels whose auxiliary problems H_i are identical share one factorisation: owner[i] is the first
+  // such panel (i itself when H_i is distinct); only owners are factored
+  std::vector<int> owner;
+  bool factor_every_panel = false;
+  int64_t nfronts_factored = 0;
+  int distinct_panels = 0;
   std::vector<Shape> shapes;
   std::vector<ShapeDev> shdev;
   std::vector<DevBuf> shape_bufs;
@@ -251,6 +257,7 @@ struct psp_ctx_s {
   bool use_tc = true;
   int tc_min_dim = 64;
   int sweep_level_tasks = 608, sweep_ctas_per_sm = 8, sweep_rhs_group = 0, solve_rhs_group = 0;
+  int gmres_basis = 0;   // 0 auto, 1 keep z_j, 2 V only
   bool test_sweep_stall = false;
   bool persistent_sweep = true;
   int64_t upd_arena_elems = 0;
@@ -326,6 +333,7 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
   std::vector<std::vector<std::pair<int, int>>> lev_fronts(L);  // (panel, sn)
   for (int lv = 0; lv < L; ++lv)
     for (int p = 0; p < X->m; ++p) {
+      if (X->owner[p] != p) continue;   // shares the factorisation of an identical panel
       const int si = X->shape_of[p];
       const int d = L - 1 - lv;
       if (d < (int)depth_sns[si].size())
@@ -1358,6 +1366,55 @@ static void build_problem(psp_ctx_s* X, const double* c, cudaStream_t st) {
     for (auto& e : errs)
       if (e) std::rethrow_exception(e);
   }
+  // identical auxiliary problems (§3: a model invariant along the sweep direction needs O(1)
+  // distinct panel factorisations): same box depth and pad, bitwise the same x3-stretch tables and
+  // the same wave speed on every plane the box uses
+  X->owner.resize(X->m);
+  for (int i = 0; i < X->m; ++i) X->owner[i] = i;
+  if (!X->factor_every_panel && X->aux_mode == PSP_AUX_MOVING_PML && X->m > 2) {
+    const int64_t plane = (int64_t)nx * ny;
+    std::vector<double> hc((size_t)X->N);
+    PSP_CK(cudaMemcpyAsync(hc.data(), c, X->N * sizeof(double), cudaMemcpyDefault, st));   // c: host or device
+    PSP_CK(cudaStreamSynchronize(st));
+    auto depth_of = [&](int i) { return X->lead[i] + X->z1[i] - X->z0[i]; };
+    auto mix = [](uint64_t h, uint64_t w) { return (h ^ (w + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2))) * 0x100000001b3ull; };
+    auto words = [&](uint64_t h, const void* p, size_t bytes) {
+      const unsigned char* b = static_cast<const unsigned char*>(p);
+      for (size_t o = 0; o + 8 <= bytes; o += 8) {
+        uint64_t w;
+        std::memcpy(&w, b + o, 8);
+        h = mix(h, w);
+      }
+      return h;
+    };
+    auto same = [&](int i, int j) {
+      const int D = depth_of(i);
+      if (D != depth_of(j) || X->lead[i] != X->lead[j]) return false;
+      if (std::memcmp(&gt[p_s3n[i]], &gt[p_s3n[j]], D * sizeof(double2)) ||
+          std::memcmp(&gt[p_s3h[i]], &gt[p_s3h[j]], (D + 1) * sizeof(double2)))
+        return false;
+      for (int k = 0; k < D; ++k)
+        if (std::memcmp(&hc[cplane_all[p_cpl[i] + k] * plane], &hc[cplane_all[p_cpl[j] + k] * plane],
+                        plane * sizeof(double)))
+          return false;
+      return true;
+    };
+    std::map<uint64_t, std::vector<int>> seen;
+    for (int i = 1; i < X->m; ++i) {
+      const int D = depth_of(i);
+      uint64_t h = mix(mix(1469598103934665603ull, D), X->lead[i]);
+      h = words(h, &gt[p_s3n[i]], D * sizeof(double2));
+      h = words(h, &gt[p_s3h[i]], (D + 1) * sizeof(double2));
+      for (int k = 0; k < D; ++k) h = words(h, &hc[cplane_all[p_cpl[i] + k] * plane], plane * sizeof(double));
+      auto& cands = seen[h];
+      for (int j : cands)
+        if (same(i, j)) {
+          X->owner[i] = j;
+          break;
+        }
+      if (X->owner[i] == i) cands.push_back(i);
+    }
+  }
   // global plane map (identity) for the full-domain operators
   const int64_t gcpl = (int64_t)cplane_all.size();
   for (int k = 0; k < nz; ++k) cplane_all.push_back(k);
@@ -1473,12 +1530,20 @@ static void finish_setup(psp_ctx_s* X, cudaStream_t st) {
   X->sn_base.assign(X->m, 0);
   X->panel_fbase.assign(X->m, 0);
   int64_t nf = 0, fe = 0;
+  X->nfronts_factored = 0;
+  X->distinct_panels = 0;
   for (int i = 0; i < X->m; ++i) {
     const Shape& sh = X->shapes[X->shape_of[i]];
     X->sn_base[i] = nf;
     nf += sh.nsn;
-    X->panel_fbase[i] = fe;
-    fe += sh.g_total;
+    if (X->owner[i] == i) {
+      X->panel_fbase[i] = fe;
+      fe += sh.g_total;
+      X->nfronts_factored += sh.nsn;
+      X->distinct_panels += 1;
+    } else {
+      X->panel_fbase[i] = X->panel_fbase[X->owner[i]];   // the owner comes first
+    }
   }
   X->nfronts = nf;
   X->factor_elems = fe;
@@ -1523,6 +1588,7 @@ static void setup_batch_impl(psp_ctx_s* B, int nprob, const double* const* c, cu
   B->m = 0;
   B->N = 0;
   B->probs.clear();
+  B->owner.clear();
   for (int q = 0; q < nprob; ++q) {
     psp_ctx_s* X = B->subs[q].get();
     build_problem(X, c[q], st);
@@ -1534,6 +1600,7 @@ static void setup_batch_impl(psp_ctx_s* B, int nprob, const double* const* c, cu
     pr.panel0 = B->m;
     B->probs.push_back(pr);
     for (int i = 0; i < X->m; ++i) {
+      B->owner.push_back(B->m + X->owner[i]);
       B->z0.push_back(X->z0[i]);
       B->z1.push_back(X->z1[i]);
       B->lead.push_back(X->lead[i]);
@@ -1557,8 +1624,11 @@ static void setup_batch_impl(psp_ctx_s* B, int nprob, const double* const* c, cu
 // ---------------------------------------------------------------------------
 // GMRES(k), right preconditioned, x0 = 0, complex128 (§2.4, §3)
 // ---------------------------------------------------------------------------
+// store_z: keep z_j = M^{-1} v_j for every Krylov vector and update x += Z y at the end of a cycle;
+// otherwise keep one work vector and form x += M^{-1} (V y) with one more application per cycle
+// (right preconditioning: both give x0 + M^{-1} V y), which halves the vectors kept per right-hand side.
 static void solve_impl(psp_ctx_s* X, const double2* f, double2* x, int nrhs_in, double tol, int k, int maxit,
-                       psp_solve_info* info, cudaStream_t st) {
+                       psp_solve_info* info, cudaStream_t st, bool store_z) {
   // GMRES columns: right-hand side r of problem q is column q * nrhs + r, the span
   // [off1_q nrhs + r N_q, + N_q) of every vector block; all columns iterate in lockstep but each
   // has its own Krylov basis, Hessenberg matrix and convergence test
@@ -1577,7 +1647,7 @@ static void solve_impl(psp_ctx_s* X, const double2* f, double2* x, int nrhs_in, 
   const ColSpan* cols = X->d_cols.as<ColSpan>();
   const int K = k;
   // workspace layout (double2 elements)
-  const int64_t nV = (int64_t)(K + 1) * NT, nZ = (int64_t)K * NT, nW = NT;
+  const int64_t nV = (int64_t)(K + 1) * NT, nZ = (store_z ? (int64_t)K : 1) * NT, nW = NT;
   const int64_t nB = nW;
   const int64_t nH = (int64_t)(K + 1) * K * nrhs, nSn = (int64_t)K * nrhs, nG = (int64_t)(K + 1) * nrhs;
   const int64_t nPart = (int64_t)multidot_blocks(maxlen) * (K + 1) * nrhs, nDot = (int64_t)(K + 1) * nrhs;
@@ -1660,7 +1730,7 @@ static void solve_impl(psp_ctx_s* X, const double2* f, double2* x, int nrhs_in, 
     int j = 0;
     for (; j < K && total_it < maxit; ++j) {
       double2* Vj = V + (int64_t)j * ldv_vec;
-      double2* Zj = Z + (int64_t)j * ldv_vec;
+      double2* Zj = store_z ? Z + (int64_t)j * ldv_vec : Z;
       PSP_CK(cudaMemcpyAsync(Zj, Vj, nW * sizeof(double2), cudaMemcpyDeviceToDevice, st));
       apply_dispatch(X, Zj, nrhs_in, st);   // z_j = M^{-1} v_j
       ++applies;
@@ -1687,10 +1757,22 @@ static void solve_impl(psp_ctx_s* X, const double2* f, double2* x, int nrhs_in, 
       PSP_CK(cudaMemcpyAsync(active, act.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
       if (all_done) { ++j; break; }
     }
-    // x += Z y for every rhs that iterated in this cycle
+    // x += M^{-1} V y for every rhs that iterated in this cycle (y is zero beyond a column's own
+    // count; only the vectors some column reached are read)
     PSP_CK(cudaMemcpyAsync(jr, jrh.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
     small("k_backsolve", [&] { launch_backsolve(Ls, jr, ybuf, st); });
-    multiaxpy(Z, K, ybuf, x, 1.0);
+    const int jmax = *std::max_element(jrh.begin(), jrh.end());
+    if (jmax > 0) {
+      if (store_z) {
+        multiaxpy(Z, jmax, ybuf, x, 1.0);
+      } else {
+        PSP_CK(cudaMemsetAsync(Z, 0, nW * sizeof(double2), st));
+        multiaxpy(V, jmax, ybuf, Z, 1.0);
+        apply_dispatch(X, Z, nrhs_in, st);
+        ++applies;
+        axpby(Z, x, nullptr, 2);
+      }
+    }
     // true residual r = b - A x
     matvec(x, w);
     axpby(b, w, nullptr, 1);
@@ -1774,7 +1856,8 @@ static psp_status check_options(const psp_options* opt, psp_options* o) {
   if (o->collect_stats < 0 || o->collect_stats > 2) return fail(PSP_ERR_ARG, "bad collect_stats");
   if (o->leaf_size < 1 || o->pml_faces < 0 || o->pml_faces > 63 ||
       (o->precision != PSP_PREC_C128 && o->precision != PSP_PREC_C64) ||
-      (o->aux_mode != PSP_AUX_MOVING_PML && o->aux_mode != PSP_AUX_EXACT) || !(o->alpha >= 0) || !(o->pml_C >= 0))
+      (o->aux_mode != PSP_AUX_MOVING_PML && o->aux_mode != PSP_AUX_EXACT) || !(o->alpha >= 0) || !(o->pml_C >= 0) ||
+      o->gmres_basis < 0 || o->gmres_basis > 2)
     return fail(PSP_ERR_ARG, "bad options");
   return PSP_OK;
 }
@@ -1800,6 +1883,8 @@ static void init_options(psp_ctx_s* X, const psp_options& o) {
   X->sweep_ctas_per_sm = o.sweep_ctas_per_sm > 0 ? o.sweep_ctas_per_sm : 8;
   X->sweep_rhs_group = o.sweep_rhs_group > 0 ? o.sweep_rhs_group : 0;
   X->solve_rhs_group = o.solve_rhs_group > 0 ? o.solve_rhs_group : 0;
+  X->gmres_basis = o.gmres_basis;
+  X->factor_every_panel = o.factor_every_panel != 0;
   X->test_sweep_stall = o.test_sweep_stall == 1;
   X->temp_budget_elems = o.setup_temp_mb > 0 ? ((int64_t)o.setup_temp_mb << 20) / (o.precision == PSP_PREC_C64 ? 8 : 16) : 0;
 }
@@ -1963,19 +2048,33 @@ psp_status psp_solve(psp_handle X, const double* f, double* u, int nrhs, double 
   // Right-hand sides per GMRES run: all of them when their Krylov bases (V and Z, 2k + 1 vectors)
   // fit the free device memory, else groups that do.  The columns iterate independently, so the
   // groups give the same result.  (Batches keep one run: their columns interleave problems.)
+  // When not all of them fit with z_j = M^{-1} v_j kept (2k + 1 vectors each), GMRES keeps V only
+  // (k + 2 vectors each, one more application per cycle) if that needs fewer runs.
   int group = nrhs;
+  bool store_z = true;
   if (X->probs.size() == 1) {
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
-      const double per_rhs = (2.0 * k + 6) * (double)X->N * sizeof(double2) +
-                             (2.0 * X->max_nloc + X->max_upd) * (double)X->elem_bytes;
+      const double ws = (2.0 * X->max_nloc + X->max_upd) * (double)X->elem_bytes;
+      const double vec = (double)X->N * sizeof(double2);
       const double held = (double)X->gm.bytes + X->ws_xf.bytes + X->ws_xb.bytes + X->ws_upd.bytes;
       const double avail = (double)free_b + held - 2.0e9;
-      group = std::max(1, std::min(nrhs, (int)(avail / per_rhs)));
+      auto fit = [&](double per_rhs) {
+        int g = std::max(1, std::min(nrhs, (int)(avail / per_rhs)));
+        if (X->solve_rhs_group > 0) g = std::min(g, X->solve_rhs_group);
+        return g;
+      };
+      const int gz = fit((2.0 * k + 6) * vec + ws), gv = fit((k + 7.0) * vec + ws);
+      const int runs_z = (nrhs + gz - 1) / gz, runs_v = (nrhs + gv - 1) / gv;
+      store_z = X->gmres_basis == 1 || (X->gmres_basis == 0 && runs_v >= runs_z);
+      group = store_z ? gz : gv;
     } else {
       cudaGetLastError();
+      if (X->solve_rhs_group > 0) group = std::min(group, X->solve_rhs_group);
+      store_z = X->gmres_basis != 2;
     }
-    if (X->solve_rhs_group > 0) group = std::min(group, X->solve_rhs_group);
+  } else {
+    store_z = X->gmres_basis != 2;
   }
   psp_status rs = PSP_OK;
   psp_solve_info agg{};
@@ -1985,7 +2084,7 @@ psp_status psp_solve(psp_handle X, const double* f, double* u, int nrhs, double 
     const int ng = std::min(group, nrhs - r0);
     psp_solve_info gi{};
     try {
-      solve_impl(X, fd + (int64_t)r0 * X->N, ud + (int64_t)r0 * X->N, ng, tol, k, maxit, &gi, st);
+      solve_impl(X, fd + (int64_t)r0 * X->N, ud + (int64_t)r0 * X->N, ng, tol, k, maxit, &gi, st, store_z);
     } catch (const Error& e) {
       if (e.st != PSP_ERR_NOT_CONVERGED) throw;
       rs = fail(e.st, e.msg);
@@ -2033,7 +2132,7 @@ psp_status psp_symbolic_export(psp_handle X, int panel, int32_t* buf, size_t* le
 psp_status psp_info(psp_handle X, int* panels, int64_t* fronts, int64_t* factor_bytes) {
   if (!X) return fail(PSP_ERR_ARG, "NULL handle");
   if (panels) *panels = X->m;
-  if (fronts) *fronts = X->nfronts;
+  if (fronts) *fronts = X->nfronts_factored;
   if (factor_bytes) *factor_bytes = X->factor_elems * (int64_t)X->elem_bytes;
   return PSP_OK;
 }

@@ -35,7 +35,8 @@ class Options(ctypes.Structure):
                 ("tc_min_dim", ctypes.c_int),
                 ("sweep_level_tasks", ctypes.c_int), ("sweep_ctas_per_sm", ctypes.c_int),
                 ("setup_temp_mb", ctypes.c_int), ("sweep_rhs_group", ctypes.c_int),
-                ("solve_rhs_group", ctypes.c_int), ("test_sweep_stall", ctypes.c_int)]
+                ("solve_rhs_group", ctypes.c_int), ("test_sweep_stall", ctypes.c_int), ("gmres_basis", ctypes.c_int),
+                ("factor_every_panel", ctypes.c_int)]
 
 
 class KernelStat(ctypes.Structure):
@@ -156,7 +157,7 @@ class SweepingPreconditioner:
     def __init__(self, c, h, omega, gamma, panel_depth, pad=None, leaf=64, pml_C=4.0, alpha=2 * math.pi,
                  precision="c128", faces=63, mode="moving", stream=None, collect_stats=0, tensor_cores=True,
                  tc_min_dim=0, sweep_level_tasks=0, sweep_ctas_per_sm=0, setup_temp_mb=0, sweep_rhs_group=0,
-                 solve_rhs_group=0, test_sweep_stall=0):
+                 solve_rhs_group=0, test_sweep_stall=0, gmres_basis="auto", factor_every_panel=False):
         nz, ny, nx = c.shape
         self.nx, self.ny, self.nz = nx, ny, nz
         self.N = nx * ny * nz
@@ -165,6 +166,8 @@ class SweepingPreconditioner:
         o = _options(pad, leaf, pml_C, alpha, precision, faces, mode, collect_stats, tensor_cores, tc_min_dim,
                      sweep_level_tasks, sweep_ctas_per_sm, setup_temp_mb, sweep_rhs_group, solve_rhs_group)
         o.test_sweep_stall = int(test_sweep_stall)
+        o.gmres_basis = {"auto": 0, "z": 1, "v": 2}[gmres_basis]
+        o.factor_every_panel = 1 if factor_every_panel else 0
         cp, n = _ptr_and_len(c, complex_=False)
         if n != self.N:
             raise ValueError("c has the wrong size")

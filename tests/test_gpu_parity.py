@@ -254,6 +254,26 @@ def test_solve_in_groups_of_right_hand_sides_equals_one_run():
     assert i3["iterations"] == i1["iterations"] and i3["converged"] == 1
 
 
+def test_gmres_v_only_basis_matches_z_basis():
+    # right preconditioning: x0 + M^{-1}(V y) equals x0 + Z y with z_j = M^{-1} v_j; keeping V only costs
+    # one more application per restart cycle (k = 6 forces several cycles)
+    case = CASES[1]
+    f = np.stack([wl.gaussian_source(case.nx, case.ny, case.nz, case.h, s) for s in ((0.5, 0.5, 0.5), (0.3, 0.6, 0.2))])
+    out = {}
+    for basis in ("z", "v"):
+        c = torch.from_numpy(case.c).cuda()
+        P = psp.SweepingPreconditioner(c, case.h, case.omega, case.gamma, case.depth, pad=case.pad, leaf=case.leaf,
+                                       pml_C=case.C, alpha=case.alpha, faces=case.faces, gmres_basis=basis)
+        u = np.zeros_like(f)
+        out[basis] = (P.solve(f, u, tol=1e-8, k=6, maxit=300), u)
+        P.close()
+    (iz, uz), (iv, uv) = out["z"], out["v"]
+    assert iz["converged"] == 1 and iv["converged"] == 1
+    assert iv["iterations"] == iz["iterations"] and iv["restarts"] == iz["restarts"] and iz["restarts"] > 1
+    assert iv["applies"] == iz["applies"] + iv["restarts"]
+    assert np.linalg.norm(uv - uz) / np.linalg.norm(uz) < 1e-9
+
+
 def test_sweep_wait_gives_up_and_the_device_stays_usable():
     # a dependency of the persistent sweep that can never be met (test option): its bounded wait
     # gives up after about two seconds, psp_solve reports PSP_ERR_TIMEOUT, and a normal handle
