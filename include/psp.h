@@ -113,6 +113,10 @@ typedef struct {
   int factor_every_panel; /* 0 (default): panels whose auxiliary problems are identical (same depth and
                              pad, bitwise the same x3-stretch and wave speed on every plane, as in a
                              model invariant along x3, §3) share one factorisation; 1: factor each */
+  int panel_begin;      /* first panel of the block this handle factors and sweeps (one GPU's share of a
+                           multi-GPU sweep, see psp_sweep_part), default 0 */
+  int panel_count;      /* panels in that block; 0 (default): through the last panel.  A handle holding
+                           a proper block takes psp_sweep_part, not psp_apply / psp_solve */
 } psp_options;
 
 /* Per-solve report filled by psp_solve (host struct). */
@@ -302,6 +306,35 @@ typedef struct {
 } psp_sweep_tuning;
 
 psp_status psp_tune_sweep(psp_handle h, int nrhs, int reps, void* stream, psp_sweep_tuning* out);
+
+/*
+ * psp_sweep_part - one half of Alg. 1.5 restricted to the handle's block of panels [b, e)
+ * (psp_options.panel_begin / panel_count), for a sweep whose panels are spread over several GPUs
+ * (§2: the panel factorisations are independent, the panel solves run in sequence).  u holds nrhs
+ * global vectors (N x nrhs, host or device) and is updated in place:
+ *   direction 0 (forward):  for i = b .. e-1:  u_i := T_i (u_i - J_{i,i-1} u_{i-1})
+ *                           (for b > 0 it reads plane z0(b) - 1, the previous block's last plane,
+ *                           which must hold that block's forward result)
+ *   direction 1 (backward): for i = min(e, m-1) - 1 .. b:  u_i -= T_i J_{i+1,i}^T u_{i+1}
+ *                           (for e < m it reads plane z0(e), the next block's first plane, which must
+ *                           hold that block's final result)
+ * Running the blocks' forward parts in order, then their backward parts in reverse order, handing
+ * those single planes between them, gives psp_apply's result on each block's planes.  Planes
+ * outside the reads above and the block's own are neither read nor written.
+ * Errors as for psp_apply; PSP_ERR_STATE for a batch handle.
+ */
+psp_status psp_sweep_part(psp_handle h, double* u, int nrhs, int direction, void* stream);
+
+/*
+ * psp_plan_panels - the paper has no counterpart: host-only planning, no GPU needed.  The panel
+ * plan psp_setup would make (§1.1, Alg. 1.4) for this grid, gamma, depth and options: *m panels,
+ * panel i holding the global planes [z0[i], z1[i]), and (cost != NULL) the algorithmic flops of
+ * factoring its auxiliary problem (8 per complex multiply-add of the LDL^T, the F_BL solve and the
+ * Schur updates of its nested-dissection fronts), for partitioning the panels over GPUs.  Entries
+ * beyond `capacity` are not written.  Errors: PSP_ERR_ARG.
+ */
+psp_status psp_plan_panels(const psp_grid* g, int pml_gamma, int panel_depth, const psp_options* opt, int* z0, int* z1,
+                           double* cost, int capacity, int* m);
 
 /*
  * psp_check_status - the paper has no counterpart: synchronises `stream` and reports whether a

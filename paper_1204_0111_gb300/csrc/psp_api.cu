@@ -237,12 +237,23 @@ struct psp_ctx_s {
   std::vector<std::vector<LevelPlan>> splan;
   DevBuf d_stasks;
   // persistent sweep plan
-  DevBuf d_sweep_steps, d_sweep_panels, d_sweep_queue, d_sweep_meta, d_sweep_sync;
-  int sweep_nsteps = 0, sweep_nqueue = 0;
-  size_t sweep_sync_words = 0;
-  int64_t meta_front_base = 0, meta_ntask_down = 0, meta_step_front = 0, meta_step_tasks = 0;
+  struct SweepPlan {
+    DevBuf steps, queue, meta;
+    std::vector<SweepStep> hsteps;
+    int nsteps = 0, nqueue = 0;
+    // meta layout: front_base | ntask_up | ntask_down | step_front | step_tasks | step_prev
+    int64_t o_up = 0, o_down = 0, o_step_front = 0, o_step_tasks = 0, o_step_prev = 0;
+    int64_t nfront_steps = 0;                 // fronts summed over the steps (counter words per direction)
+    double entries = 0, vec = 0;              // algorithmic factor entries / vector words per sweep
+  };
+  SweepPlan plans[3];              // 0: Alg. 1.5 over the handle's panels; 1: its forward part; 2: its backward part
+  DevBuf d_sweep_panels, d_sweep_sync;
+  size_t sweep_sync_words = 0;     // counters of the largest plan (one sweep runs at a time per handle)
   size_t sweep_rhs_bytes = 0;      // shared memory per right-hand side of the widest level
-  double sweep_entries = 0, sweep_vec = 0;   // algorithmic entries / vector words per apply
+  // block of panels [range_begin, range_end) this handle factors and sweeps (all of them unless the
+  // handle is one block of a multi-GPU sweep)
+  int range_begin = 0, range_count = 0, range_end = 0;
+  bool partial = false;
   int64_t max_nloc = 0, max_upd = 0;
   // apply workspaces
   DevBuf ws_xf, ws_xb, ws_upd;
@@ -276,7 +287,6 @@ struct psp_ctx_s {
   std::vector<BoxOp> h_boxops;                    // per panel, uploaded to d_boxops
   DevBuf d_sweep_probs, d_cols;
   int cols_nrhs = 0;
-  int64_t meta_step_prev = -1;
   Stats stats;
 };
 
@@ -957,30 +967,6 @@ static void plan_solve(psp_ctx_s* X, cudaStream_t st) {
   }
   upload_async(X->d_stasks, tasks, st);
 
-  // persistent sweep: panel solves in Alg. 1.5 order and one task queue in topological order.  The
-  // chains of a batch's problems are interleaved step by step; each step follows the previous step
-  // of its own problem.
-  std::vector<SweepStep> steps;
-  std::vector<int> step_prev;
-  {
-    const int np = (int)X->probs.size();
-    std::vector<std::vector<SweepStep>> chain(np);
-    size_t longest = 0;
-    for (int q = 0; q < np; ++q) {
-      const auto& pr = X->probs[q];
-      for (int i = 0; i < pr.m; ++i) chain[q].push_back({pr.panel0 + i, 0, q});
-      for (int i = pr.m - 2; i >= 0; --i) chain[q].push_back({pr.panel0 + i, 1, q});
-      longest = std::max(longest, chain[q].size());
-    }
-    std::vector<int> last(np, -1);
-    for (size_t t = 0; t < longest; ++t)
-      for (int q = 0; q < np; ++q)
-        if (t < chain[q].size()) {
-          step_prev.push_back(last[q]);
-          last[q] = (int)steps.size();
-          steps.push_back(chain[q][t]);
-        }
-  }
   // per shape: tasks per front, up and down
   std::vector<int> front_base(X->shapes.size() + 1, 0), ntask_up, ntask_down;
   size_t per_rhs = 0;
@@ -1001,44 +987,80 @@ static void plan_solve(psp_ctx_s* X, cudaStream_t st) {
     }
   }
   front_base[X->shapes.size()] = (int)ntask_up.size();
-  std::vector<QueueEntry> queue;
-  std::vector<int> step_front(steps.size() + 1, 0), step_tasks(steps.size(), 0);
-  X->sweep_entries = 0;
-  X->sweep_vec = 0;
-  for (size_t k = 0; k < steps.size(); ++k) {
-    const int si = X->shape_of[steps[k].panel];
-    step_front[k + 1] = step_front[k] + X->shapes[si].nsn;
-    step_tasks[k] = shape_tasks[si];
-    X->sweep_entries += shape_entries[si];
-    X->sweep_vec += shape_vec[si];
-    const auto& plan = X->splan[si];
-    for (size_t lv = 0; lv < plan.size(); ++lv)
-      for (int t = 0; t < plan[lv].nfwd; ++t)
-        queue.push_back({(int)k, (int)(plan[lv].fwd_off + t), 0, (short)plan[lv].R});
-    for (int lv = (int)plan.size() - 1; lv >= 0; --lv)
-      for (int t = 0; t < plan[lv].nbwd; ++t) queue.push_back({(int)k, (int)(plan[lv].bwd_off + t), 1, 0});
-  }
   X->sweep_rhs_bytes = per_rhs;
-  X->sweep_nsteps = (int)steps.size();
-  X->sweep_nqueue = (int)queue.size();
-  upload_async(X->d_sweep_steps, steps, st);
-  upload_async(X->d_sweep_queue, queue, st);
-  // metadata: front_base | ntask_up | ntask_down | step_front | step_tasks | step_prev
-  std::vector<int> meta;
-  meta.insert(meta.end(), front_base.begin(), front_base.end());
-  const int64_t o_up = (int64_t)meta.size();
-  meta.insert(meta.end(), ntask_up.begin(), ntask_up.end());
-  X->meta_ntask_down = (int64_t)meta.size();
-  meta.insert(meta.end(), ntask_down.begin(), ntask_down.end());
-  X->meta_step_front = (int64_t)meta.size();
-  meta.insert(meta.end(), step_front.begin(), step_front.end());
-  X->meta_step_tasks = (int64_t)meta.size();
-  meta.insert(meta.end(), step_tasks.begin(), step_tasks.end());
-  if (X->test_sweep_stall && steps.size() > 1) meta[X->meta_step_tasks] += 1;   // step 0 never "completes"
-  X->meta_step_prev = (int64_t)meta.size();
-  meta.insert(meta.end(), step_prev.begin(), step_prev.end());
-  X->meta_front_base = o_up;
-  upload_async(X->d_sweep_meta, meta, st);
+
+  // Persistent sweep plans: panel solves in Alg. 1.5 order and one task queue in topological order.
+  // Plan 0 is the whole Alg. 1.5 over the handle's panels; plans 1 and 2 are its forward and its
+  // backward part alone (a block of panels of a multi-GPU sweep runs them between plane hand-offs).
+  // The chains of a batch's problems are interleaved step by step; each step follows the previous
+  // step of its own problem.
+  size_t sync_words = 0;
+  for (int pi = 0; pi < 3; ++pi) {
+    psp_ctx_s::SweepPlan& SP = X->plans[pi];
+    std::vector<SweepStep> steps;
+    std::vector<int> step_prev;
+    const int np = (int)X->probs.size();
+    std::vector<std::vector<SweepStep>> chain(np);
+    size_t longest = 0;
+    for (int q = 0; q < np; ++q) {
+      const auto& pr = X->probs[q];
+      const int last = pr.panel0 + pr.m;
+      const int b = pr.panel0 + (X->partial ? X->range_begin : 0), e = X->partial ? pr.panel0 + X->range_end : last;
+      if (pi != 2)
+        for (int i = b; i < e; ++i) chain[q].push_back({i, 0, q});
+      if (pi != 1)
+        for (int i = std::min(e, last - 1) - 1; i >= b; --i) chain[q].push_back({i, 1, q});
+      longest = std::max(longest, chain[q].size());
+    }
+    std::vector<int> lastq(np, -1);
+    for (size_t t = 0; t < longest; ++t)
+      for (int q = 0; q < np; ++q)
+        if (t < chain[q].size()) {
+          step_prev.push_back(lastq[q]);
+          lastq[q] = (int)steps.size();
+          steps.push_back(chain[q][t]);
+        }
+    std::vector<QueueEntry> queue;
+    std::vector<int> step_front(steps.size() + 1, 0), step_tasks(steps.size(), 0);
+    SP.entries = 0;
+    SP.vec = 0;
+    for (size_t k = 0; k < steps.size(); ++k) {
+      const int si = X->shape_of[steps[k].panel];
+      step_front[k + 1] = step_front[k] + X->shapes[si].nsn;
+      step_tasks[k] = shape_tasks[si];
+      SP.entries += shape_entries[si];
+      SP.vec += shape_vec[si];
+      const auto& plan = X->splan[si];
+      for (size_t lv = 0; lv < plan.size(); ++lv)
+        for (int t = 0; t < plan[lv].nfwd; ++t)
+          queue.push_back({(int)k, (int)(plan[lv].fwd_off + t), 0, (short)plan[lv].R});
+      for (int lv = (int)plan.size() - 1; lv >= 0; --lv)
+        for (int t = 0; t < plan[lv].nbwd; ++t) queue.push_back({(int)k, (int)(plan[lv].bwd_off + t), 1, 0});
+    }
+    SP.hsteps = steps;
+    SP.nsteps = (int)steps.size();
+    SP.nqueue = (int)queue.size();
+    upload_async(SP.steps, steps, st);
+    upload_async(SP.queue, queue, st);
+    // metadata: front_base | ntask_up | ntask_down | step_front | step_tasks | step_prev
+    std::vector<int> meta;
+    meta.insert(meta.end(), front_base.begin(), front_base.end());
+    SP.o_up = (int64_t)meta.size();
+    meta.insert(meta.end(), ntask_up.begin(), ntask_up.end());
+    SP.o_down = (int64_t)meta.size();
+    meta.insert(meta.end(), ntask_down.begin(), ntask_down.end());
+    SP.o_step_front = (int64_t)meta.size();
+    meta.insert(meta.end(), step_front.begin(), step_front.end());
+    SP.o_step_tasks = (int64_t)meta.size();
+    meta.insert(meta.end(), step_tasks.begin(), step_tasks.end());
+    if (X->test_sweep_stall && steps.size() > 1) meta[SP.o_step_tasks] += 1;   // step 0 never "completes"
+    SP.o_step_prev = (int64_t)meta.size();
+    meta.insert(meta.end(), step_prev.begin(), step_prev.end());
+    upload_async(SP.meta, meta, st);
+    SP.nfront_steps = step_front[steps.size()];
+    // counters zeroed before every sweep: head | status[4] | step_done[nsteps] | done_up | done_down
+    sync_words = std::max(sync_words, 1 + 4 + steps.size() + 2 * (size_t)SP.nfront_steps);
+  }
   std::vector<ProblemSweep> pss;
   for (const auto& pr : X->probs) {
     ProblemSweep p{};
@@ -1052,8 +1074,7 @@ static void plan_solve(psp_ctx_s* X, cudaStream_t st) {
     pss.push_back(p);
   }
   upload_async(X->d_sweep_probs, pss, st);
-  // counters zeroed before every sweep: head | status[4] | step_done[nsteps] | done_up | done_down
-  X->sweep_sync_words = 1 + 4 + steps.size() + 2 * (size_t)step_front[steps.size()];
+  X->sweep_sync_words = sync_words;
   X->d_sweep_sync.alloc(X->sweep_sync_words * 4);
   PSP_CK(cudaMemsetAsync(X->d_sweep_sync.p, 0, X->sweep_sync_words * 4, st));
 }
@@ -1070,10 +1091,13 @@ static void ensure_apply_ws(psp_ctx_s* X, int nrhs) {
   X->ws_nrhs = nrhs;
 }
 
-// Alg. 1.5 on a device block u (N x nrhs, in place), with the box and update-vector work
-// vectors given by the caller.  `timed` allows CUDA-event timing of the launches.
+// Alg. 1.5 (plan 0), or its forward (plan 1) or backward (plan 2) part over the handle's panels, on a
+// device block u (N x nrhs, in place), with the box and update-vector work vectors given by the
+// caller.  `timed` allows CUDA-event timing of the launches.
 template <typename T>
-static void apply_core(psp_ctx_s* X, double2* u, int nrhs, T* xf, T* xb, T* upd, bool timed, cudaStream_t st) {
+static void apply_core(psp_ctx_s* X, double2* u, int nrhs, T* xf, T* xb, T* upd, bool timed, cudaStream_t st,
+                       int plan_index = 0) {
+  const psp_ctx_s::SweepPlan& SP = X->plans[plan_index];
   SolveCtx<T> cx{};
   const int np = (int)X->probs.size();
   // problem q's vectors and work vectors
@@ -1133,48 +1157,45 @@ static void apply_core(psp_ctx_s* X, double2* u, int nrhs, T* xf, T* xb, T* upd,
     SweepArgs<T> sa{};
     sa.cx = cx;
     sa.nshapes = (int)X->shapes.size();
-    sa.nsteps = X->sweep_nsteps;
+    sa.nsteps = SP.nsteps;
     sa.npanels = X->m;
-    sa.steps = X->d_sweep_steps.as<SweepStep>();
+    sa.steps = SP.steps.as<SweepStep>();
     sa.panels = X->d_sweep_panels.as<PanelSweep>();
     sa.shapes = X->d_shapes.as<ShapeDev>();
     sa.tasks = tasks;
     sa.factor = X->d_factor.as<T>();
-    sa.queue = X->d_sweep_queue.as<QueueEntry>();
-    sa.nqueue = X->sweep_nqueue;
-    const int* meta = X->d_sweep_meta.as<int>();
+    sa.queue = SP.queue.as<QueueEntry>();
+    sa.nqueue = SP.nqueue;
+    const int* meta = SP.meta.as<int>();
     sa.front_base = meta;
-    sa.ntask_up = meta + X->meta_front_base;
-    sa.ntask_down = meta + X->meta_ntask_down;
-    sa.step_front_base = meta + X->meta_step_front;
-    sa.step_tasks = meta + X->meta_step_tasks;
+    sa.ntask_up = meta + SP.o_up;
+    sa.ntask_down = meta + SP.o_down;
+    sa.step_front_base = meta + SP.o_step_front;
+    sa.step_tasks = meta + SP.o_step_tasks;
     sa.nprobs = np;
     sa.probs = X->d_sweep_probs.as<ProblemSweep>();
-    sa.step_prev = np > 1 ? meta + X->meta_step_prev : nullptr;
+    sa.step_prev = np > 1 ? meta + SP.o_step_prev : nullptr;
     unsigned* sync = X->d_sweep_sync.as<unsigned>();
-    const int64_t nfront_steps = ((int64_t)X->sweep_sync_words - 5 - X->sweep_nsteps) / 2;
     sa.queue_head = sync;
     sa.status = reinterpret_cast<int*>(sync + 1);
     sa.sticky = X->d_status.as<int>() + 2;
     sa.step_done = sync + 5;
-    sa.done_up = sync + 5 + X->sweep_nsteps;
-    sa.done_down = sa.done_up + nfront_steps;
+    sa.done_up = sync + 5 + SP.nsteps;
+    sa.done_down = sa.done_up + SP.nfront_steps;
+    const size_t words = 5 + (size_t)SP.nsteps + 2 * (size_t)SP.nfront_steps;
     int rc = -1;
-    if (X->persistent_sweep) {
+    if (SP.nsteps == 0) rc = 0;   // an empty part (the backward part of a block holding the last panel alone)
+    else if (X->persistent_sweep) {
       // queue head and completion counters start at zero; status[2] is cleared too
-      PSP_CK(cudaMemsetAsync(sync, 0, X->sweep_sync_words * 4, st));
+      PSP_CK(cudaMemsetAsync(sync, 0, words * 4, st));
       const double es = sizeof(T);
-      X->stats.run("k_sweep", st, 1, 8.0 * X->sweep_entries * nrhs,
-                   X->sweep_entries * es + X->sweep_vec * es * nrhs,
+      X->stats.run("k_sweep", st, 1, 8.0 * SP.entries * nrhs, SP.entries * es + SP.vec * es * nrhs,
                    [&] { rc = launch_sweep<T>(sa, X->sweep_rhs_bytes * sizeof(T), X->sweep_ctas_per_sm, X->sweep_rhs_group, st); });
       if (rc > 0) throw Error{PSP_ERR_CUDA, std::string("sweep launch: ") + cudaGetErrorString((cudaError_t)rc)};
     }
     if (rc != 0) {
-      for (int q = 0; q < np; ++q) {
-        const auto& pr = X->probs[q];
-        for (int i = 0; i < pr.m; ++i) runT(q, pr.panel0 + i, 0);        // u_i := T_i (u_i - J_{i,i-1} u_{i-1})
-        for (int i = pr.m - 2; i >= 0; --i) runT(q, pr.panel0 + i, 1);   // u_i -= T_i J_{i+1,i}^T u_{i+1}
-      }
+      // one launch per tree level: mode 0 u_i := T_i (u_i - J_{i,i-1} u_{i-1}); mode 1 u_i -= T_i J_{i+1,i}^T u_{i+1}
+      for (const SweepStep& sp : SP.hsteps) runT(sp.prob, sp.panel, sp.mode);
     }
   } catch (...) {
     X->stats.timing = was_timing;
@@ -1199,6 +1220,7 @@ size_t apply_workspace_bytes(const psp_ctx_s* X, int nrhs) {
 }
 
 psp_status apply_with_workspace(psp_ctx_s* X, double2* u, int nrhs, void* ws, cudaStream_t st) {
+  if (X->partial) return set_error(PSP_ERR_STATE, "the handle holds one block of panels; use psp_sweep_part");
   try {
     char* p = static_cast<char*>(ws);
     const size_t e = X->elem_bytes;
@@ -1251,6 +1273,36 @@ static void apply_dispatch(psp_ctx_s* X, double2* u, int nrhs, cudaStream_t st) 
 // ---------------------------------------------------------------------------
 // setup
 // ---------------------------------------------------------------------------
+// Panel plan (§1.1, Alg. 1.4): panel 0 = planes [0, gamma + d), then d planes each, the last one
+// taking the remainder; lead = planes of the auxiliary box before the panel's own (the pad, or all
+// planes below in exact mode, none for panel 0).
+static void panel_plan(int nz, int gamma, int depth, int pad, int aux_mode, std::vector<int>& z0, std::vector<int>& z1,
+                       std::vector<int>& lead) {
+  z0.clear();
+  z1.clear();
+  lead.clear();
+  const int first = std::min(gamma + depth, nz);
+  z0.push_back(0);
+  z1.push_back(first);
+  for (int z = first; z < nz; z += depth) {
+    z0.push_back(z);
+    z1.push_back(std::min(z + depth, nz));
+  }
+  for (size_t i = 0; i < z0.size(); ++i)
+    lead.push_back(z0[i] == 0 ? 0 : aux_mode == PSP_AUX_EXACT ? z0[i] : pad);
+}
+
+// algorithmic setup flops of one factored box: per front LDL^T of F_TL (s^3/3), F_BL L^{-T} (u s^2/2)
+// and the Schur update (u(u+1)/2 s) complex multiply-adds, 8 flops each
+static double shape_setup_flops(const Shape& sh) {
+  double cm = 0;
+  for (int f = 0; f < sh.nsn; ++f) {
+    const double s = sh.s[f], u = sh.u[f];
+    cm += s * s * s / 3 + u * s * s / 2 + u * (u + 1) / 2 * s;
+  }
+  return 8.0 * cm;
+}
+
 // One problem's own part of setup: wave speed, PML tables, panel plan, shapes and box operators
 // (kept on the host in X->h_boxops); no factor storage yet.
 static void build_problem(psp_ctx_s* X, const double* c, cudaStream_t st) {
@@ -1276,18 +1328,14 @@ static void build_problem(psp_ctx_s* X, const double* c, cudaStream_t st) {
     for (int k = 0; k <= n; ++k)
       gt.push_back(inv_stretch(sigma_axis(k - 0.5, n, X->gamma, X->C, X->h, f[2 * a], f[2 * a + 1]), X->omega));
   }
-  // panel plan (§1.1, Alg. 1.4): panel 0 = [0, gamma + d), then d planes each
-  X->z0.clear(); X->z1.clear(); X->lead.clear();
-  {
-    int first = std::min(X->gamma + X->depth, nz);
-    X->z0.push_back(0);
-    X->z1.push_back(first);
-    for (int z = first; z < nz; z += X->depth) {
-      X->z0.push_back(z);
-      X->z1.push_back(std::min(z + X->depth, nz));
-    }
-  }
+  panel_plan(nz, X->gamma, X->depth, X->pad, X->aux_mode, X->z0, X->z1, X->lead);
   X->m = (int)X->z0.size();
+  // the block of panels this handle factors and sweeps
+  X->range_end = X->range_count > 0 ? X->range_begin + X->range_count : X->m;
+  if (X->range_begin < 0 || X->range_begin >= X->m || X->range_end > X->m)
+    throw Error{PSP_ERR_ARG, "panel block [" + std::to_string(X->range_begin) + ", " + std::to_string(X->range_end) +
+                                 ") is not within the " + std::to_string(X->m) + " panels"};
+  X->partial = X->range_begin > 0 || X->range_end < X->m;
   // per-panel tables: s3 nodes, 1/s3 half-points, c plane map (device-global layout appended to gt)
   std::vector<int32_t> cplane_all;
   std::vector<int64_t> p_s3n(X->m), p_s3h(X->m), p_cpl(X->m);
@@ -1297,11 +1345,7 @@ static void build_problem(psp_ctx_s* X, const double* c, cudaStream_t st) {
   X->shape_of.assign(X->m, 0);
   for (int i = 0; i < X->m; ++i) {
     const int z0 = X->z0[i], z1 = X->z1[i];
-    int lead;
-    if (z0 == 0) lead = 0;
-    else if (X->aux_mode == PSP_AUX_EXACT) lead = z0;
-    else lead = X->pad;
-    X->lead.push_back(lead);
+    const int lead = X->lead[i];
     const int D = lead + (z1 - z0);
     p_s3n[i] = (int64_t)gt.size();
     for (int k = 0; k < D; ++k) {
@@ -1370,8 +1414,8 @@ static void build_problem(psp_ctx_s* X, const double* c, cudaStream_t st) {
   // distinct panel factorisations): same box depth and pad, bitwise the same x3-stretch tables and
   // the same wave speed on every plane the box uses
   X->owner.resize(X->m);
-  for (int i = 0; i < X->m; ++i) X->owner[i] = i;
-  if (!X->factor_every_panel && X->aux_mode == PSP_AUX_MOVING_PML && X->m > 2) {
+  for (int i = 0; i < X->m; ++i) X->owner[i] = i >= X->range_begin && i < X->range_end ? i : -1;   // -1: not factored here
+  if (!X->factor_every_panel && X->aux_mode == PSP_AUX_MOVING_PML && X->range_end - X->range_begin > 1) {
     const int64_t plane = (int64_t)nx * ny;
     std::vector<double> hc((size_t)X->N);
     PSP_CK(cudaMemcpyAsync(hc.data(), c, X->N * sizeof(double), cudaMemcpyDefault, st));   // c: host or device
@@ -1400,7 +1444,7 @@ static void build_problem(psp_ctx_s* X, const double* c, cudaStream_t st) {
       return true;
     };
     std::map<uint64_t, std::vector<int>> seen;
-    for (int i = 1; i < X->m; ++i) {
+    for (int i = std::max(1, X->range_begin); i < X->range_end; ++i) {
       const int D = depth_of(i);
       uint64_t h = mix(mix(1469598103934665603ull, D), X->lead[i]);
       h = words(h, &gt[p_s3n[i]], D * sizeof(double2));
@@ -1541,8 +1585,10 @@ static void finish_setup(psp_ctx_s* X, cudaStream_t st) {
       fe += sh.g_total;
       X->nfronts_factored += sh.nsn;
       X->distinct_panels += 1;
-    } else {
+    } else if (X->owner[i] >= 0) {
       X->panel_fbase[i] = X->panel_fbase[X->owner[i]];   // the owner comes first
+    } else {
+      X->panel_fbase[i] = 0;                              // outside this handle's block: never read
     }
   }
   X->nfronts = nf;
@@ -1857,7 +1903,7 @@ static psp_status check_options(const psp_options* opt, psp_options* o) {
   if (o->leaf_size < 1 || o->pml_faces < 0 || o->pml_faces > 63 ||
       (o->precision != PSP_PREC_C128 && o->precision != PSP_PREC_C64) ||
       (o->aux_mode != PSP_AUX_MOVING_PML && o->aux_mode != PSP_AUX_EXACT) || !(o->alpha >= 0) || !(o->pml_C >= 0) ||
-      o->gmres_basis < 0 || o->gmres_basis > 2)
+      o->gmres_basis < 0 || o->gmres_basis > 2 || o->panel_begin < 0 || o->panel_count < 0)
     return fail(PSP_ERR_ARG, "bad options");
   return PSP_OK;
 }
@@ -1885,6 +1931,8 @@ static void init_options(psp_ctx_s* X, const psp_options& o) {
   X->solve_rhs_group = o.solve_rhs_group > 0 ? o.solve_rhs_group : 0;
   X->gmres_basis = o.gmres_basis;
   X->factor_every_panel = o.factor_every_panel != 0;
+  X->range_begin = o.panel_begin;
+  X->range_count = o.panel_count;
   X->test_sweep_stall = o.test_sweep_stall == 1;
   X->temp_budget_elems = o.setup_temp_mb > 0 ? ((int64_t)o.setup_temp_mb << 20) / (o.precision == PSP_PREC_C64 ? 8 : 16) : 0;
 }
@@ -1938,6 +1986,7 @@ psp_status psp_setup_batch(int nprob, const psp_grid* grids, const double* const
   psp_options o;
   psp_status cs = check_options(opt, &o);
   if (cs != PSP_OK) return cs;
+  if (o.panel_begin != 0 || o.panel_count != 0) return fail(PSP_ERR_ARG, "a batch handle holds every panel of its problems");
   psp_ctx_s* B = nullptr;
   try {
     B = new psp_ctx_s();
@@ -1965,9 +2014,12 @@ psp_status psp_batch_layout(psp_handle X, int* nprob, int64_t* points, int capac
   return PSP_OK;
 }
 
+static const char* kPartialMsg = "the handle holds one block of panels; apply its part with psp_sweep_part";
+
 psp_status psp_apply(psp_handle X, const double* rhs, double* out, int nrhs, void* stream) {
   if (!X || !rhs || !out || nrhs < 1) return fail(PSP_ERR_ARG, "bad apply arguments");
   if (!X->d_factor.p) return fail(PSP_ERR_STATE, "handle has no factorisation");
+  if (X->partial) return fail(PSP_ERR_STATE, kPartialMsg);
   PSP_TRY
   check_device(X);
   cudaStream_t st = (cudaStream_t)stream;
@@ -2029,6 +2081,7 @@ psp_status psp_solve(psp_handle X, const double* f, double* u, int nrhs, double 
                      psp_solve_info* info, void* stream) {
   if (!X || !f || !u || nrhs < 1 || !(tol > 0) || k < 1 || maxit < 1) return fail(PSP_ERR_ARG, "bad solve arguments");
   if (!X->d_factor.p) return fail(PSP_ERR_STATE, "handle has no factorisation");
+  if (X->partial) return fail(PSP_ERR_STATE, kPartialMsg);
   PSP_TRY
   check_device(X);
   cudaStream_t st = (cudaStream_t)stream;
@@ -2141,6 +2194,7 @@ psp_status psp_export_front(psp_handle X, int panel, int sn, double* buf, int* s
   if (!X || panel < 0 || panel >= X->m) return fail(PSP_ERR_ARG, "bad panel");
   const Shape& sh = X->shapes[X->shape_of[panel]];
   if (sn < 0 || sn >= sh.nsn) return fail(PSP_ERR_ARG, "bad supernode");
+  if (X->owner.empty() || X->owner[panel] < 0) return fail(PSP_ERR_ARG, "the panel is outside this handle's block");
   if (s) *s = sh.s[sn];
   if (u) *u = sh.u[sn];
   if (!buf) return PSP_OK;
@@ -2262,6 +2316,70 @@ psp_status psp_tune_sweep(psp_handle X, int nrhs, int reps, void* stream, psp_sw
     out->candidates = timed;
     out->initial_ms = initial_ms;
     out->best_ms = best_ms;
+  }
+  return PSP_OK;
+  PSP_CATCH
+}
+
+psp_status psp_sweep_part(psp_handle X, double* u, int nrhs, int direction, void* stream) {
+  if (!X || !u || nrhs < 1 || (direction != 0 && direction != 1)) return fail(PSP_ERR_ARG, "bad sweep-part arguments");
+  if (!X->d_factor.p) return fail(PSP_ERR_STATE, "handle has no factorisation");
+  if (X->probs.size() != 1) return fail(PSP_ERR_STATE, "psp_sweep_part takes single-problem handles");
+  PSP_TRY
+  check_device(X);
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = (size_t)X->N * nrhs * sizeof(double2);
+  const bool dev = is_device_pointer(u);
+  double2* ud = reinterpret_cast<double2*>(u);
+  if (!dev) {
+    X->stage_out.ensure(bytes);
+    ud = X->stage_out.as<double2>();
+    PSP_CK(cudaMemcpyAsync(ud, u, bytes, cudaMemcpyHostToDevice, st));
+  }
+  const int plan = direction == 0 ? 1 : 2;
+  if (X->prec == PSP_PREC_C64) {
+    ensure_apply_ws<float2>(X, nrhs);
+    apply_core<float2>(X, ud, nrhs, X->ws_xf.as<float2>(), X->ws_xb.as<float2>(), X->ws_upd.as<float2>(), true, st, plan);
+  } else {
+    ensure_apply_ws<double2>(X, nrhs);
+    apply_core<double2>(X, ud, nrhs, X->ws_xf.as<double2>(), X->ws_xb.as<double2>(), X->ws_upd.as<double2>(), true, st,
+                        plan);
+  }
+  if (!dev) {
+    PSP_CK(cudaMemcpyAsync(u, ud, bytes, cudaMemcpyDeviceToHost, st));
+    PSP_CK(cudaStreamSynchronize(st));
+    if (sweep_gave_up(X, st)) return fail(PSP_ERR_TIMEOUT, "a dependency wait of the sweep gave up; u is incomplete");
+  }
+  return PSP_OK;
+  PSP_CATCH
+}
+
+psp_status psp_plan_panels(const psp_grid* g, int pml_gamma, int panel_depth, const psp_options* opt, int* z0, int* z1,
+                           double* cost, int capacity, int* m) {
+  if (!g || !m || capacity < 0 || (capacity > 0 && (!z0 || !z1))) return fail(PSP_ERR_ARG, "bad plan arguments");
+  if (g->nx < 1 || g->ny < 1 || g->nz < 1 || pml_gamma < 0 || panel_depth < 1) return fail(PSP_ERR_ARG, "bad grid");
+  psp_options o;
+  psp_status cs = check_options(opt, &o);
+  if (cs != PSP_OK) return cs;
+  PSP_TRY
+  const int pad = o.pad_depth < 0 ? pml_gamma : o.pad_depth;
+  std::vector<int> a, b, lead;
+  panel_plan(g->nz, pml_gamma, panel_depth, pad, o.aux_mode, a, b, lead);
+  *m = (int)a.size();
+  std::map<int, double> flops_of_depth;   // box depth -> setup flops of its factorisation
+  for (int i = 0; i < (int)a.size() && i < capacity; ++i) {
+    z0[i] = a[i];
+    z1[i] = b[i];
+    if (cost) {
+      const int D = lead[i] + b[i] - a[i];
+      auto it = flops_of_depth.find(D);
+      if (it == flops_of_depth.end()) {
+        Shape sh;
+        build_shape(sh, g->nx, g->ny, D, o.leaf_size);
+        it = flops_of_depth.emplace(D, shape_setup_flops(sh)).first;
+      }
+      cost[i] = it->second;
+    }
   }
   return PSP_OK;
   PSP_CATCH

@@ -36,7 +36,7 @@ class Options(ctypes.Structure):
                 ("sweep_level_tasks", ctypes.c_int), ("sweep_ctas_per_sm", ctypes.c_int),
                 ("setup_temp_mb", ctypes.c_int), ("sweep_rhs_group", ctypes.c_int),
                 ("solve_rhs_group", ctypes.c_int), ("test_sweep_stall", ctypes.c_int), ("gmres_basis", ctypes.c_int),
-                ("factor_every_panel", ctypes.c_int)]
+                ("factor_every_panel", ctypes.c_int), ("panel_begin", ctypes.c_int), ("panel_count", ctypes.c_int)]
 
 
 class KernelStat(ctypes.Structure):
@@ -105,6 +105,9 @@ def lib():
         "psp_stats": (_I, [_P, ctypes.POINTER(KernelStat), _I, ctypes.POINTER(_I), _I]),
         "psp_tune_sweep": (_I, [_P, _I, _I, _P, ctypes.POINTER(SweepTuning)]),
         "psp_check_status": (_I, [_P, _P]),
+        "psp_sweep_part": (_I, [_P, _P, _I, _I, _P]),
+        "psp_plan_panels": (_I, [ctypes.POINTER(Grid), _I, _I, ctypes.POINTER(Options), ctypes.POINTER(_I),
+                                 ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double), _I, ctypes.POINTER(_I)]),
         "psp_destroy": (_I, [_P]),
         "psp_status_string": (ctypes.c_char_p, [_I]),
         "psp_last_error": (ctypes.c_char_p, []),
@@ -157,7 +160,8 @@ class SweepingPreconditioner:
     def __init__(self, c, h, omega, gamma, panel_depth, pad=None, leaf=64, pml_C=4.0, alpha=2 * math.pi,
                  precision="c128", faces=63, mode="moving", stream=None, collect_stats=0, tensor_cores=True,
                  tc_min_dim=0, sweep_level_tasks=0, sweep_ctas_per_sm=0, setup_temp_mb=0, sweep_rhs_group=0,
-                 solve_rhs_group=0, test_sweep_stall=0, gmres_basis="auto", factor_every_panel=False):
+                 solve_rhs_group=0, test_sweep_stall=0, gmres_basis="auto", factor_every_panel=False,
+                 panels=None):
         nz, ny, nx = c.shape
         self.nx, self.ny, self.nz = nx, ny, nz
         self.N = nx * ny * nz
@@ -168,6 +172,8 @@ class SweepingPreconditioner:
         o.test_sweep_stall = int(test_sweep_stall)
         o.gmres_basis = {"auto": 0, "z": 1, "v": 2}[gmres_basis]
         o.factor_every_panel = 1 if factor_every_panel else 0
+        if panels is not None:                   # (first, count): one block of a multi-GPU sweep
+            o.panel_begin, o.panel_count = int(panels[0]), int(panels[1])
         cp, n = _ptr_and_len(c, complex_=False)
         if n != self.N:
             raise ValueError("c has the wrong size")
@@ -221,6 +227,12 @@ class SweepingPreconditioner:
         if st != 0 and (raise_on_nonconvergence or st != 5):
             _check(st)
         return info.as_dict()
+
+    def sweep_part(self, u, direction, stream=None):
+        """psp_sweep_part: the forward (0) or backward (1) half of Alg. 1.5 over this handle's block, in place."""
+        nr = self._nrhs(u)
+        _check(lib().psp_sweep_part(self._h, _ptr_and_len(u)[0], nr, int(direction), _stream(stream)))
+        return u
 
     def check_status(self, stream=None):
         """psp_check_status: raise PSPError(PSP_ERR_TIMEOUT) if a sweep wait gave up since the last check."""
@@ -367,3 +379,18 @@ def parse_symbolic(buf):
         p += u
         sns.append((s, u, par, nodes, struct))
     return {"nx": nx, "ny": ny, "nz": nz, "lead": lead, "nsn": nsn}, sns
+
+
+def plan_panels(nx, ny, nz, h, gamma, panel_depth, pad=None, leaf=64, mode="moving"):
+    """psp_plan_panels (host only): [(z0, z1), ...] of the m panels and each panel's setup flops."""
+    o = _options(pad, leaf, 4.0, 2 * math.pi, "c128", 63, mode, 0, True, 0, 0, 0, 0)
+    g = Grid(int(nx), int(ny), int(nz), float(h))
+    m = _I()
+    _check(lib().psp_plan_panels(ctypes.byref(g), int(gamma), int(panel_depth), ctypes.byref(o), None, None, None, 0,
+                                 ctypes.byref(m)))
+    z0 = (_I * m.value)()
+    z1 = (_I * m.value)()
+    cost = (ctypes.c_double * m.value)()
+    _check(lib().psp_plan_panels(ctypes.byref(g), int(gamma), int(panel_depth), ctypes.byref(o), z0, z1, cost, m.value,
+                                 ctypes.byref(m)))
+    return [(z0[i], z1[i]) for i in range(m.value)], [cost[i] for i in range(m.value)]
