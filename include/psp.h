@@ -117,6 +117,16 @@ typedef struct {
                            multi-GPU sweep, see psp_sweep_part), default 0 */
   int panel_count;      /* panels in that block; 0 (default): through the last panel.  A handle holding
                            a proper block takes psp_sweep_part, not psp_apply / psp_solve */
+  /* Device memory of the handle (factors, update matrices, work vectors, tables): when both are
+     given, every allocation the library makes for this handle calls dev_alloc(bytes, alloc_ctx) and
+     every release dev_free(ptr, alloc_ctx), so a framework's allocator can own that memory; NULL
+     (default): cudaMalloc / cudaFree.  dev_alloc returns device memory of the current device aligned
+     to 256 bytes, or NULL, which the call reports as PSP_ERR_OOM.  It is called from the thread
+     that calls the library, outside any kernel; memory is handed back with dev_free only after the
+     work using it has finished.  One given without the other is PSP_ERR_ARG. */
+  void* (*dev_alloc)(size_t bytes, void* ctx);
+  void (*dev_free)(void* ptr, void* ctx);
+  void* alloc_ctx;
 } psp_options;
 
 /* Per-solve report filled by psp_solve (host struct). */
@@ -130,7 +140,9 @@ typedef struct {
   int status_front;    /* front id of a zero pivot, -1 if none */
   int groups;          /* GMRES runs the right-hand sides were solved in (1 unless their Krylov bases
                           did not fit the free device memory together) */
-  int reserved[6];
+  double min_pivot_abs; /* smallest |d_jj| of the handle's LDL^T factorisation (the pivot monitor of the
+                           unpivoted factorisation, §2.5: the solver does no pivoting) */
+  int reserved[4];
 } psp_solve_info;
 
 void psp_default_options(psp_options* opt);
@@ -237,6 +249,17 @@ psp_status psp_matvec(psp_handle h, int which, const double* x, double* y, int n
  */
 psp_status psp_solve(psp_handle h, const double* f, double* u, int nrhs, double tol, int k, int maxit,
                      psp_solve_info* info, void* stream);
+
+/*
+ * psp_solve_history - the residual history of the handle's last psp_solve, one column per
+ * right-hand side (per problem and right-hand side for a batch), row-major rows x cols:
+ *   kind 0: the Arnoldi estimate |g_{j+1}| / ||b|| after each inner GMRES iteration;
+ *   kind 1: the true relative residual ||b - A_s u|| / ||b|| at the end of each restart cycle.
+ * A column that stopped earlier than others (converged, or solved in another GMRES run) repeats its
+ * last value.  Call with buf = NULL for the sizes.  Errors: PSP_ERR_ARG (kind, or capacity below
+ * rows x cols), PSP_ERR_STATE (no solve yet).
+ */
+psp_status psp_solve_history(psp_handle h, int kind, double* buf, int capacity, int* rows, int* cols);
 
 /*
  * psp_symbolic_export - the nested-dissection tree of panel `panel`'s auxiliary

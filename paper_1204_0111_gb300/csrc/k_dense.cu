@@ -13,7 +13,9 @@ constexpr int kNB = 32;  // diagonal block size of the blocked LDL^T and inverse
 // ---------------------------------------------------------------------------
 // LDL^T of the kb-th diagonal block of F_TL (unblocked, right-looking, in shared memory).
 // The block is overwritten by its unit lower factor (strict part) and D (diagonal).
-// A pivot with |d| < tiny records 1 + (front's global id) in status[0].
+// A pivot with |d| < tiny records 1 + (front's global id) in status[0]; the smallest |d| of all
+// pivots is kept in status[4..5] as the bitwise complement of its double (atomicMax of the
+// complement = minimum of the non-negative value; 0 = no pivot yet).
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256) k_diag_ldlt(const FrontTask<T>* __restrict__ fronts, const int* __restrict__ list,
@@ -30,9 +32,13 @@ __global__ void __launch_bounds__(256) k_diag_ldlt(const FrontTask<T>* __restric
     if (r >= c) S[c][r] = B[(int64_t)c * ld + r];
   }
   __syncthreads();
+  double dmin = INFINITY;
   for (int j = 0; j < bs; ++j) {
     const T d = S[j][j];
-    if (threadIdx.x == 0 && fmax(fabs((double)d.x), fabs((double)d.y)) < tiny) atomicCAS(status, 0, (int)(1 + ft.gfid));
+    if (threadIdx.x == 0) {
+      if (fmax(fabs((double)d.x), fabs((double)d.y)) < tiny) atomicCAS(status, 0, (int)(1 + ft.gfid));
+      dmin = fmin(dmin, hypot((double)d.x, (double)d.y));
+    }
     const T dinv = cdiv(CplxTraits<T>::one(), d);
     for (int i = j + 1 + threadIdx.x; i < bs; i += blockDim.x) {
       const T a = S[j][i];
@@ -52,6 +58,8 @@ __global__ void __launch_bounds__(256) k_diag_ldlt(const FrontTask<T>* __restric
     const int r = e % bs, c = e / bs;
     if (r >= c) B[(int64_t)c * ld + r] = S[c][r];
   }
+  if (threadIdx.x == 0 && dmin == dmin)   // a NaN pivot leaves the minimum alone (status[0] reports it if tiny)
+    atomicMax(reinterpret_cast<unsigned long long*>(status + 4), ~(unsigned long long)__double_as_longlong(dmin));
 }
 
 // ---------------------------------------------------------------------------

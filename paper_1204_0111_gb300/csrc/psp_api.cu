@@ -37,24 +37,61 @@ struct Error {
                   std::string(#call) + ": " + cudaGetErrorString(e_) + " (line " + std::to_string(__LINE__) + ")"}; \
   } while (0)
 
-// Owning device allocation.
+// Device allocator of a handle: the caller's callbacks (psp_options.dev_alloc / dev_free) or, when
+// they are not given, cudaMalloc / cudaFree.
+struct Allocator {
+  void* (*alloc)(size_t, void*) = nullptr;
+  void (*free)(void*, void*) = nullptr;
+  void* ctx = nullptr;
+};
+// The allocator of the handle whose entry point is running on this thread (set by AllocScope).
+static thread_local const Allocator* g_alloc = nullptr;
+struct AllocScope {
+  const Allocator* prev;
+  explicit AllocScope(const Allocator* a) : prev(g_alloc) { g_alloc = a; }
+  ~AllocScope() { g_alloc = prev; }
+};
+
+static void* dev_alloc(size_t b, const Allocator* A) {
+  void* p = nullptr;
+  if (A && A->alloc) {
+    p = A->alloc(b, A->ctx);
+    if (!p) throw Error{PSP_ERR_OOM, "the caller's dev_alloc returned NULL for " + std::to_string(b) + " bytes"};
+  } else {
+    PSP_CK(cudaMalloc(&p, b));
+  }
+  return p;
+}
+static void dev_free(void* p, const Allocator* A) {
+  if (!p) return;
+  if (A && A->free) {
+    cudaDeviceSynchronize();   // the caller's allocator need not be stream-ordered: no work may still use p
+    A->free(p, A->ctx);
+  } else {
+    cudaFree(p);
+  }
+}
+
+// Owning device allocation; freed with the allocator it was made with.
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
+  const Allocator* A = nullptr;
   DevBuf() = default;
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
-  DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+  DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes), A(o.A) { o.p = nullptr; o.bytes = 0; }
   ~DevBuf() { release(); }
   void release() {
-    if (p) cudaFree(p);
+    dev_free(p, A);
     p = nullptr;
     bytes = 0;
   }
   void alloc(size_t b) {
     release();
     if (b == 0) b = 16;
-    PSP_CK(cudaMalloc(&p, b));
+    A = g_alloc;
+    p = dev_alloc(b, A);
     bytes = b;
   }
   void ensure(size_t b) {
@@ -196,6 +233,7 @@ struct Stats {
 using namespace psp;
 
 struct psp_ctx_s {
+  Allocator allocator;   // first member: destroyed after every buffer made with it
   // problem
   int nx = 0, ny = 0, nz = 0;
   int64_t N = 0;
@@ -264,6 +302,12 @@ struct psp_ctx_s {
   DevBuf gm;
   int gm_nrhs = 0, gm_k = 0;
   int zero_pivot_front = -1;
+  double min_pivot_abs = INFINITY;   // smallest |d_jj| of the factorisation (pivot monitor)
+  // residual history of the last solve: [kind][row][col], kind 0 Arnoldi estimates per iteration,
+  // kind 1 true residuals per restart cycle
+  std::vector<std::vector<double>> hist[2];
+  int hist_cols = 0;
+  bool has_history = false;
   int device = -1;          // CUDA device current at setup; every later call must run with it current
   bool use_tc = true;
   int tc_min_dim = 64;
@@ -477,17 +521,25 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
   // the host plans the next group while the device factors this one.  Task arrays go to
   // stream-ordered device chunks, one per group and array, freed after the final synchronisation.
   int* status = X->d_status.as<int>();
-  PSP_CK(cudaMemsetAsync(status, 0, 4 * sizeof(int), st));
+  // status: [0] 1 + front of a zero pivot, [1] tensor-core wait gave up, [2] sweep wait gave up (sticky),
+  // [4..5] ~bits of the smallest |pivot| (0: none yet)
+  PSP_CK(cudaMemsetAsync(status, 0, 8 * sizeof(int), st));
   static const char* names[] = {"k_assemble", "k_diag_ldlt", "k_panel_right", "k_panel_left", "k_gemm", "k_copy_linv",
                                 "k_tc_gemm", "k_tc_pack", "k_scale_zd"};
   std::vector<void*> chunks;
+  const Allocator* chunk_alloc = g_alloc && g_alloc->alloc ? g_alloc : nullptr;
   struct ChunkGuard {
     std::vector<void*>& c;
     cudaStream_t s;
+    const Allocator* A;
     ~ChunkGuard() {
-      for (void* p : c) cudaFreeAsync(p, s);
+      if (A && !c.empty()) cudaStreamSynchronize(s);   // the caller's free is not stream-ordered
+      for (void* p : c) {
+        if (A) dev_free(p, A);
+        else cudaFreeAsync(p, s);
+      }
     }
-  } chunk_guard{chunks, st};
+  } chunk_guard{chunks, st, chunk_alloc};
   // copies v[done, size) to a new device chunk (the copy from pageable memory is staged before the
   // call returns, so the vector may grow afterwards); returns the chunk and advances done
   auto upload_tail = [&](const auto& v, size_t& done) {
@@ -495,7 +547,8 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
     const size_t n = v.size() - done;
     E* d = nullptr;
     if (n > 0) {
-      PSP_CK(cudaMallocAsync(reinterpret_cast<void**>(&d), n * sizeof(E), st));
+      if (chunk_alloc) d = static_cast<E*>(dev_alloc(n * sizeof(E), chunk_alloc));
+      else PSP_CK(cudaMallocAsync(reinterpret_cast<void**>(&d), n * sizeof(E), st));
       chunks.push_back(d);
       PSP_CK(cudaMemcpyAsync(d, v.data() + done, n * sizeof(E), cudaMemcpyHostToDevice, st));
     }
@@ -918,8 +971,16 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
   tp = std::chrono::steady_clock::now();
   PSP_CK(cudaStreamSynchronize(st));
   X->stats.host("wait_setup", ms_since(tp));
-  int hs[4];
+  int hs[8];
   PSP_CK(cudaMemcpy(hs, status, sizeof(hs), cudaMemcpyDeviceToHost));
+  {
+    unsigned long long nb;
+    std::memcpy(&nb, hs + 4, sizeof(nb));
+    const unsigned long long bits = ~nb;
+    double mp;
+    std::memcpy(&mp, &bits, sizeof(mp));
+    X->min_pivot_abs = nb == 0 ? INFINITY : mp;
+  }
   if (hs[1] != 0) throw Error{PSP_ERR_TIMEOUT, "a tensor-core GEMM gave up waiting for its MMAs"};
   if (hs[0] != 0) {
     X->zero_pivot_front = hs[0] - 1;
@@ -1611,7 +1672,7 @@ static void finish_setup(psp_ctx_s* X, cudaStream_t st) {
   X->stats.host("device_tables", ms_since(t_start));
   auto ta = std::chrono::steady_clock::now();
   X->d_factor.alloc((size_t)fe * X->elem_bytes);
-  X->d_status.alloc(4 * sizeof(int));
+  X->d_status.alloc(8 * sizeof(int));
   X->stats.host("alloc_factors", ms_since(ta));
   // the sweep's plan is host work the device does not need for the factorisation: it runs while
   // the device factors
@@ -1674,7 +1735,9 @@ static void setup_batch_impl(psp_ctx_s* B, int nprob, const double* const* c, cu
 // otherwise keep one work vector and form x += M^{-1} (V y) with one more application per cycle
 // (right preconditioning: both give x0 + M^{-1} V y), which halves the vectors kept per right-hand side.
 static void solve_impl(psp_ctx_s* X, const double2* f, double2* x, int nrhs_in, double tol, int k, int maxit,
-                       psp_solve_info* info, cudaStream_t st, bool store_z) {
+                       psp_solve_info* info, cudaStream_t st, bool store_z,
+                       std::vector<std::vector<double>>* hist_est = nullptr,
+                       std::vector<std::vector<double>>* hist_true = nullptr) {
   // GMRES columns: right-hand side r of problem q is column q * nrhs + r, the span
   // [off1_q nrhs + r N_q, + N_q) of every vector block; all columns iterate in lockstep but each
   // has its own Krylov basis, Hessenberg matrix and convergence test
@@ -1752,7 +1815,7 @@ static void solve_impl(psp_ctx_s* X, const double2* f, double2* x, int nrhs_in, 
           [&] { launch_scale_rhs(pr.opA, f + o, b + o, nrhs_in, pr.N, st); });
   }
   // ||b||
-  std::vector<double> bnorm(nrhs), rel(nrhs, 1.0), hres(nrhs);
+  std::vector<double> bnorm(nrhs), rel(nrhs, 1.0), hres(nrhs), est(nrhs, 1.0);
   std::vector<int> act(nrhs, 1), its(nrhs, 0), restarts(nrhs, 0), jrh(nrhs, 0);
   multidot(b, 0, 1, b, nrm);
   std::vector<double2> hn(nrhs);
@@ -1797,9 +1860,11 @@ static void solve_impl(psp_ctx_s* X, const double2* f, double2* x, int nrhs_in, 
         if (!act[r]) continue;
         its[r]++;
         jrh[r] = j + 1;
-        if (hres[r] / bnorm[r] < tol) act[r] = 0;   // converged within the cycle (estimate)
+        est[r] = hres[r] / bnorm[r];
+        if (est[r] < tol) act[r] = 0;   // converged within the cycle (estimate)
         else all_done = false;
       }
+      if (hist_est) hist_est->push_back(est);
       PSP_CK(cudaMemcpyAsync(active, act.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
       if (all_done) { ++j; break; }
     }
@@ -1833,6 +1898,7 @@ static void solve_impl(psp_ctx_s* X, const double2* f, double2* x, int nrhs_in, 
       act[r] = rel[r] >= tol ? 1 : 0;
       if (act[r]) any = true;
     }
+    if (hist_true) hist_true->push_back(rel);
   }
   auto t1 = std::chrono::steady_clock::now();
   const double relmax = *std::max_element(rel.begin(), rel.end());
@@ -1903,7 +1969,8 @@ static psp_status check_options(const psp_options* opt, psp_options* o) {
   if (o->leaf_size < 1 || o->pml_faces < 0 || o->pml_faces > 63 ||
       (o->precision != PSP_PREC_C128 && o->precision != PSP_PREC_C64) ||
       (o->aux_mode != PSP_AUX_MOVING_PML && o->aux_mode != PSP_AUX_EXACT) || !(o->alpha >= 0) || !(o->pml_C >= 0) ||
-      o->gmres_basis < 0 || o->gmres_basis > 2 || o->panel_begin < 0 || o->panel_count < 0)
+      o->gmres_basis < 0 || o->gmres_basis > 2 || o->panel_begin < 0 || o->panel_count < 0 ||
+      (o->dev_alloc == nullptr) != (o->dev_free == nullptr))
     return fail(PSP_ERR_ARG, "bad options");
   return PSP_OK;
 }
@@ -1918,6 +1985,9 @@ static psp_status check_problem(const psp_grid* g, const double* c, double omega
 
 // handle-wide settings from the options
 static void init_options(psp_ctx_s* X, const psp_options& o) {
+  X->allocator.alloc = o.dev_alloc;
+  X->allocator.free = o.dev_free;
+  X->allocator.ctx = o.alloc_ctx;
   X->alpha = o.alpha; X->C = o.pml_C;
   X->leaf = o.leaf_size; X->prec = o.precision; X->faces = o.pml_faces; X->aux_mode = o.aux_mode;
   X->stats.timing = o.collect_stats != 0;
@@ -1964,6 +2034,7 @@ psp_status psp_setup(const psp_grid* g, const double* c, double omega, int pml_g
   init_problem(X, g, omega, pml_gamma, panel_depth, o);
   *out = X;
   PSP_TRY
+  AllocScope scope(&X->allocator);
   PSP_CK(cudaGetDevice(&X->device));
   setup_impl(X, c, (cudaStream_t)stream);
   return PSP_OK;
@@ -2001,6 +2072,7 @@ psp_status psp_setup_batch(int nprob, const psp_grid* grids, const double* const
   init_problem(B, grids, omega[0], pml_gamma[0], panel_depth[0], o);
   *out = B;
   PSP_TRY
+  AllocScope scope(&B->allocator);
   PSP_CK(cudaGetDevice(&B->device));
   setup_batch_impl(B, nprob, c, (cudaStream_t)stream);
   return PSP_OK;
@@ -2022,6 +2094,7 @@ psp_status psp_apply(psp_handle X, const double* rhs, double* out, int nrhs, voi
   if (X->partial) return fail(PSP_ERR_STATE, kPartialMsg);
   PSP_TRY
   check_device(X);
+  AllocScope scope(&X->allocator);
   cudaStream_t st = (cudaStream_t)stream;
   const size_t bytes = (size_t)X->N * nrhs * sizeof(double2);
   const bool dev_out = is_device_pointer(out);
@@ -2048,6 +2121,7 @@ psp_status psp_matvec(psp_handle X, int which, const double* x, double* y, int n
   if (!X || !x || !y || nrhs < 1 || (which != 0 && which != 1)) return fail(PSP_ERR_ARG, "bad matvec arguments");
   PSP_TRY
   check_device(X);
+  AllocScope scope(&X->allocator);
   cudaStream_t st = (cudaStream_t)stream;
   const size_t bytes = (size_t)X->N * nrhs * sizeof(double2);
   const double2* xd = reinterpret_cast<const double2*>(x);
@@ -2084,6 +2158,7 @@ psp_status psp_solve(psp_handle X, const double* f, double* u, int nrhs, double 
   if (X->partial) return fail(PSP_ERR_STATE, kPartialMsg);
   PSP_TRY
   check_device(X);
+  AllocScope scope(&X->allocator);
   cudaStream_t st = (cudaStream_t)stream;
   const size_t bytes = (size_t)X->N * nrhs * sizeof(double2);
   const double2* fd = reinterpret_cast<const double2*>(f);
@@ -2133,15 +2208,33 @@ psp_status psp_solve(psp_handle X, const double* f, double* u, int nrhs, double 
   psp_solve_info agg{};
   agg.converged = 1;
   agg.status_front = -1;
+  agg.min_pivot_abs = X->min_pivot_abs;
+  const int ncols = nrhs * (int)X->probs.size();
+  for (int kind = 0; kind < 2; ++kind) X->hist[kind].clear();
+  X->hist_cols = ncols;
+  X->has_history = true;
+  // a group's history rows go into its columns; a column that stopped repeats its last value
+  auto merge = [&](std::vector<std::vector<double>>& dst, const std::vector<std::vector<double>>& src, int c0, int nc) {
+    for (size_t r = 0; r < src.size(); ++r) {
+      if (dst.size() <= r) dst.push_back(dst.empty() ? std::vector<double>(ncols, 1.0) : dst.back());
+      for (int c = 0; c < nc; ++c) dst[r][c0 + c] = src[r][c];
+    }
+    for (size_t r = src.size(); r < dst.size() && !src.empty(); ++r)
+      for (int c = 0; c < nc; ++c) dst[r][c0 + c] = src.back()[c];
+  };
   for (int r0 = 0; r0 < nrhs; r0 += group) {
     const int ng = std::min(group, nrhs - r0);
     psp_solve_info gi{};
+    std::vector<std::vector<double>> he, ht;
     try {
-      solve_impl(X, fd + (int64_t)r0 * X->N, ud + (int64_t)r0 * X->N, ng, tol, k, maxit, &gi, st, store_z);
+      solve_impl(X, fd + (int64_t)r0 * X->N, ud + (int64_t)r0 * X->N, ng, tol, k, maxit, &gi, st, store_z, &he, &ht);
     } catch (const Error& e) {
       if (e.st != PSP_ERR_NOT_CONVERGED) throw;
       rs = fail(e.st, e.msg);
     }
+    // columns of this run: one per right-hand side (single-problem handles run in groups)
+    merge(X->hist[0], he, r0, (int)(he.empty() ? ng : he[0].size()));
+    merge(X->hist[1], ht, r0, (int)(ht.empty() ? ng : ht[0].size()));
     agg.iterations = std::max(agg.iterations, gi.iterations);
     agg.restarts = std::max(agg.restarts, gi.restarts);
     agg.converged = agg.converged && gi.converged;
@@ -2157,6 +2250,19 @@ psp_status psp_solve(psp_handle X, const double* f, double* u, int nrhs, double 
   }
   return rs;
   PSP_CATCH
+}
+
+psp_status psp_solve_history(psp_handle X, int kind, double* buf, int capacity, int* rows, int* cols) {
+  if (!X || (kind != 0 && kind != 1) || capacity < 0) return fail(PSP_ERR_ARG, "bad history arguments");
+  if (!X->has_history) return fail(PSP_ERR_STATE, "no solve has run on this handle");
+  const auto& H = X->hist[kind];
+  if (rows) *rows = (int)H.size();
+  if (cols) *cols = X->hist_cols;
+  if (!buf) return PSP_OK;
+  if ((int64_t)capacity < (int64_t)H.size() * X->hist_cols) return fail(PSP_ERR_ARG, "history buffer too small");
+  for (size_t r = 0; r < H.size(); ++r)
+    std::memcpy(buf + r * X->hist_cols, H[r].data(), X->hist_cols * sizeof(double));
+  return PSP_OK;
 }
 
 psp_status psp_symbolic_export(psp_handle X, int panel, int32_t* buf, size_t* len) {
@@ -2246,6 +2352,7 @@ psp_status psp_tune_sweep(psp_handle X, int nrhs, int reps, void* stream, psp_sw
   if (!X->d_factor.p) return fail(PSP_ERR_STATE, "handle has no factorisation");
   PSP_TRY
   check_device(X);
+  AllocScope scope(&X->allocator);
   cudaStream_t st = (cudaStream_t)stream;
   DevBuf u;
   const size_t bytes = (size_t)X->N * nrhs * sizeof(double2);
@@ -2327,6 +2434,7 @@ psp_status psp_sweep_part(psp_handle X, double* u, int nrhs, int direction, void
   if (X->probs.size() != 1) return fail(PSP_ERR_STATE, "psp_sweep_part takes single-problem handles");
   PSP_TRY
   check_device(X);
+  AllocScope scope(&X->allocator);
   cudaStream_t st = (cudaStream_t)stream;
   const size_t bytes = (size_t)X->N * nrhs * sizeof(double2);
   const bool dev = is_device_pointer(u);

@@ -36,7 +36,13 @@ class Options(ctypes.Structure):
                 ("sweep_level_tasks", ctypes.c_int), ("sweep_ctas_per_sm", ctypes.c_int),
                 ("setup_temp_mb", ctypes.c_int), ("sweep_rhs_group", ctypes.c_int),
                 ("solve_rhs_group", ctypes.c_int), ("test_sweep_stall", ctypes.c_int), ("gmres_basis", ctypes.c_int),
-                ("factor_every_panel", ctypes.c_int), ("panel_begin", ctypes.c_int), ("panel_count", ctypes.c_int)]
+                ("factor_every_panel", ctypes.c_int), ("panel_begin", ctypes.c_int), ("panel_count", ctypes.c_int),
+                ("dev_alloc", ctypes.c_void_p), ("dev_free", ctypes.c_void_p), ("alloc_ctx", ctypes.c_void_p)]
+
+
+# psp_options.dev_alloc / dev_free callback types
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
 
 class KernelStat(ctypes.Structure):
@@ -47,7 +53,8 @@ class KernelStat(ctypes.Structure):
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int), ("converged", ctypes.c_int),
                 ("applies", ctypes.c_int), ("relres_max", ctypes.c_double), ("solve_ms", ctypes.c_double),
-                ("status_front", ctypes.c_int), ("groups", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+                ("status_front", ctypes.c_int), ("groups", ctypes.c_int), ("min_pivot_abs", ctypes.c_double),
+                ("reserved", ctypes.c_int * 4)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -106,6 +113,7 @@ def lib():
         "psp_tune_sweep": (_I, [_P, _I, _I, _P, ctypes.POINTER(SweepTuning)]),
         "psp_check_status": (_I, [_P, _P]),
         "psp_sweep_part": (_I, [_P, _P, _I, _I, _P]),
+        "psp_solve_history": (_I, [_P, _I, ctypes.POINTER(ctypes.c_double), _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
         "psp_plan_panels": (_I, [ctypes.POINTER(Grid), _I, _I, ctypes.POINTER(Options), ctypes.POINTER(_I),
                                  ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double), _I, ctypes.POINTER(_I)]),
         "psp_destroy": (_I, [_P]),
@@ -161,7 +169,7 @@ class SweepingPreconditioner:
                  precision="c128", faces=63, mode="moving", stream=None, collect_stats=0, tensor_cores=True,
                  tc_min_dim=0, sweep_level_tasks=0, sweep_ctas_per_sm=0, setup_temp_mb=0, sweep_rhs_group=0,
                  solve_rhs_group=0, test_sweep_stall=0, gmres_basis="auto", factor_every_panel=False,
-                 panels=None):
+                 panels=None, allocator=None):
         nz, ny, nx = c.shape
         self.nx, self.ny, self.nz = nx, ny, nz
         self.N = nx * ny * nz
@@ -174,6 +182,10 @@ class SweepingPreconditioner:
         o.factor_every_panel = 1 if factor_every_panel else 0
         if panels is not None:                   # (first, count): one block of a multi-GPU sweep
             o.panel_begin, o.panel_count = int(panels[0]), int(panels[1])
+        if allocator is not None:                # (alloc(bytes) -> int, free(int)): the caller owns device memory
+            self._alloc_cbs = _allocator_callbacks(*allocator)
+            o.dev_alloc = ctypes.cast(self._alloc_cbs[0], ctypes.c_void_p)
+            o.dev_free = ctypes.cast(self._alloc_cbs[1], ctypes.c_void_p)
         cp, n = _ptr_and_len(c, complex_=False)
         if n != self.N:
             raise ValueError("c has the wrong size")
@@ -227,6 +239,15 @@ class SweepingPreconditioner:
         if st != 0 and (raise_on_nonconvergence or st != 5):
             _check(st)
         return info.as_dict()
+
+    def solve_history(self, kind=0):
+        """psp_solve_history: (rows, cols) array of the last solve's residuals; kind 0 per iteration (Arnoldi
+        estimate), kind 1 per restart cycle (true residual)."""
+        r, c = _I(), _I()
+        _check(lib().psp_solve_history(self._h, int(kind), None, 0, ctypes.byref(r), ctypes.byref(c)))
+        buf = (ctypes.c_double * max(r.value * c.value, 1))()
+        _check(lib().psp_solve_history(self._h, int(kind), buf, r.value * c.value, ctypes.byref(r), ctypes.byref(c)))
+        return np.frombuffer(buf, dtype=np.float64)[:r.value * c.value].reshape(r.value, c.value).copy()
 
     def sweep_part(self, u, direction, stream=None):
         """psp_sweep_part: the forward (0) or backward (1) half of Alg. 1.5 over this handle's block, in place."""
@@ -341,6 +362,21 @@ class SweepingPreconditionerBatch(SweepingPreconditioner):
     def unpack(self, flat, nrhs):
         """Flat batched block -> [(nrhs, N_q) views]."""
         return [flat[o:o + n * nrhs].reshape(nrhs, n) for o, n in zip(self.offsets(nrhs), self.points)]
+
+
+def _allocator_callbacks(alloc, free):
+    """ctypes callbacks for psp_options.dev_alloc / dev_free around Python callables (kept alive by
+    the handle).  alloc(bytes) returns a device address (int) or 0; free(address) releases it."""
+    def a(nbytes, _ctx):
+        try:
+            return int(alloc(int(nbytes)) or 0)
+        except Exception:
+            return 0
+
+    def f(ptr, _ctx):
+        free(int(ptr))
+
+    return ALLOC_FN(a), FREE_FN(f)
 
 
 def _options(pad, leaf, pml_C, alpha, precision, faces, mode, collect_stats, tensor_cores, tc_min_dim,

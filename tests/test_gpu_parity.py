@@ -274,6 +274,65 @@ def test_gmres_v_only_basis_matches_z_basis():
     assert np.linalg.norm(uv - uz) / np.linalg.norm(uz) < 1e-9
 
 
+def test_allocator_callbacks_own_every_device_allocation():
+    # the caller's allocator (here torch's caching allocator) receives every allocation of the handle;
+    # results are those of a handle using cudaMalloc, and a failing allocator gives PSP_ERR_OOM
+    case = CASES[2]
+    live, calls = {}, [0]
+
+    def alloc(n):
+        p = torch.cuda.caching_allocator_alloc(n)
+        live[p] = n
+        calls[0] += 1
+        return p
+
+    def free(p):
+        torch.cuda.caching_allocator_delete(p)
+        del live[p]
+
+    c = torch.from_numpy(case.c).cuda()
+    kw = dict(pad=case.pad, leaf=case.leaf, pml_C=case.C, alpha=case.alpha, faces=case.faces)
+    P = psp.SweepingPreconditioner(c, case.h, case.omega, case.gamma, case.depth, allocator=(alloc, free), **kw)
+    Q = psp.SweepingPreconditioner(c, case.h, case.omega, case.gamma, case.depth, **kw)
+    assert sum(live.values()) >= P.info()["factor_bytes"] > 0
+    x = torch.from_numpy(wl.random_vector(case.N, 2, seed=4)).cuda()
+    a, b = torch.empty_like(x), torch.empty_like(x)
+    P.apply(x, a)
+    Q.apply(x, b)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    f = wl.gaussian_source(case.nx, case.ny, case.nz, case.h, (0.5, 0.5, 0.5))[None, :].copy()
+    u = np.zeros_like(f)
+    assert P.solve(f, u, tol=1e-6, k=10, maxit=200)["converged"] == 1
+    n_before = calls[0]
+    P.close()
+    Q.close()
+    assert not live and calls[0] == n_before
+    with pytest.raises(psp.PSPError) as e:
+        psp.SweepingPreconditioner(c, case.h, case.omega, case.gamma, case.depth, allocator=(lambda n: 0, free), **kw)
+    assert e.value.name == "PSP_ERR_OOM"
+
+
+def test_solve_history_and_pivot_monitor():
+    case = CASES[1]
+    O = oracle_for(case)
+    dmin = min(float(np.min(np.abs(fr.d))) for fronts in O.fronts.values() for fr in fronts)
+    P = gpu_for(case)
+    f = np.stack([wl.gaussian_source(case.nx, case.ny, case.nz, case.h, s) for s in ((0.5, 0.5, 0.5), (0.2, 0.7, 0.3))])
+    u = np.zeros_like(f)
+    info = P.solve(f, u, tol=1e-8, k=5, maxit=300)
+    assert abs(info["min_pivot_abs"] - dmin) <= 1e-12 * dmin
+    est, true = P.solve_history(0), P.solve_history(1)
+    assert est.shape == (info["iterations"], 2) and true.shape == (info["restarts"], 2)
+    assert np.all(est[-1] < 1e-8) and np.all(est > 0)
+    assert np.max(true[-1]) == pytest.approx(info["relres_max"], rel=1e-12)
+    # within a restart cycle the GMRES residual estimate does not increase
+    for c0 in range(0, info["iterations"], 5):
+        cyc = est[c0:c0 + 5]
+        assert np.all(np.diff(cyc, axis=0) <= 1e-12 * cyc[:-1])
+    P.close()
+
+
 def test_sweep_wait_gives_up_and_the_device_stays_usable():
     # a dependency of the persistent sweep that can never be met (test option): its bounded wait
     # gives up after about two seconds, psp_solve reports PSP_ERR_TIMEOUT, and a normal handle
