@@ -70,6 +70,17 @@ typedef enum {
   PSP_PREC_C64 = 1    /* fronts and sweeps in complex64; GMRES and matvec stay complex128 */
 } psp_precision;
 
+/* What the factor of each front keeps (§2.2): after the partial LDL^T of the front
+   F = [F_TL F_BL^T; F_BL F_BR], L_TL D L_TL^T = F_TL and L_BL = F_BL L_TL^{-T} D^{-1}. */
+typedef enum {
+  PSP_SI_EXTENDED = 0, /* G = [inv(L_TL); L_BL inv(L_TL)]: selective inversion extended to the bottom block, so
+                          each front is one matrix-vector product per sweep direction (default) */
+  PSP_SI_PAPER = 1,    /* G = [inv(L_TL); L_BL]: the paper's selective inversion; each front takes two dependent
+                          products per direction, and setup skips the u s^2 / 2 products of L_BL inv(L_TL) */
+  PSP_SI_NONE = 2      /* G = [L_TL; L_BL]: no inversion; the sweep solves with L_TL by substitution, one CTA
+                          per front (complex64 fronts stay on CUDA cores) */
+} psp_si_mode;
+
 typedef enum {
   PSP_AUX_MOVING_PML = 0, /* H_i = PML pad + panel (Alg. 1.4): the preconditioner */
   PSP_AUX_EXACT = 1       /* H_i = all planes below the panel's top (Fig. 2 middle): M = J exactly */
@@ -127,6 +138,7 @@ typedef struct {
   void* (*dev_alloc)(size_t bytes, void* ctx);
   void (*dev_free)(void* ptr, void* ctx);
   void* alloc_ctx;
+  int selective_inversion; /* psp_si_mode, default PSP_SI_EXTENDED */
 } psp_options;
 
 /* Per-solve report filled by psp_solve (host struct). */
@@ -277,8 +289,9 @@ psp_status psp_info(psp_handle h, int* panels, int64_t* fronts, int64_t* factor_
 
 /*
  * psp_export_front - copy the factor of one front (panel, supernode) to host memory:
- * the (s+u) x s column-major block G = [inv(L_TL) with D on its diagonal; L_BL inv(L_TL)]
- * after selective inversion, as complex128 (converted if the handle is complex64).
+ * the (s+u) x s column-major block G the handle keeps (psp_si_mode, D on the top block's
+ * diagonal): [inv(L_TL); L_BL inv(L_TL)], [inv(L_TL); L_BL] or [L_TL; L_BL], as complex128
+ * (converted if the handle is complex64).
  * Call with buf = NULL to get s and u.
  */
 psp_status psp_export_front(psp_handle h, int panel, int supernode, double* buf, int* s, int* u);

@@ -292,7 +292,8 @@ __global__ void __launch_bounds__(256) k_copy_linv(const FrontTask<T>* __restric
 }
 
 // ZD = Z D^{-1}, column by column, once per front: the Schur update and the M_BL product then
-// read plain operands in every tile instead of dividing each element by its pivot again
+// read plain operands in every tile instead of dividing each element by its pivot again.  When the
+// factor keeps L_BL = F_BL L^{-T} D^{-1} itself, ZD is G's bottom block (ldzd = s + u)
 template <typename T>
 __global__ void __launch_bounds__(256) k_scale_zd(const FrontTask<T>* __restrict__ fronts,
                                                   const ColTask* __restrict__ tasks) {
@@ -302,7 +303,7 @@ __global__ void __launch_bounds__(256) k_scale_zd(const FrontTask<T>* __restrict
   for (int c = tk.c0; c < tk.c1; ++c) {
     const T dinv = cdiv(CplxTraits<T>::one(), ft.G[(int64_t)c * (ld + 1)]);
     const T* z = ft.Z + (int64_t)c * ft.u;
-    T* zd = ft.ZD + (int64_t)c * ft.u;
+    T* zd = ft.ZD + (int64_t)c * ft.ldzd;
     for (int r = threadIdx.x; r < ft.u; r += blockDim.x) zd[r] = cmul(z[r], dinv);
   }
 }

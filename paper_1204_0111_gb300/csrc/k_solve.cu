@@ -56,10 +56,14 @@ __device__ __forceinline__ void pull_add(const SolveCtx<T>& cx, const int32_t* p
   }
 }
 
-// up-the-tree task: rows [r0, r1) of front sn, right-hand sides [rhs0, rhs0 + RG)
+// up-the-tree task: rows [r0, r1) of front sn, right-hand sides [rhs0, rhs0 + RG).
+// phase 0 gathers w_S (zero-extended input + children's updates) and, for rows r < s, writes
+// x_r = D^{-1} y_r with y_S = inv(L_TL) w_S (and y_r itself into xb when the second phase needs it);
+// for rows r >= s it writes the update w_U - M_BL w_S (extended selective inversion).
+// phase 1 (factors keeping L_BL) takes y_S from xb and writes the update w_U - L_BL y_S of rows r >= s.
 template <typename T, int RG>
 __device__ __forceinline__ void fwd_task(const SolveTask tk, const int rhs0, const SolveCtx<T>& cx, const int R,
-                                         unsigned char* smem_raw) {
+                                         unsigned char* smem_raw, const int phase) {
   const int sn = tk.sn;
   const int s = cx.sh.s[sn], u = cx.sh.u[sn], ld = s + u;
   const int first = cx.sh.first[sn];
@@ -68,15 +72,23 @@ __device__ __forceinline__ void fwd_task(const SolveTask tk, const int rhs0, con
   T* w = reinterpret_cast<T*>(smem_raw);        // s x RG
   T* red = w + (int64_t)s * RG;                  // blockDim x RG
 
-  // w_S = (zero-extended input) + children's updates
-  for (int p = threadIdx.x; p < s; p += blockDim.x) {
-    const int node = cx.sh.order[first + p];
-    T v[RG];
+  if (phase == 0) {
+    // w_S = (zero-extended input) + children's updates
+    for (int p = threadIdx.x; p < s; p += blockDim.x) {
+      const int node = cx.sh.order[first + p];
+      T v[RG];
 #pragma unroll
-    for (int q = 0; q < RG; ++q) v[q] = (rhs0 + q < cx.nrhs) ? input_value(cx, node, rhs0 + q) : CplxTraits<T>::zero();
-    pull_add<T, RG>(cx, pull + 2 * p, rhs0, v);
+      for (int q = 0; q < RG; ++q) v[q] = (rhs0 + q < cx.nrhs) ? input_value(cx, node, rhs0 + q) : CplxTraits<T>::zero();
+      pull_add<T, RG>(cx, pull + 2 * p, rhs0, v);
 #pragma unroll
-    for (int q = 0; q < RG; ++q) w[p * RG + q] = v[q];
+      for (int q = 0; q < RG; ++q) w[p * RG + q] = v[q];
+    }
+  } else {
+    for (int p = threadIdx.x; p < s; p += blockDim.x)
+#pragma unroll
+      for (int q = 0; q < RG; ++q)
+        w[p * RG + q] = (rhs0 + q < cx.nrhs) ? __ldcg(cx.xb + (int64_t)(rhs0 + q) * cx.n_loc + first + p)
+                                             : CplxTraits<T>::zero();
   }
   __syncthreads();
 
@@ -86,7 +98,7 @@ __device__ __forceinline__ void fwd_task(const SolveTask tk, const int rhs0, con
 #pragma unroll
   for (int q = 0; q < RG; ++q) acc[q] = CplxTraits<T>::zero();
   if (r < tk.r1) {
-    const int jmax = r < s ? r : s;   // strictly lower part of inv(L_TL), all of M_BL
+    const int jmax = r < s ? r : s;   // strictly lower part of inv(L_TL), all of the bottom block
     const T* Gr = G + r;
     const int64_t step = (int64_t)ngrp * ld;
     int j = grp;
@@ -117,8 +129,12 @@ __device__ __forceinline__ void fwd_task(const SolveTask tk, const int rhs0, con
       const T dinv = cdiv(CplxTraits<T>::one(), G[(int64_t)r * ld + r]);
 #pragma unroll
       for (int q = 0; q < RG; ++q)
-        if (rhs0 + q < cx.nrhs)
-          cx.xf[(int64_t)(rhs0 + q) * cx.n_loc + first + r] = cmul(cadd(acc[q], w[r * RG + q]), dinv);
+        if (rhs0 + q < cx.nrhs) {
+          const T y = cadd(acc[q], w[r * RG + q]);
+          const int64_t o = (int64_t)(rhs0 + q) * cx.n_loc + first + r;
+          cx.xf[o] = cmul(y, dinv);
+          if (cx.si != PSP_SI_EXTENDED) cx.xb[o] = y;
+        }
     } else {
       T wu[RG];
 #pragma unroll
@@ -132,24 +148,117 @@ __device__ __forceinline__ void fwd_task(const SolveTask tk, const int rhs0, con
   }
 }
 
+// Without inversion (G keeps L_TL): the first phase up the tree of front sn by one CTA: w_S gathered
+// as above, then forward substitution y_S = L_TL^{-1} w_S in blocks of 32 columns (one warp solves
+// the diagonal block, all threads update the rows below it), x_S = D^{-1} y_S into xf, y_S into xb.
 template <typename T, int RG>
-__global__ void __launch_bounds__(256) k_solve_fwd(const SolveTask* __restrict__ tasks, SolveCtx<T> cx, int R) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  fwd_task<T, RG>(tasks[blockIdx.x], blockIdx.y * RG, cx, R, smem_raw);
+__device__ __forceinline__ void fwd_tri_task(const SolveTask tk, const int rhs0, const SolveCtx<T>& cx,
+                                             unsigned char* smem_raw) {
+  const int sn = tk.sn;
+  const int s = cx.sh.s[sn], ld = s + cx.sh.u[sn];
+  const int first = cx.sh.first[sn];
+  const T* G = cx.G + cx.sh.g_off[sn];
+  const int32_t* pull = cx.sh.pull + 2 * cx.sh.pull_ptr[sn];
+  T* w = reinterpret_cast<T*>(smem_raw);        // s x RG
+  for (int p = threadIdx.x; p < s; p += blockDim.x) {
+    const int node = cx.sh.order[first + p];
+    T v[RG];
+#pragma unroll
+    for (int q = 0; q < RG; ++q) v[q] = (rhs0 + q < cx.nrhs) ? input_value(cx, node, rhs0 + q) : CplxTraits<T>::zero();
+    pull_add<T, RG>(cx, pull + 2 * p, rhs0, v);
+#pragma unroll
+    for (int q = 0; q < RG; ++q) w[p * RG + q] = v[q];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int b = 0; b < s; b += 32) {
+    const int be = min(b + 32, s);
+    if (warp == 0) {
+      // diagonal block: y_j final, then w_k -= L[k, j] y_j for b <= j < k < be
+      for (int j = b; j < be; ++j) {
+        const int k = b + lane;
+        const T l = (k > j && k < be) ? __ldg(G + (int64_t)j * ld + k) : CplxTraits<T>::zero();
+        __syncwarp();
+        if (k > j && k < be)
+#pragma unroll
+          for (int q = 0; q < RG; ++q) cfms(w[k * RG + q], l, w[j * RG + q]);
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    // rows below the block: w_i -= sum_{j in block} L[i, j] y_j
+    for (int i = be + threadIdx.x; i < s; i += blockDim.x) {
+      T acc[RG];
+#pragma unroll
+      for (int q = 0; q < RG; ++q) acc[q] = CplxTraits<T>::zero();
+      for (int j = b; j < be; ++j) {
+        const T l = __ldg(G + (int64_t)j * ld + i);
+#pragma unroll
+        for (int q = 0; q < RG; ++q) cfma(acc[q], l, w[j * RG + q]);
+      }
+#pragma unroll
+      for (int q = 0; q < RG; ++q) w[i * RG + q] = csub(w[i * RG + q], acc[q]);
+    }
+    __syncthreads();
+  }
+  for (int r = threadIdx.x; r < s; r += blockDim.x) {
+    const T dinv = cdiv(CplxTraits<T>::one(), G[(int64_t)r * ld + r]);
+#pragma unroll
+    for (int q = 0; q < RG; ++q)
+      if (rhs0 + q < cx.nrhs) {
+        const int64_t o = (int64_t)(rhs0 + q) * cx.n_loc + first + r;
+        cx.xb[o] = w[r * RG + q];
+        cx.xf[o] = cmul(w[r * RG + q], dinv);
+      }
+  }
 }
 
-// down-the-tree task: columns [r0, r1) of S of front sn
+template <typename T, int RG>
+__global__ void __launch_bounds__(256) k_solve_fwd(const SolveTask* __restrict__ tasks, SolveCtx<T> cx, int R,
+                                                   int phase) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (phase == 0 && cx.si == PSP_SI_NONE) fwd_tri_task<T, RG>(tasks[blockIdx.x], blockIdx.y * RG, cx, smem_raw);
+  else fwd_task<T, RG>(tasks[blockIdx.x], blockIdx.y * RG, cx, R, smem_raw, phase);
+}
+
+// the final write of x_S column c of a front: xb (elimination order) and, for the panel's own
+// planes, the global vector (Alg. 1.3 extraction; assigned in the forward sweep, subtracted in the
+// backward sweep)
+template <typename T>
+__device__ __forceinline__ void write_solution(const SolveCtx<T>& cx, const int first, const int c, const int q,
+                                               const T out) {
+  cx.xb[(int64_t)q * cx.n_loc + first + c] = out;
+  const int node = cx.sh.order[first + c];
+  const int nx = cx.sh.nx, ny = cx.sh.ny;
+  const int k = node / (nx * ny);
+  if (k >= cx.lead) {
+    const int64_t g = (node % (nx * ny)) + (int64_t)nx * ny * (cx.z0 + k - cx.lead);
+    double2* uq = cx.u + (int64_t)q * cx.N + g;
+    const double2 o = to_c128(out);
+    *uq = (cx.mode == 0) ? o : csub(__ldcg(uq), o);
+  }
+}
+
+// down-the-tree task: columns [r0, r1) of S of front sn.
+//   extended factors (phase 0): x_c = xf_c + sum_{r > c} G[r, c] y_r over all s + u rows, with
+//     y = xf on S and -x_U on the struct rows; writes the solution.
+//   factors keeping L_BL, phase 0: t_c = xf_c - sum_{r >= s} L_BL[r, c] x_U[r] into xf.
+//   paper's factors, phase 1: x_c = t_c + sum_{c < r < s} inv(L_TL)[r, c] t_r; writes the solution.
 template <typename T, int RG>
 __device__ __forceinline__ void bwd_task(const SolveTask tk, const int rhs0, const SolveCtx<T>& cx,
-                                         unsigned char* smem_raw) {
+                                         unsigned char* smem_raw, const int phase) {
   const int sn = tk.sn;
   const int s = cx.sh.s[sn], u = cx.sh.u[sn], ld = s + u;
   const int first = cx.sh.first[sn];
   const T* G = cx.G + cx.sh.g_off[sn];
   const int32_t* sel = cx.sh.struct_elim + cx.sh.struct_ptr[sn];
   const int c0 = tk.r0;
-  T* y = reinterpret_cast<T*>(smem_raw);   // rows [c0, s+u) x RG
-  for (int r = c0 + threadIdx.x; r < ld; r += blockDim.x) {
+  const bool ext = cx.si == PSP_SI_EXTENDED;
+  // rows of the inner sums kept in shared memory: [lo, hi)
+  const int lo = (ext || phase == 1) ? c0 : s;
+  const int hi = (ext || phase == 0) ? ld : s;
+  T* y = reinterpret_cast<T*>(smem_raw);   // rows [lo, hi) x RG
+  for (int r = lo + threadIdx.x; r < hi; r += blockDim.x) {
 #pragma unroll
     for (int q = 0; q < RG; ++q) {
       T v = CplxTraits<T>::zero();
@@ -157,7 +266,7 @@ __device__ __forceinline__ void bwd_task(const SolveTask tk, const int rhs0, con
         const int64_t base = (int64_t)(rhs0 + q) * cx.n_loc;
         v = (r < s) ? __ldcg(cx.xf + base + first + r) : cneg(__ldcg(cx.xb + base + sel[r - s]));
       }
-      y[(r - c0) * RG + q] = v;
+      y[(r - lo) * RG + q] = v;
     }
   }
   __syncthreads();
@@ -167,20 +276,20 @@ __device__ __forceinline__ void bwd_task(const SolveTask tk, const int rhs0, con
 #pragma unroll
     for (int q = 0; q < RG; ++q) acc[q] = CplxTraits<T>::zero();
     const T* Gc = G + (int64_t)c * ld;
-    int r = c + 1 + lane;
-    for (; r + 7 * 32 < ld; r += 8 * 32) {   // eight independent factor loads in flight per lane
+    int r = (lo > c + 1 ? lo : c + 1) + lane;
+    for (; r + 7 * 32 < hi; r += 8 * 32) {   // eight independent factor loads in flight per lane
       T gv[8];
 #pragma unroll
       for (int t = 0; t < 8; ++t) gv[t] = __ldg(Gc + r + 32 * t);
 #pragma unroll
       for (int t = 0; t < 8; ++t)
 #pragma unroll
-        for (int q = 0; q < RG; ++q) cfma(acc[q], gv[t], y[(r + 32 * t - c0) * RG + q]);
+        for (int q = 0; q < RG; ++q) cfma(acc[q], gv[t], y[(r + 32 * t - lo) * RG + q]);
     }
-    for (; r < ld; r += 32) {
+    for (; r < hi; r += 32) {
       const T gv = __ldg(Gc + r);
 #pragma unroll
-      for (int q = 0; q < RG; ++q) cfma(acc[q], gv, y[(r - c0) * RG + q]);
+      for (int q = 0; q < RG; ++q) cfma(acc[q], gv, y[(r - lo) * RG + q]);
     }
 #pragma unroll
     for (int q = 0; q < RG; ++q) {
@@ -190,29 +299,86 @@ __device__ __forceinline__ void bwd_task(const SolveTask tk, const int rhs0, con
       }
     }
     if (lane == 0) {
-      const int node = cx.sh.order[first + c];
-      const int nx = cx.sh.nx, ny = cx.sh.ny;
-      const int k = node / (nx * ny);
-      const int64_t g = (node % (nx * ny)) + (int64_t)nx * ny * (cx.z0 + k - cx.lead);
 #pragma unroll
       for (int q = 0; q < RG; ++q) {
         if (rhs0 + q >= cx.nrhs) continue;
-        const T out = cadd(acc[q], y[(c - c0) * RG + q]);
-        cx.xb[(int64_t)(rhs0 + q) * cx.n_loc + first + c] = out;
-        if (k >= cx.lead) {   // the panel's own planes (Alg. 1.3 extraction)
-          double2* uq = cx.u + (int64_t)(rhs0 + q) * cx.N + g;
-          const double2 o = to_c128(out);
-          *uq = (cx.mode == 0) ? o : csub(__ldcg(uq), o);
+        const int64_t o = (int64_t)(rhs0 + q) * cx.n_loc + first + c;
+        if (!ext && phase == 0) {
+          cx.xf[o] = cadd(acc[q], __ldcg(cx.xf + o));   // t_c, read and written by this lane only
+        } else {
+          write_solution(cx, first, c, rhs0 + q, cadd(acc[q], y[(c - lo) * RG + q]));
         }
       }
     }
   }
 }
 
+// Without inversion: the second phase down the tree of front sn by one CTA: back substitution
+// L_TL^T x_S = t (t in xf) in blocks of 32 columns from the last, each block first takes the
+// products with the solved rows below it (one warp per column), then one warp solves the block.
 template <typename T, int RG>
-__global__ void __launch_bounds__(256) k_solve_bwd(const SolveTask* __restrict__ tasks, SolveCtx<T> cx) {
+__device__ __forceinline__ void bwd_tri_task(const SolveTask tk, const int rhs0, const SolveCtx<T>& cx,
+                                             unsigned char* smem_raw) {
+  const int sn = tk.sn;
+  const int s = cx.sh.s[sn], ld = s + cx.sh.u[sn];
+  const int first = cx.sh.first[sn];
+  const T* G = cx.G + cx.sh.g_off[sn];
+  T* x = reinterpret_cast<T*>(smem_raw);   // s x RG: t, overwritten by x block by block
+  for (int r = threadIdx.x; r < s; r += blockDim.x)
+#pragma unroll
+    for (int q = 0; q < RG; ++q)
+      x[r * RG + q] = (rhs0 + q < cx.nrhs) ? __ldcg(cx.xf + (int64_t)(rhs0 + q) * cx.n_loc + first + r)
+                                           : CplxTraits<T>::zero();
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nblk = (s + 31) / 32;
+  for (int bi = nblk - 1; bi >= 0; --bi) {
+    const int b = bi * 32, be = min(b + 32, s);
+    // x_c -= sum_{r >= be} L[r, c] x_r for the block's columns
+    for (int c = b + warp; c < be; c += nw) {
+      T acc[RG];
+#pragma unroll
+      for (int q = 0; q < RG; ++q) acc[q] = CplxTraits<T>::zero();
+      for (int r = be + lane; r < s; r += 32) {
+        const T l = __ldg(G + (int64_t)c * ld + r);
+#pragma unroll
+        for (int q = 0; q < RG; ++q) cfma(acc[q], l, x[r * RG + q]);
+      }
+#pragma unroll
+      for (int q = 0; q < RG; ++q) {
+        for (int off = 16; off > 0; off >>= 1) {
+          acc[q].x += __shfl_xor_sync(0xffffffffu, acc[q].x, off);
+          acc[q].y += __shfl_xor_sync(0xffffffffu, acc[q].y, off);
+        }
+        if (lane == 0) x[c * RG + q] = csub(x[c * RG + q], acc[q]);
+      }
+    }
+    __syncthreads();
+    if (warp == 0) {
+      // the block, from its last column: x_c final, then x_k -= L[c, k] x_c for b <= k < c
+      for (int c = be - 1; c >= b; --c) {
+        const int k = b + lane;
+        const T l = (k < c) ? __ldg(G + (int64_t)k * ld + c) : CplxTraits<T>::zero();
+        __syncwarp();
+        if (k < c)
+#pragma unroll
+          for (int q = 0; q < RG; ++q) cfms(x[k * RG + q], l, x[c * RG + q]);
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+  }
+  for (int c = threadIdx.x; c < s; c += blockDim.x)
+#pragma unroll
+    for (int q = 0; q < RG; ++q)
+      if (rhs0 + q < cx.nrhs) write_solution(cx, first, c, rhs0 + q, x[c * RG + q]);
+}
+
+template <typename T, int RG>
+__global__ void __launch_bounds__(256) k_solve_bwd(const SolveTask* __restrict__ tasks, SolveCtx<T> cx, int phase) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  bwd_task<T, RG>(tasks[blockIdx.x], blockIdx.y * RG, cx, smem_raw);
+  if (phase == 1 && cx.si == PSP_SI_NONE) bwd_tri_task<T, RG>(tasks[blockIdx.x], blockIdx.y * RG, cx, smem_raw);
+  else bwd_task<T, RG>(tasks[blockIdx.x], blockIdx.y * RG, cx, smem_raw, phase);
 }
 
 // rhs group size so that the shared-memory footprint stays below ~200 KB
@@ -263,7 +429,7 @@ __device__ __forceinline__ void prefetch_task(const SolveTask tk, const int dir,
   const int s = cx.sh.s[sn], ld = s + cx.sh.u[sn];
   const char* G = reinterpret_cast<const char*>(cx.G + cx.sh.g_off[sn]);
   constexpr int kLine = 128;
-  if (dir == 0) {
+  if (dir == 0 || dir == kDirUpB) {
     const int ncol = min(tk.r1, s);
     const int64_t seg = (int64_t)(tk.r1 - tk.r0) * sizeof(T);
     const int lines = (int)((seg + kLine - 1) / kLine) + 1;   // the segment may straddle one more line
@@ -377,6 +543,10 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs<T> a) {
           const int ch = cx.sh.child_idx[c];
           ok = wait_count(up + ch, (unsigned)a.ntask_up[c_fb + ch], a.status, a.sticky);
         }
+      } else if (ce.dir == kDirUpB) {   // the front's own first phase up
+        ok = wait_count(up + ctk.sn, (unsigned)a.ntask_upA[c_fb + ctk.sn], a.status, a.sticky);
+      } else if (ce.dir == kDirDownB) {   // the front's own first phase down
+        ok = wait_count(down + ctk.sn, (unsigned)a.ntask_downA[c_fb + ctk.sn], a.status, a.sticky);
       } else {
         const int par = cx.sh.parent[ctk.sn];
         ok = par >= 0 ? wait_count(down + par, (unsigned)a.ntask_down[c_fb + par], a.status, a.sticky)
@@ -389,15 +559,18 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs<T> a) {
     if (!s_ok) break;
     const SolveTask tk = s_tk;
     const int dir = s_dir;
+    const bool tri = s_cx.si == PSP_SI_NONE;
     for (int g = 0; g < nrg; ++g) {
-      if (dir == 0) fwd_task<T, RG>(tk, g * RG, s_cx, s_R, smem_raw);
-      else bwd_task<T, RG>(tk, g * RG, s_cx, smem_raw);
+      if (dir == 0 && tri) fwd_tri_task<T, RG>(tk, g * RG, s_cx, smem_raw);
+      else if (dir == 0 || dir == kDirUpB) fwd_task<T, RG>(tk, g * RG, s_cx, s_R, smem_raw, dir == 0 ? 0 : 1);
+      else if (dir == kDirDownB && tri) bwd_tri_task<T, RG>(tk, g * RG, s_cx, smem_raw);
+      else bwd_task<T, RG>(tk, g * RG, s_cx, smem_raw, dir == 1 ? 0 : 1);
       __syncthreads();
     }
     if (threadIdx.x == 0) {
       // completion counters of this task's step and front, then the next task's tables
       __threadfence();
-      atomicAdd((dir == 0 ? a.done_up : a.done_down) + c_sfb + tk.sn, 1u);
+      atomicAdd((dir == 0 || dir == kDirUpB ? a.done_up : a.done_down) + c_sfb + tk.sn, 1u);
       atomicAdd(a.step_done + ce.step, 1u);
       const int nx = s_next;
       if (nx < a.nqueue) fetch(nx);
@@ -450,7 +623,7 @@ int launch_sweep(const SweepArgs<T>& args, size_t per_rhs_bytes, int max_per_sm,
 }
 
 template <typename T, int RG>
-static void fwd_rg(const SolveTask* tasks, int ntasks, const SolveCtx<T>& cx, int R, int smax, cudaStream_t st) {
+static void fwd_rg(const SolveTask* tasks, int ntasks, const SolveCtx<T>& cx, int R, int smax, int phase, cudaStream_t st) {
   const size_t smem = ((size_t)smax + 256) * RG * sizeof(T);
   static bool attr_set = false;
   if (!attr_set) {
@@ -458,11 +631,11 @@ static void fwd_rg(const SolveTask* tasks, int ntasks, const SolveCtx<T>& cx, in
     attr_set = true;
   }
   dim3 grid(ntasks, (cx.nrhs + RG - 1) / RG);
-  k_solve_fwd<T, RG><<<grid, 256, smem, st>>>(tasks, cx, R);
+  k_solve_fwd<T, RG><<<grid, 256, smem, st>>>(tasks, cx, R, phase);
 }
 
 template <typename T, int RG>
-static void bwd_rg(const SolveTask* tasks, int ntasks, const SolveCtx<T>& cx, int ldmax, cudaStream_t st) {
+static void bwd_rg(const SolveTask* tasks, int ntasks, const SolveCtx<T>& cx, int ldmax, int phase, cudaStream_t st) {
   const size_t smem = (size_t)ldmax * RG * sizeof(T);
   static bool attr_set = false;
   if (!attr_set) {
@@ -470,37 +643,38 @@ static void bwd_rg(const SolveTask* tasks, int ntasks, const SolveCtx<T>& cx, in
     attr_set = true;
   }
   dim3 grid(ntasks, (cx.nrhs + RG - 1) / RG);
-  k_solve_bwd<T, RG><<<grid, 256, smem, st>>>(tasks, cx);
+  k_solve_bwd<T, RG><<<grid, 256, smem, st>>>(tasks, cx, phase);
 }
 
 template <typename T>
-void launch_solve_fwd(const SolveTask* tasks, int ntasks, const SolveCtx<T>& cx, int R, int smax, cudaStream_t st) {
+void launch_solve_fwd(const SolveTask* tasks, int ntasks, const SolveCtx<T>& cx, int R, int smax, int phase,
+                      cudaStream_t st) {
   if (ntasks <= 0) return;
   const int rg = pick_rg<T>(cx.nrhs, ((size_t)smax + 256) * sizeof(T));
   switch (rg) {
-    case 8: fwd_rg<T, 8>(tasks, ntasks, cx, R, smax, st); break;
-    case 4: fwd_rg<T, 4>(tasks, ntasks, cx, R, smax, st); break;
-    case 2: fwd_rg<T, 2>(tasks, ntasks, cx, R, smax, st); break;
-    default: fwd_rg<T, 1>(tasks, ntasks, cx, R, smax, st); break;
+    case 8: fwd_rg<T, 8>(tasks, ntasks, cx, R, smax, phase, st); break;
+    case 4: fwd_rg<T, 4>(tasks, ntasks, cx, R, smax, phase, st); break;
+    case 2: fwd_rg<T, 2>(tasks, ntasks, cx, R, smax, phase, st); break;
+    default: fwd_rg<T, 1>(tasks, ntasks, cx, R, smax, phase, st); break;
   }
 }
 
 template <typename T>
-void launch_solve_bwd(const SolveTask* tasks, int ntasks, const SolveCtx<T>& cx, int ldmax, cudaStream_t st) {
+void launch_solve_bwd(const SolveTask* tasks, int ntasks, const SolveCtx<T>& cx, int ldmax, int phase, cudaStream_t st) {
   if (ntasks <= 0) return;
   const int rg = pick_rg<T>(cx.nrhs, (size_t)ldmax * sizeof(T));
   switch (rg) {
-    case 8: bwd_rg<T, 8>(tasks, ntasks, cx, ldmax, st); break;
-    case 4: bwd_rg<T, 4>(tasks, ntasks, cx, ldmax, st); break;
-    case 2: bwd_rg<T, 2>(tasks, ntasks, cx, ldmax, st); break;
-    default: bwd_rg<T, 1>(tasks, ntasks, cx, ldmax, st); break;
+    case 8: bwd_rg<T, 8>(tasks, ntasks, cx, ldmax, phase, st); break;
+    case 4: bwd_rg<T, 4>(tasks, ntasks, cx, ldmax, phase, st); break;
+    case 2: bwd_rg<T, 2>(tasks, ntasks, cx, ldmax, phase, st); break;
+    default: bwd_rg<T, 1>(tasks, ntasks, cx, ldmax, phase, st); break;
   }
 }
 
-template void launch_solve_fwd<double2>(const SolveTask*, int, const SolveCtx<double2>&, int, int, cudaStream_t);
-template void launch_solve_fwd<float2>(const SolveTask*, int, const SolveCtx<float2>&, int, int, cudaStream_t);
-template void launch_solve_bwd<double2>(const SolveTask*, int, const SolveCtx<double2>&, int, cudaStream_t);
-template void launch_solve_bwd<float2>(const SolveTask*, int, const SolveCtx<float2>&, int, cudaStream_t);
+template void launch_solve_fwd<double2>(const SolveTask*, int, const SolveCtx<double2>&, int, int, int, cudaStream_t);
+template void launch_solve_fwd<float2>(const SolveTask*, int, const SolveCtx<float2>&, int, int, int, cudaStream_t);
+template void launch_solve_bwd<double2>(const SolveTask*, int, const SolveCtx<double2>&, int, int, cudaStream_t);
+template void launch_solve_bwd<float2>(const SolveTask*, int, const SolveCtx<float2>&, int, int, cudaStream_t);
 template int launch_sweep<double2>(const SweepArgs<double2>&, size_t, int, int, cudaStream_t);
 template int launch_sweep<float2>(const SweepArgs<float2>&, size_t, int, int, cudaStream_t);
 

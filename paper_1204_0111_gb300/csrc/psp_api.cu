@@ -269,6 +269,9 @@ struct psp_ctx_s {
     int nfwd = 0, R = 64, smax = 0;
     int64_t bwd_off = 0;
     int nbwd = 0, ldmax = 0;
+    // second phases of the fronts (factors that keep L_BL): up rows r >= s, down columns
+    int64_t fwdB_off = 0, bwdB_off = 0;
+    int nfwdB = 0, nbwdB = 0;
     double entries = 0;   // factor entries read by one direction of this level
     double vec = 0;       // vector entries gathered / written by one direction
   };
@@ -280,7 +283,7 @@ struct psp_ctx_s {
     std::vector<SweepStep> hsteps;
     int nsteps = 0, nqueue = 0;
     // meta layout: front_base | ntask_up | ntask_down | step_front | step_tasks | step_prev
-    int64_t o_up = 0, o_down = 0, o_step_front = 0, o_step_tasks = 0, o_step_prev = 0;
+    int64_t o_up = 0, o_down = 0, o_upA = 0, o_downA = 0, o_step_front = 0, o_step_tasks = 0, o_step_prev = 0;
     int64_t nfront_steps = 0;                 // fronts summed over the steps (counter words per direction)
     double entries = 0, vec = 0;              // algorithmic factor entries / vector words per sweep
   };
@@ -313,6 +316,7 @@ struct psp_ctx_s {
   int tc_min_dim = 64;
   int sweep_level_tasks = 608, sweep_ctas_per_sm = 8, sweep_rhs_group = 0, solve_rhs_group = 0;
   int gmres_basis = 0;   // 0 auto, 1 keep z_j, 2 V only
+  int si_mode = 0;       // psp_si_mode: what the factor of each front keeps (selective inversion, §2.2)
   bool test_sweep_stall = false;
   bool persistent_sweep = true;
   int64_t upd_arena_elems = 0;
@@ -393,7 +397,10 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
       if (d < (int)depth_sns[si].size())
         for (int sn : depth_sns[si][d]) lev_fronts[lv].push_back({p, sn});
     }
-  const bool tc_ok = std::is_same<T, float2>::value && X->use_tc;
+  // selective inversion (§2.2): 0 extended (G = [inv(L_TL); L_BL inv(L_TL)]), 1 the paper's
+  // (G = [inv(L_TL); L_BL]), 2 none (G = [L_TL; L_BL], right-looking LDL^T over all s + u rows)
+  const int si = X->si_mode;
+  const bool tc_ok = std::is_same<T, float2>::value && X->use_tc && si != PSP_SI_NONE;
   auto use_tc = [&](int64_t s_, int64_t u_) { return tc_ok && s_ >= X->tc_min_dim && u_ >= X->tc_min_dim; };
   const int64_t TBLK = tc_block_bytes() / (int64_t)sizeof(T);   // packed block in T elements
   auto nrb = [](int64_t r) { return (r + 127) / 128; };
@@ -402,7 +409,9 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
     return TBLK * (3 * nrb(u_) * nkb16(s_) + 2 * nrb(s_) * nkb16(s_));
   };
   auto front_temp = [&](int64_t s_, int64_t u_) {     // W (s x s), Z (u x s), Z D^-1 or packed operands
-    return pad16(s_ * s_) + pad16(u_ * s_) + (use_tc(s_, u_) ? packed_elems(s_, u_) : pad16(u_ * s_));
+    if (si == PSP_SI_NONE) return (int64_t)0;
+    return pad16(s_ * s_) + pad16(u_ * s_) +
+           (use_tc(s_, u_) ? packed_elems(s_, u_) : si == PSP_SI_EXTENDED ? pad16(u_ * s_) : 0);
   };
   int64_t arena[2] = {0, 0}, temp_level_max = 0, temp_front_max = 16;
   for (int lv = 0; lv < L; ++lv) {
@@ -611,18 +620,25 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
       ft.G = fbase + X->panel_fbase[p] + sh.g_off[sn];
       ft.U = upd_ptr[ft.gfid];
       ft.ut = upd_tile[ft.gfid];
-      ft.W = tbase + toff;
-      toff += pad16((int64_t)ft.s * ft.s);
-      ft.Z = tbase + toff;
-      toff += pad16((int64_t)ft.u * ft.s);
-      ft.ZD = nullptr;
+      ft.W = ft.Z = ft.ZD = nullptr;
+      ft.ldzd = ft.u;
       packs.push_back(nullptr);
-      if (use_tc(ft.s, ft.u)) {
-        packs.back() = reinterpret_cast<unsigned char*>(tbase + toff);
-        toff += packed_elems(ft.s, ft.u);
-      } else {
-        ft.ZD = tbase + toff;
+      if (si != PSP_SI_NONE) {
+        ft.W = tbase + toff;
+        toff += pad16((int64_t)ft.s * ft.s);
+        ft.Z = tbase + toff;
         toff += pad16((int64_t)ft.u * ft.s);
+        if (use_tc(ft.s, ft.u)) {
+          packs.back() = reinterpret_cast<unsigned char*>(tbase + toff);
+          toff += packed_elems(ft.s, ft.u);
+        } else if (si == PSP_SI_EXTENDED) {
+          ft.ZD = tbase + toff;
+          toff += pad16((int64_t)ft.u * ft.s);
+        }
+        if (si == PSP_SI_PAPER) {   // L_BL = Z D^{-1} is the factor's bottom block
+          ft.ZD = ft.G + ft.s;
+          ft.ldzd = ft.s + ft.u;
+        }
       }
       fronts.push_back(ft);
       smax = std::max(smax, ft.s);
@@ -658,7 +674,8 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
       }
       launches.push_back(la);
     }
-    // blocked LDL^T of F_TL with the inverse of L_TL built alongside in W
+    // blocked LDL^T of F_TL with the inverse of L_TL built alongside in W; without selective
+    // inversion the blocked factorisation runs over all s + u rows, so F_BL becomes L_BL directly
     const int nblk = (smax + nb - 1) / nb;
     for (int kb = 0; kb < nblk; ++kb) {
       const int o = kb * nb;
@@ -676,7 +693,9 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
       const int64_t pr0 = (int64_t)ctasks.size();
       for (int f = 0; f < nf; ++f) {
         const auto& ft = fronts[f0 + f];
-        for (int r = o + nb; r < ft.s; r += 64) ctasks.push_back({f, r, std::min(r + 64, ft.s)});
+        if (ft.s <= o) continue;
+        const int rend = si == PSP_SI_NONE ? ft.s + ft.u : ft.s;
+        for (int r = o + nb; r < rend; r += 64) ctasks.push_back({f, r, std::min(r + 64, rend)});
       }
       Launch lr{PRIGHT, f0, pr0, (int)(ctasks.size() - pr0), kb};
       for (int64_t t = pr0; t < (int64_t)ctasks.size(); ++t) {
@@ -686,7 +705,7 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
       }
       launches.push_back(lr);
       const int64_t pl0 = (int64_t)ctasks.size();
-      for (int f = 0; f < nf; ++f) {
+      for (int f = 0; f < nf && si != PSP_SI_NONE; ++f) {
         const auto& ft = fronts[f0 + f];
         if (ft.s <= o) continue;
         const int cend = std::min(ft.s, o + nb);
@@ -721,6 +740,27 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
           g.flags = GF_D_MUL | GF_NEG | (ti == tj ? GF_C_LOWER : 0);
           gtasks.push_back(g);
         });
+        if (si == PSP_SI_NONE) {
+          // F_BL trailing update: F_BL(r, c) -= L_BL(r, kb) D_kb L(c, kb)^T, full tiles
+          for (int tj = 0; tj < ft.s - t0; tj += 64)
+            for (int ti = 0; ti < ft.u; ti += 64) {
+              GemmTask<T> g{};
+              g.C = ft.G + (int64_t)(t0 + tj) * ld + (ft.s + ti);
+              g.ldc = ld;
+              g.A = ft.G + (int64_t)o * ld + (ft.s + ti);
+              g.lda = ld;
+              g.B = ft.G + (int64_t)o * ld + (t0 + tj);
+              g.ldb = ld;
+              g.d = ft.G + (int64_t)o * ld + o;
+              g.ldd = ld + 1;
+              g.m = std::min(64, ft.u - ti);
+              g.n = std::min(64, ft.s - t0 - tj);
+              g.k = bs;
+              g.flags = GF_D_MUL | GF_NEG;
+              gtasks.push_back(g);
+            }
+          continue;   // no inverse of L_TL is built
+        }
         // W(r, c) -= L(r, kb) W(kb, c) for rows below the block, columns up to its end
         const int cend = o + bs;
         for (int tj = 0; tj < cend; tj += 64)
@@ -746,7 +786,7 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
       launches.push_back(lg);
     }
     // inv(L_TL) into F_TL's strict lower part
-    {
+    if (si != PSP_SI_NONE) {
       const int64_t c0 = (int64_t)ctasks.size();
       for (int f = 0; f < nf; ++f) {
         const auto& ft = fronts[f0 + f];
@@ -787,16 +827,27 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
           GemmTask<T> g{};
           g.C = ft.U + upd_index(ti, tj, ft.u, 64);   // the packed 64 x 64 tile (ti, tj)
           g.ldc = 64;
-          g.A = ft.ZD + ti;
-          g.lda = ft.u;
-          g.B = ft.Z + tj;
-          g.ldb = ft.u;
           g.m = std::min(64, ft.u - ti);
           g.n = std::min(64, ft.u - tj);
           g.k = ft.s;
           g.flags = GF_NEG | (ti == tj ? GF_C_LOWER : 0);
+          if (si == PSP_SI_NONE) {   // F_BR -= L_BL D L_BL^T
+            g.A = ft.G + ft.s + ti;
+            g.lda = ld;
+            g.B = ft.G + ft.s + tj;
+            g.ldb = ld;
+            g.d = ft.G;
+            g.ldd = ld + 1;
+            g.flags |= GF_D_MUL;
+          } else {                   // F_BR -= (Z D^{-1}) Z^T
+            g.A = ft.ZD + ti;
+            g.lda = ft.ldzd;
+            g.B = ft.Z + tj;
+            g.ldb = ft.u;
+          }
           gtasks.push_back(g);
         }
+      if (si != PSP_SI_EXTENDED) return;
       for (int tj = 0; tj < ft.s; tj += 64)
         for (int ti = 0; ti < ft.u; ti += 64) {
           GemmTask<T> g{};
@@ -847,14 +898,15 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
       for (size_t i = t0; i < ttasks.size(); ++i) by += 2.0 * ttasks[i].nkb * tc_block_bytes();
       (void)fl;
     };
-    for (int phase = 0; phase < 2; ++phase) {
-      if (phase == 1) {
-        // Z D^{-1} of the CUDA-core fronts, once per front
+    for (int phase = si == PSP_SI_NONE ? 1 : 0; phase < 2; ++phase) {
+      if (phase == 1 && si != PSP_SI_NONE) {
+        // Z D^{-1} once per front: of the CUDA-core fronts (extended form), or of every front into the
+        // factor's bottom block (L_BL, the paper's form)
         const int64_t c0 = (int64_t)ctasks.size();
         Launch ls{SCALE, f0, c0, 0, 0};
         for (int f : ord) {
           const auto& ft = fronts[f0 + f];
-          if (ft.u == 0 || packs[f0 + f]) continue;
+          if (ft.u == 0 || (packs[f0 + f] && si == PSP_SI_EXTENDED)) continue;
           for (int c = 0; c < ft.s; c += 16) ctasks.push_back({f, c, std::min(c + 16, ft.s)});
           ls.bytes += 2.0 * es * ft.u * ft.s;
         }
@@ -888,7 +940,7 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
         if (phase == 0) {
           pack(ft.G + ft.s, nullptr, P.bl, ld, 0, ft.u, ft.s, TC_PACK_PLAIN);
           pack(ft.G, nullptr, P.l, ld, 0, ft.s, ft.s, TC_PACK_UNIT_LOWER);
-          pack(ft.G, nullptr, P.lt, ld, 0, ft.s, ft.s, TC_PACK_UNIT_LOWER_T);
+          if (si == PSP_SI_EXTENDED) pack(ft.G, nullptr, P.lt, ld, 0, ft.s, ft.s, TC_PACK_UNIT_LOWER_T);
           for (int tj = 0; tj < ft.s; tj += 128)
             for (int ti = 0; ti < ft.u; ti += 128) {
               const int j1 = std::min(tj + 128, ft.s);
@@ -927,7 +979,7 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
               sh.m = t.m; sh.n = t.n; sh.k = ft.s; sh.flags = (ti == tj ? GF_C_LOWER : 0);
               tflops += 8.0 * gemm_cmacs(sh);
             }
-          for (int tj = 0; tj < ft.s; tj += 128)
+          for (int tj = 0; tj < ft.s && si == PSP_SI_EXTENDED; tj += 128)
             for (int ti = 0; ti < ft.u; ti += 128) {
               TcGemmTask t{};
               t.A = P.zd + (int64_t)(ti / 128) * P.ku * bb;
@@ -1016,20 +1068,41 @@ static void plan_solve(psp_ctx_s* X, cudaStream_t st) {
       P.R = R;
       int Cc = 64;
       while (Cc > 8 && cols / Cc < X->sweep_level_tasks) Cc >>= 1;
+      // extended factors: one pass per front and direction over all s + u rows; factors keeping L_BL:
+      // up, rows r < s (one whole-front substitution task without inversion) then rows r >= s; down,
+      // columns for L_BL^T then columns for the triangle (one whole-front task without inversion)
+      const bool two = X->si_mode != PSP_SI_EXTENDED, tri = X->si_mode == PSP_SI_NONE;
+      auto rows_of = [&](int sn, int a, int b, int step) {
+        for (int r = a; r < b; r += step) tasks.push_back({sn, r, std::min(r + step, b)});
+      };
       P.fwd_off = (int64_t)tasks.size();
-      for (int sn : sh.level_sns[lv])
-        for (int r = 0; r < sh.s[sn] + sh.u[sn]; r += R) tasks.push_back({sn, r, std::min(r + R, sh.s[sn] + sh.u[sn])});
+      for (int sn : sh.level_sns[lv]) {
+        const int s_ = sh.s[sn], ld_ = s_ + sh.u[sn];
+        if (!two) rows_of(sn, 0, ld_, R);
+        else if (tri) tasks.push_back({sn, 0, s_});
+        else rows_of(sn, 0, s_, R);
+      }
       P.nfwd = (int)(tasks.size() - P.fwd_off);
+      P.fwdB_off = (int64_t)tasks.size();
+      if (two)
+        for (int sn : sh.level_sns[lv]) rows_of(sn, sh.s[sn], sh.s[sn] + sh.u[sn], R);
+      P.nfwdB = (int)(tasks.size() - P.fwdB_off);
       P.bwd_off = (int64_t)tasks.size();
-      for (int sn : sh.level_sns[lv])
-        for (int c = 0; c < sh.s[sn]; c += Cc) tasks.push_back({sn, c, std::min(c + Cc, (int)sh.s[sn])});
+      for (int sn : sh.level_sns[lv]) rows_of(sn, 0, sh.s[sn], Cc);
       P.nbwd = (int)(tasks.size() - P.bwd_off);
+      P.bwdB_off = (int64_t)tasks.size();
+      if (two)
+        for (int sn : sh.level_sns[lv]) {
+          if (tri) tasks.push_back({sn, 0, (int)sh.s[sn]});
+          else rows_of(sn, 0, sh.s[sn], Cc);
+        }
+      P.nbwdB = (int)(tasks.size() - P.bwdB_off);
     }
   }
   upload_async(X->d_stasks, tasks, st);
 
   // per shape: tasks per front, up and down
-  std::vector<int> front_base(X->shapes.size() + 1, 0), ntask_up, ntask_down;
+  std::vector<int> front_base(X->shapes.size() + 1, 0), ntask_up, ntask_down, ntask_upA, ntask_downA;
   size_t per_rhs = 0;
   std::vector<double> shape_entries(X->shapes.size(), 0.0), shape_vec(X->shapes.size(), 0.0);
   std::vector<int> shape_tasks(X->shapes.size(), 0);
@@ -1038,14 +1111,22 @@ static void plan_solve(psp_ctx_s* X, cudaStream_t st) {
     front_base[si] = (int)ntask_up.size();
     ntask_up.resize(ntask_up.size() + sh.nsn, 0);
     ntask_down.resize(ntask_down.size() + sh.nsn, 0);
+    ntask_upA.resize(ntask_upA.size() + sh.nsn, 0);
+    ntask_downA.resize(ntask_downA.size() + sh.nsn, 0);
     for (const auto& P : X->splan[si]) {
-      for (int t = 0; t < P.nfwd; ++t) ntask_up[front_base[si] + tasks[P.fwd_off + t].sn]++;
-      for (int t = 0; t < P.nbwd; ++t) ntask_down[front_base[si] + tasks[P.bwd_off + t].sn]++;
+      for (int t = 0; t < P.nfwd; ++t) ntask_upA[front_base[si] + tasks[P.fwd_off + t].sn]++;
+      for (int t = 0; t < P.nbwd; ++t) ntask_downA[front_base[si] + tasks[P.bwd_off + t].sn]++;
+      for (int t = 0; t < P.nfwdB; ++t) ntask_up[front_base[si] + tasks[P.fwdB_off + t].sn]++;
+      for (int t = 0; t < P.nbwdB; ++t) ntask_down[front_base[si] + tasks[P.bwdB_off + t].sn]++;
       per_rhs = std::max(per_rhs, (size_t)std::max(P.smax + 256, P.ldmax));
       shape_entries[si] += 2 * P.entries;
       shape_vec[si] += 2 * P.vec;
-      shape_tasks[si] += P.nfwd + P.nbwd;
+      shape_tasks[si] += P.nfwd + P.nbwd + P.nfwdB + P.nbwdB;
     }
+  }
+  for (size_t f = 0; f < ntask_up.size(); ++f) {   // totals: both phases
+    ntask_up[f] += ntask_upA[f];
+    ntask_down[f] += ntask_downA[f];
   }
   front_base[X->shapes.size()] = (int)ntask_up.size();
   X->sweep_rhs_bytes = per_rhs;
@@ -1092,24 +1173,35 @@ static void plan_solve(psp_ctx_s* X, cudaStream_t st) {
       SP.entries += shape_entries[si];
       SP.vec += shape_vec[si];
       const auto& plan = X->splan[si];
-      for (size_t lv = 0; lv < plan.size(); ++lv)
+      for (size_t lv = 0; lv < plan.size(); ++lv) {
         for (int t = 0; t < plan[lv].nfwd; ++t)
           queue.push_back({(int)k, (int)(plan[lv].fwd_off + t), 0, (short)plan[lv].R});
-      for (int lv = (int)plan.size() - 1; lv >= 0; --lv)
+        for (int t = 0; t < plan[lv].nfwdB; ++t)
+          queue.push_back({(int)k, (int)(plan[lv].fwdB_off + t), (short)kDirUpB, (short)plan[lv].R});
+      }
+      for (int lv = (int)plan.size() - 1; lv >= 0; --lv) {
         for (int t = 0; t < plan[lv].nbwd; ++t) queue.push_back({(int)k, (int)(plan[lv].bwd_off + t), 1, 0});
+        for (int t = 0; t < plan[lv].nbwdB; ++t)
+          queue.push_back({(int)k, (int)(plan[lv].bwdB_off + t), (short)kDirDownB, 0});
+      }
     }
     SP.hsteps = steps;
     SP.nsteps = (int)steps.size();
     SP.nqueue = (int)queue.size();
     upload_async(SP.steps, steps, st);
     upload_async(SP.queue, queue, st);
-    // metadata: front_base | ntask_up | ntask_down | step_front | step_tasks | step_prev
+    // metadata: front_base | ntask_up | ntask_down | ntask_upA | ntask_downA | step_front | step_tasks |
+    // step_prev
     std::vector<int> meta;
     meta.insert(meta.end(), front_base.begin(), front_base.end());
     SP.o_up = (int64_t)meta.size();
     meta.insert(meta.end(), ntask_up.begin(), ntask_up.end());
     SP.o_down = (int64_t)meta.size();
     meta.insert(meta.end(), ntask_down.begin(), ntask_down.end());
+    SP.o_upA = (int64_t)meta.size();
+    meta.insert(meta.end(), ntask_upA.begin(), ntask_upA.end());
+    SP.o_downA = (int64_t)meta.size();
+    meta.insert(meta.end(), ntask_downA.begin(), ntask_downA.end());
     SP.o_step_front = (int64_t)meta.size();
     meta.insert(meta.end(), step_front.begin(), step_front.end());
     SP.o_step_tasks = (int64_t)meta.size();
@@ -1176,6 +1268,7 @@ static void apply_core(psp_ctx_s* X, double2* u, int nrhs, T* xf, T* xb, T* upd,
     cx.inv_h2 = 1.0 / (pr.h * pr.h);
   };
   cx.nrhs = nrhs;
+  cx.si = X->si_mode;
   cx.upd_ld = X->max_upd;
   cx.n_loc = X->max_nloc;
   set_problem(0);
@@ -1204,13 +1297,17 @@ static void apply_core(psp_ctx_s* X, double2* u, int nrhs, T* xf, T* xb, T* upd,
     const double es = sizeof(T);
     for (int lv = 0; lv < nl; ++lv) {
       const auto& P = plan[lv];
-      X->stats.run("k_solve_fwd", st, 1, 8.0 * P.entries * nrhs, P.entries * es + P.vec * es * nrhs,
-                   [&] { launch_solve_fwd<T>(tasks + P.fwd_off, P.nfwd, cx, P.R, P.smax, st); });
+      X->stats.run("k_solve_fwd", st, 1, 8.0 * P.entries * nrhs, P.entries * es + P.vec * es * nrhs, [&] {
+        launch_solve_fwd<T>(tasks + P.fwd_off, P.nfwd, cx, P.R, P.smax, 0, st);
+        launch_solve_fwd<T>(tasks + P.fwdB_off, P.nfwdB, cx, P.R, P.smax, 1, st);
+      });
     }
     for (int lv = nl - 1; lv >= 0; --lv) {
       const auto& P = plan[lv];
-      X->stats.run("k_solve_bwd", st, 1, 8.0 * P.entries * nrhs, P.entries * es + P.vec * es * nrhs,
-                   [&] { launch_solve_bwd<T>(tasks + P.bwd_off, P.nbwd, cx, P.ldmax, st); });
+      X->stats.run("k_solve_bwd", st, 1, 8.0 * P.entries * nrhs, P.entries * es + P.vec * es * nrhs, [&] {
+        launch_solve_bwd<T>(tasks + P.bwd_off, P.nbwd, cx, P.ldmax, 0, st);
+        launch_solve_bwd<T>(tasks + P.bwdB_off, P.nbwdB, cx, P.ldmax, 1, st);
+      });
     }
   };
   try {
@@ -1231,6 +1328,8 @@ static void apply_core(psp_ctx_s* X, double2* u, int nrhs, T* xf, T* xb, T* upd,
     sa.front_base = meta;
     sa.ntask_up = meta + SP.o_up;
     sa.ntask_down = meta + SP.o_down;
+    sa.ntask_upA = meta + SP.o_upA;
+    sa.ntask_downA = meta + SP.o_downA;
     sa.step_front_base = meta + SP.o_step_front;
     sa.step_tasks = meta + SP.o_step_tasks;
     sa.nprobs = np;
@@ -1970,7 +2069,7 @@ static psp_status check_options(const psp_options* opt, psp_options* o) {
       (o->precision != PSP_PREC_C128 && o->precision != PSP_PREC_C64) ||
       (o->aux_mode != PSP_AUX_MOVING_PML && o->aux_mode != PSP_AUX_EXACT) || !(o->alpha >= 0) || !(o->pml_C >= 0) ||
       o->gmres_basis < 0 || o->gmres_basis > 2 || o->panel_begin < 0 || o->panel_count < 0 ||
-      (o->dev_alloc == nullptr) != (o->dev_free == nullptr))
+      (o->dev_alloc == nullptr) != (o->dev_free == nullptr) || o->selective_inversion < 0 || o->selective_inversion > 2)
     return fail(PSP_ERR_ARG, "bad options");
   return PSP_OK;
 }
@@ -2000,6 +2099,7 @@ static void init_options(psp_ctx_s* X, const psp_options& o) {
   X->sweep_rhs_group = o.sweep_rhs_group > 0 ? o.sweep_rhs_group : 0;
   X->solve_rhs_group = o.solve_rhs_group > 0 ? o.solve_rhs_group : 0;
   X->gmres_basis = o.gmres_basis;
+  X->si_mode = o.selective_inversion;
   X->factor_every_panel = o.factor_every_panel != 0;
   X->range_begin = o.panel_begin;
   X->range_count = o.panel_count;

@@ -148,11 +148,12 @@ struct FrontTask {
   T* U;        // u x u update (F_BR) in lower tiles of ut x ut (upd_index); nullptr for the root
   T* W;        // s x s work: inv(L_TL) under construction
   T* Z;        // u x s work: F_BL L^{-T}
-  T* ZD;       // u x s work: Z D^{-1} (fronts whose products run on CUDA cores; else nullptr)
+  T* ZD;       // u x s: Z D^{-1}, leading dimension ldzd (a work block for the extended selective
+               // inversion of CUDA-core fronts, G's bottom block when L_BL itself is stored; else nullptr)
   int s, u;
   int panel, sn;
   int64_t gfid;
-  int ut, pad_;   // tile size of U
+  int ut, ldzd;   // tile size of U; leading dimension of ZD
 };
 
 struct ColTask {   // a chunk of columns / rows of one front
@@ -227,16 +228,19 @@ struct SolveCtx {
   int z0, z1, lead, nz;    // panel planes, pad planes, global plane count
   int mode;                // 0: forward sweep (u_i := T_i(u_i - J_{i,i-1} u_{i-1})); 1: backward (u_i -= T_i J^T u_{i+1})
   int has_prev, has_next;
+  int si;                  // psp_si_mode of the factors (what G keeps)
   const double2* s1n;      // global stretch tables for the plane coupling J_{i+1,i}
   const double2* s2n;
   const double2* s3h;
   double inv_h2;
 };
 
+// phase 0: the single pass (extended factors) or first phase of a front; phase 1: its second phase
 template <typename T>
-void launch_solve_fwd(const SolveTask* tasks, int ntasks, const SolveCtx<T>& cx, int R, int smax, cudaStream_t st);
+void launch_solve_fwd(const SolveTask* tasks, int ntasks, const SolveCtx<T>& cx, int R, int smax, int phase,
+                      cudaStream_t st);
 template <typename T>
-void launch_solve_bwd(const SolveTask* tasks, int ntasks, const SolveCtx<T>& cx, int ldmax, cudaStream_t st);
+void launch_solve_bwd(const SolveTask* tasks, int ntasks, const SolveCtx<T>& cx, int ldmax, int phase, cudaStream_t st);
 
 // ---- the whole sweep in one cooperative launch ----
 struct SweepStep {      // one panel solve of Alg. 1.5, in order
@@ -266,9 +270,12 @@ struct LevelSweep {
 struct QueueEntry {
   int step;                     // panel solve index
   int task;                     // index into the shape's SolveTask list
-  short dir;                    // 0 up the tree, 1 down the tree
+  short dir;                    // 0 up the tree, 1 down the tree; 2 / 3 the second phase up / down of a front
+                                // whose factor keeps L_BL (the first phase is then 0 / 1)
   short R;                      // rows per up-the-tree task
 };
+// second phases of a front (factors that keep L_BL rather than L_BL inv(L_TL))
+constexpr int kDirUpB = 2, kDirDownB = 3;
 template <typename T>
 struct SweepArgs {
   SolveCtx<T> cx;               // fields common to every panel (vectors, sizes, coupling tables); for a batch
@@ -283,6 +290,8 @@ struct SweepArgs {
   int nqueue;
   const int* ntask_up;          // per shape-front: number of up / down tasks (shape offset: front_base)
   const int* ntask_down;
+  const int* ntask_upA;         // per shape-front: tasks of the first phase up / down (two-phase fronts)
+  const int* ntask_downA;
   const int* front_base;        // per shape: offset of its fronts in ntask_up / ntask_down
   const int* step_front_base;   // per step: offset of its fronts in the done counters
   const int* step_tasks;        // per step: number of tasks

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(HERE, "lib", "libpsp.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "psp.h")
 
 PREC_C128, PREC_C64 = 0, 1
+SI_MODES = {"extended": 0, "paper": 1, "none": 2}   # psp_si_mode
 AUX_MOVING_PML, AUX_EXACT = 0, 1
 STATUS = {0: "PSP_OK", 1: "PSP_ERR_ARG", 2: "PSP_ERR_OOM", 3: "PSP_ERR_CUDA", 4: "PSP_ERR_ZERO_PIVOT",
           5: "PSP_ERR_NOT_CONVERGED", 6: "PSP_ERR_TIMEOUT", 7: "PSP_ERR_STATE"}
@@ -37,7 +38,8 @@ class Options(ctypes.Structure):
                 ("setup_temp_mb", ctypes.c_int), ("sweep_rhs_group", ctypes.c_int),
                 ("solve_rhs_group", ctypes.c_int), ("test_sweep_stall", ctypes.c_int), ("gmres_basis", ctypes.c_int),
                 ("factor_every_panel", ctypes.c_int), ("panel_begin", ctypes.c_int), ("panel_count", ctypes.c_int),
-                ("dev_alloc", ctypes.c_void_p), ("dev_free", ctypes.c_void_p), ("alloc_ctx", ctypes.c_void_p)]
+                ("dev_alloc", ctypes.c_void_p), ("dev_free", ctypes.c_void_p), ("alloc_ctx", ctypes.c_void_p),
+                ("selective_inversion", ctypes.c_int)]
 
 
 # psp_options.dev_alloc / dev_free callback types
@@ -169,7 +171,7 @@ class SweepingPreconditioner:
                  precision="c128", faces=63, mode="moving", stream=None, collect_stats=0, tensor_cores=True,
                  tc_min_dim=0, sweep_level_tasks=0, sweep_ctas_per_sm=0, setup_temp_mb=0, sweep_rhs_group=0,
                  solve_rhs_group=0, test_sweep_stall=0, gmres_basis="auto", factor_every_panel=False,
-                 panels=None, allocator=None):
+                 panels=None, allocator=None, selective_inversion="extended"):
         nz, ny, nx = c.shape
         self.nx, self.ny, self.nz = nx, ny, nz
         self.N = nx * ny * nz
@@ -182,6 +184,7 @@ class SweepingPreconditioner:
         o.factor_every_panel = 1 if factor_every_panel else 0
         if panels is not None:                   # (first, count): one block of a multi-GPU sweep
             o.panel_begin, o.panel_count = int(panels[0]), int(panels[1])
+        o.selective_inversion = SI_MODES[selective_inversion]
         if allocator is not None:                # (alloc(bytes) -> int, free(int)): the caller owns device memory
             self._alloc_cbs = _allocator_callbacks(*allocator)
             o.dev_alloc = ctypes.cast(self._alloc_cbs[0], ctypes.c_void_p)
