@@ -344,6 +344,31 @@ typedef struct {
 psp_status psp_tune_sweep(psp_handle h, int nrhs, int reps, void* stream, psp_sweep_tuning* out);
 
 /*
+ * psp_tune_setup - the paper has no counterpart: an autotuner for what the setup builds.  The paper
+ * weighs selective inversion's dearer setup against its faster solves (§2.2, §3 Table 2); this call
+ * measures that trade on the handle's own problem.  It re-factors the handle under each candidate
+ * (the three psp_si_mode forms and, for complex64 tensor-core fronts, tc_min_dim 32 / 64 / 128),
+ * timing the setup (host clock, the factorisation synchronises) and one application to nrhs
+ * right-hand sides (CUDA events on `stream`, after an untimed one), and keeps the candidate with
+ * the least setup_ms + expected_applies x apply_ms; the handle ends factored that way.  Results
+ * change only by rounding (the forms apply the same preconditioner).  Costs one factorisation per
+ * candidate.
+ * Errors: PSP_ERR_ARG, PSP_ERR_STATE (no factorisation, or a block handle), PSP_ERR_CUDA.
+ */
+typedef struct {
+  int selective_inversion;  /* chosen psp_si_mode */
+  int tc_min_dim;           /* chosen tensor-core threshold (complex64) */
+  int candidates;           /* configurations timed */
+  double setup_ms;          /* setup of the chosen configuration */
+  double apply_ms;          /* one application of the chosen configuration */
+  double initial_total_ms;  /* setup + expected_applies x apply under the handle's configuration before */
+  double best_total_ms;     /* the same for the chosen one */
+  int reserved[4];
+} psp_setup_tuning;
+
+psp_status psp_tune_setup(psp_handle h, int nrhs, int expected_applies, void* stream, psp_setup_tuning* out);
+
+/*
  * psp_sweep_part - one half of Alg. 1.5 restricted to the handle's block of panels [b, e)
  * (psp_options.panel_begin / panel_count), for a sweep whose panels are spread over several GPUs
  * (§2: the panel factorisations are independent, the panel solves run in sequence).  u holds nrhs

@@ -2604,6 +2604,92 @@ psp_status psp_check_status(psp_handle X, void* stream) {
   PSP_CATCH
 }
 
+psp_status psp_tune_setup(psp_handle X, int nrhs, int expected_applies, void* stream, psp_setup_tuning* out) {
+  if (!X || nrhs < 1 || expected_applies < 0) return fail(PSP_ERR_ARG, "bad tuning arguments");
+  if (!X->d_factor.p) return fail(PSP_ERR_STATE, "handle has no factorisation");
+  if (X->partial) return fail(PSP_ERR_STATE, kPartialMsg);
+  PSP_TRY
+  check_device(X);
+  AllocScope scope(&X->allocator);
+  cudaStream_t st = (cudaStream_t)stream;
+  struct Cand { int si, tc; };
+  std::vector<Cand> cands;
+  const bool tc = X->prec == PSP_PREC_C64 && X->use_tc;
+  for (int si : {PSP_SI_EXTENDED, PSP_SI_PAPER, PSP_SI_NONE})
+    if (tc && si != PSP_SI_NONE)
+      for (int t : {32, 64, 128}) cands.push_back({si, t});
+    else
+      cands.push_back({si, X->tc_min_dim});
+  const Cand initial{X->si_mode, X->tc_min_dim};
+  DevBuf u;
+  const size_t bytes = (size_t)X->N * nrhs * sizeof(double2);
+  u.alloc(bytes);
+  cudaEvent_t e0, e1;
+  PSP_CK(cudaEventCreate(&e0));
+  PSP_CK(cudaEventCreate(&e1));
+  struct EventGuard {
+    cudaEvent_t a, b;
+    ~EventGuard() { cudaEventDestroy(a); cudaEventDestroy(b); }
+  } eg{e0, e1};
+  const bool was_timing = X->stats.timing;
+  X->stats.timing = false;
+  struct TimingGuard {
+    psp_ctx_s* X;
+    bool was;
+    ~TimingGuard() { X->stats.timing = was; }
+  } tg{X, was_timing};
+  // setup (host and device, the factorisation synchronises) and one application after a warm one
+  auto time_one = [&](const Cand& c, double& setup_ms, double& apply_ms) {
+    X->si_mode = c.si;
+    X->tc_min_dim = c.tc;
+    const auto t0 = std::chrono::steady_clock::now();
+    finish_setup(X, st);
+    setup_ms = ms_since(t0);
+    PSP_CK(cudaMemsetAsync(u.p, 0x3f, bytes, st));   // a fixed, finite, normal pattern
+    apply_dispatch(X, u.as<double2>(), nrhs, st);
+    PSP_CK(cudaEventRecord(e0, st));
+    apply_dispatch(X, u.as<double2>(), nrhs, st);
+    PSP_CK(cudaEventRecord(e1, st));
+    PSP_CK(cudaEventSynchronize(e1));
+    float ms = 0;
+    PSP_CK(cudaEventElapsedTime(&ms, e0, e1));
+    apply_ms = ms;
+  };
+  Cand best = initial;
+  double best_total = 0, initial_total = 0, best_setup = 0, best_apply = 0;
+  int tried = 0;
+  for (const Cand& c : cands) {
+    double sm = 0, am = 0;
+    time_one(c, sm, am);
+    ++tried;
+    const double total = sm + (double)expected_applies * am;
+    if (c.si == initial.si && c.tc == initial.tc) initial_total = total;
+    if (tried == 1 || total < best_total) {
+      best_total = total;
+      best = c;
+      best_setup = sm;
+      best_apply = am;
+    }
+  }
+  if (X->si_mode != best.si || X->tc_min_dim != best.tc) {   // keep the factorisation of the best choice
+    X->si_mode = best.si;
+    X->tc_min_dim = best.tc;
+    finish_setup(X, st);
+  }
+  if (out) {
+    std::memset(out, 0, sizeof(*out));
+    out->selective_inversion = best.si;
+    out->tc_min_dim = best.tc;
+    out->candidates = tried;
+    out->setup_ms = best_setup;
+    out->apply_ms = best_apply;
+    out->initial_total_ms = initial_total;
+    out->best_total_ms = best_total;
+  }
+  return PSP_OK;
+  PSP_CATCH
+}
+
 psp_status psp_destroy(psp_handle X) {
   if (!X) return PSP_OK;
   delete X;

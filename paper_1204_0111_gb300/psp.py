@@ -71,6 +71,17 @@ class SweepTuning(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
+class SetupTuning(ctypes.Structure):
+    _fields_ = [("selective_inversion", ctypes.c_int), ("tc_min_dim", ctypes.c_int), ("candidates", ctypes.c_int),
+                ("setup_ms", ctypes.c_double), ("apply_ms", ctypes.c_double), ("initial_total_ms", ctypes.c_double),
+                ("best_total_ms", ctypes.c_double), ("reserved", ctypes.c_int * 4)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        d["selective_inversion"] = {v: k for k, v in SI_MODES.items()}[d["selective_inversion"]]
+        return d
+
+
 class PSPError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -114,6 +125,7 @@ def lib():
         "psp_stats": (_I, [_P, ctypes.POINTER(KernelStat), _I, ctypes.POINTER(_I), _I]),
         "psp_tune_sweep": (_I, [_P, _I, _I, _P, ctypes.POINTER(SweepTuning)]),
         "psp_check_status": (_I, [_P, _P]),
+        "psp_tune_setup": (_I, [_P, _I, _I, _P, ctypes.POINTER(SetupTuning)]),
         "psp_sweep_part": (_I, [_P, _P, _I, _I, _P]),
         "psp_solve_history": (_I, [_P, _I, ctypes.POINTER(ctypes.c_double), _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
         "psp_plan_panels": (_I, [ctypes.POINTER(Grid), _I, _I, ctypes.POINTER(Options), ctypes.POINTER(_I),
@@ -257,6 +269,12 @@ class SweepingPreconditioner:
         nr = self._nrhs(u)
         _check(lib().psp_sweep_part(self._h, _ptr_and_len(u)[0], nr, int(direction), _stream(stream)))
         return u
+
+    def tune_setup(self, nrhs=1, expected_applies=20, stream=None):
+        """psp_tune_setup: re-factor under each candidate setup and keep the cheapest for the expected solve."""
+        t = SetupTuning()
+        _check(lib().psp_tune_setup(self._h, int(nrhs), int(expected_applies), _stream(stream), ctypes.byref(t)))
+        return t.as_dict()
 
     def check_status(self, stream=None):
         """psp_check_status: raise PSPError(PSP_ERR_TIMEOUT) if a sweep wait gave up since the last check."""

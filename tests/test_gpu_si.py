@@ -139,3 +139,25 @@ def test_blocks_in_each_form(si):
     assert float(torch.linalg.norm(u - ref) / torch.linalg.norm(ref)) < 1e-13
     for P in parts + [full]:
         P.close()
+
+
+@pytest.mark.parametrize("precision,ncand", [("c128", 3), ("c64", 7)])
+def test_setup_autotuner_keeps_results(precision, ncand):
+    # psp_tune_setup re-factors the handle under each form (and tensor-core threshold) and keeps the
+    # cheapest for the expected number of applications; the preconditioner stays the same
+    case = CASES[2]
+    P = gpu_for(case, "extended", precision=precision)
+    r = wl.random_vector(case.N, 1, seed=29)
+    before = torch.empty((1, case.N), dtype=torch.complex128, device="cuda")
+    P.apply(torch.from_numpy(r).cuda(), before)
+    t = P.tune_setup(nrhs=1, expected_applies=25)
+    assert t["candidates"] == ncand and t["best_total_ms"] <= t["initial_total_ms"]
+    assert t["selective_inversion"] in ("extended", "paper", "none")
+    after = torch.empty_like(before)
+    P.apply(torch.from_numpy(r).cuda(), after)
+    torch.cuda.synchronize()
+    tol = 1e-10 if precision == "c128" else 1e-4
+    assert float(torch.linalg.norm(after - before) / torch.linalg.norm(before)) < tol
+    if precision == "c128":
+        assert rel(after.cpu().numpy(), oracle_for(case).apply(r)) < 1e-10
+    P.close()
