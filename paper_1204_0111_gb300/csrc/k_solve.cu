@@ -63,59 +63,70 @@ __device__ __forceinline__ void pull_add(const SolveCtx<T>& cx, const int32_t* p
 // phase 1 (factors keeping L_BL) takes y_S from xb and writes the update w_U - L_BL y_S of rows r >= s.
 template <typename T, int RG>
 __device__ __forceinline__ void fwd_task(const SolveTask tk, const int rhs0, const SolveCtx<T>& cx, const int R,
-                                         unsigned char* smem_raw, const int phase) {
+                                         unsigned char* smem_raw, const int phase, const int chunk) {
   const int sn = tk.sn;
   const int s = cx.sh.s[sn], u = cx.sh.u[sn], ld = s + u;
   const int first = cx.sh.first[sn];
   const T* G = cx.G + cx.sh.g_off[sn];
   const int32_t* pull = cx.sh.pull + 2 * cx.sh.pull_ptr[sn];
-  T* w = reinterpret_cast<T*>(smem_raw);        // s x RG
-  T* red = w + (int64_t)s * RG;                  // blockDim x RG
-
-  if (phase == 0) {
-    // w_S = (zero-extended input) + children's updates
-    for (int p = threadIdx.x; p < s; p += blockDim.x) {
-      const int node = cx.sh.order[first + p];
-      T v[RG];
-#pragma unroll
-      for (int q = 0; q < RG; ++q) v[q] = (rhs0 + q < cx.nrhs) ? input_value(cx, node, rhs0 + q) : CplxTraits<T>::zero();
-      pull_add<T, RG>(cx, pull + 2 * p, rhs0, v);
-#pragma unroll
-      for (int q = 0; q < RG; ++q) w[p * RG + q] = v[q];
-    }
-  } else {
-    for (int p = threadIdx.x; p < s; p += blockDim.x)
-#pragma unroll
-      for (int q = 0; q < RG; ++q)
-        w[p * RG + q] = (rhs0 + q < cx.nrhs) ? __ldcg(cx.xb + (int64_t)(rhs0 + q) * cx.n_loc + first + p)
-                                             : CplxTraits<T>::zero();
-  }
-  __syncthreads();
+  // the vector w_S (or y_S) passes through shared memory in chunks of `chunk` entries (a multiple of
+  // 256), so a CTA carries RG right-hand sides over a factor block of any width and reads it once
+  T* w = reinterpret_cast<T*>(smem_raw);        // chunk x RG
+  T* red = w + (int64_t)chunk * RG;              // blockDim x RG
 
   const int i = threadIdx.x % R, grp = threadIdx.x / R, ngrp = blockDim.x / R;
   const int r = tk.r0 + i;
-  T acc[RG];
+  const int jmax = r < tk.r1 ? (r < s ? r : s) : 0;   // strictly lower part of inv(L_TL), all of the bottom block
+  const int jend = min(tk.r1, s);                      // entries of w_S this task needs (w_r of its rows r < s too)
+  T acc[RG], wr[RG];
 #pragma unroll
-  for (int q = 0; q < RG; ++q) acc[q] = CplxTraits<T>::zero();
-  if (r < tk.r1) {
-    const int jmax = r < s ? r : s;   // strictly lower part of inv(L_TL), all of the bottom block
-    const T* Gr = G + r;
-    const int64_t step = (int64_t)ngrp * ld;
-    int j = grp;
-    // eight independent factor loads in flight per thread
-    for (; j + 7 * ngrp < jmax; j += 8 * ngrp) {
-      T gv[8];
+  for (int q = 0; q < RG; ++q) acc[q] = wr[q] = CplxTraits<T>::zero();
+  const T* Gr = G + r;
+  const int64_t step = (int64_t)ngrp * ld;
+  for (int j0 = 0; j0 < jend; j0 += chunk) {
+    const int j1 = min(j0 + chunk, jend);
+    if (j0 > 0) __syncthreads();   // the previous chunk is consumed
+    if (phase == 0) {
+      // w_S = (zero-extended input) + children's updates
+      for (int p = j0 + threadIdx.x; p < j1; p += blockDim.x) {
+        const int node = cx.sh.order[first + p];
+        T v[RG];
 #pragma unroll
-      for (int t = 0; t < 8; ++t) gv[t] = __ldg(Gr + (int64_t)j * ld + t * step);
+        for (int q = 0; q < RG; ++q) v[q] = (rhs0 + q < cx.nrhs) ? input_value(cx, node, rhs0 + q) : CplxTraits<T>::zero();
+        pull_add<T, RG>(cx, pull + 2 * p, rhs0, v);
 #pragma unroll
-      for (int t = 0; t < 8; ++t)
+        for (int q = 0; q < RG; ++q) w[(p - j0) * RG + q] = v[q];
+      }
+    } else {
+      for (int p = j0 + threadIdx.x; p < j1; p += blockDim.x)
 #pragma unroll
-        for (int q = 0; q < RG; ++q) cfma(acc[q], gv[t], w[(j + t * ngrp) * RG + q]);
+        for (int q = 0; q < RG; ++q)
+          w[(p - j0) * RG + q] = (rhs0 + q < cx.nrhs) ? __ldcg(cx.xb + (int64_t)(rhs0 + q) * cx.n_loc + first + p)
+                                                      : CplxTraits<T>::zero();
     }
-    for (; j < jmax; j += ngrp) {
-      const T gv = __ldg(Gr + (int64_t)j * ld);
+    __syncthreads();
+    if (r < tk.r1) {
+      if (r < s && r >= j0 && r < j1)
 #pragma unroll
-      for (int q = 0; q < RG; ++q) cfma(acc[q], gv, w[j * RG + q]);
+        for (int q = 0; q < RG; ++q) wr[q] = w[(r - j0) * RG + q];
+      // the same j sequence j = grp, grp + ngrp, ... in every chunking (j0 is a multiple of ngrp)
+      const int jm = min(jmax, j1);
+      int j = j0 + grp;
+      // eight independent factor loads in flight per thread
+      for (; j + 7 * ngrp < jm; j += 8 * ngrp) {
+        T gv[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) gv[t] = __ldg(Gr + (int64_t)j * ld + t * step);
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+#pragma unroll
+          for (int q = 0; q < RG; ++q) cfma(acc[q], gv[t], w[(j - j0 + t * ngrp) * RG + q]);
+      }
+      for (; j < jm; j += ngrp) {
+        const T gv = __ldg(Gr + (int64_t)j * ld);
+#pragma unroll
+        for (int q = 0; q < RG; ++q) cfma(acc[q], gv, w[(j - j0) * RG + q]);
+      }
     }
   }
 #pragma unroll
@@ -130,7 +141,7 @@ __device__ __forceinline__ void fwd_task(const SolveTask tk, const int rhs0, con
 #pragma unroll
       for (int q = 0; q < RG; ++q)
         if (rhs0 + q < cx.nrhs) {
-          const T y = cadd(acc[q], w[r * RG + q]);
+          const T y = cadd(acc[q], wr[q]);
           const int64_t o = (int64_t)(rhs0 + q) * cx.n_loc + first + r;
           cx.xf[o] = cmul(y, dinv);
           if (cx.si != PSP_SI_EXTENDED) cx.xb[o] = y;
@@ -215,10 +226,10 @@ __device__ __forceinline__ void fwd_tri_task(const SolveTask tk, const int rhs0,
 
 template <typename T, int RG>
 __global__ void __launch_bounds__(256) k_solve_fwd(const SolveTask* __restrict__ tasks, SolveCtx<T> cx, int R,
-                                                   int phase) {
+                                                   int phase, int chunk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (phase == 0 && cx.si == PSP_SI_NONE) fwd_tri_task<T, RG>(tasks[blockIdx.x], blockIdx.y * RG, cx, smem_raw);
-  else fwd_task<T, RG>(tasks[blockIdx.x], blockIdx.y * RG, cx, R, smem_raw, phase);
+  else fwd_task<T, RG>(tasks[blockIdx.x], blockIdx.y * RG, cx, R, smem_raw, phase, chunk);
 }
 
 // the final write of x_S column c of a front: xb (elimination order) and, for the panel's own
@@ -246,7 +257,7 @@ __device__ __forceinline__ void write_solution(const SolveCtx<T>& cx, const int 
 //   paper's factors, phase 1: x_c = t_c + sum_{c < r < s} inv(L_TL)[r, c] t_r; writes the solution.
 template <typename T, int RG>
 __device__ __forceinline__ void bwd_task(const SolveTask tk, const int rhs0, const SolveCtx<T>& cx,
-                                         unsigned char* smem_raw, const int phase) {
+                                         unsigned char* smem_raw, const int phase, const int chunk) {
   const int sn = tk.sn;
   const int s = cx.sh.s[sn], u = cx.sh.u[sn], ld = s + u;
   const int first = cx.sh.first[sn];
@@ -254,61 +265,67 @@ __device__ __forceinline__ void bwd_task(const SolveTask tk, const int rhs0, con
   const int32_t* sel = cx.sh.struct_elim + cx.sh.struct_ptr[sn];
   const int c0 = tk.r0;
   const bool ext = cx.si == PSP_SI_EXTENDED;
-  // rows of the inner sums kept in shared memory: [lo, hi)
+  // rows of the inner sums: [lo, hi), passed through shared memory in chunks of `chunk` rows
   const int lo = (ext || phase == 1) ? c0 : s;
   const int hi = (ext || phase == 0) ? ld : s;
-  T* y = reinterpret_cast<T*>(smem_raw);   // rows [lo, hi) x RG
-  for (int r = lo + threadIdx.x; r < hi; r += blockDim.x) {
+  T* y = reinterpret_cast<T*>(smem_raw);        // chunk x RG
+  T* sums = y + (int64_t)chunk * RG;            // (r1 - c0) x RG column sums (<= 64 columns)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int e = threadIdx.x; e < (tk.r1 - c0) * RG; e += blockDim.x) sums[e] = CplxTraits<T>::zero();
+  for (int rb = lo; rb < hi; rb += chunk) {
+    const int re = min(rb + chunk, hi);
+    __syncthreads();   // sums initialised / the previous chunk consumed
+    for (int r = rb + threadIdx.x; r < re; r += blockDim.x) {
 #pragma unroll
-    for (int q = 0; q < RG; ++q) {
-      T v = CplxTraits<T>::zero();
-      if (rhs0 + q < cx.nrhs) {
-        const int64_t base = (int64_t)(rhs0 + q) * cx.n_loc;
-        v = (r < s) ? __ldcg(cx.xf + base + first + r) : cneg(__ldcg(cx.xb + base + sel[r - s]));
+      for (int q = 0; q < RG; ++q) {
+        T v = CplxTraits<T>::zero();
+        if (rhs0 + q < cx.nrhs) {
+          const int64_t base = (int64_t)(rhs0 + q) * cx.n_loc;
+          v = (r < s) ? __ldcg(cx.xf + base + first + r) : cneg(__ldcg(cx.xb + base + sel[r - s]));
+        }
+        y[(r - rb) * RG + q] = v;
       }
-      y[(r - lo) * RG + q] = v;
+    }
+    __syncthreads();
+    for (int c = c0 + warp; c < tk.r1; c += nw) {
+      T acc[RG];
+#pragma unroll
+      for (int q = 0; q < RG; ++q) acc[q] = CplxTraits<T>::zero();
+      const T* Gc = G + (int64_t)c * ld;
+      int r = (rb > c + 1 ? rb : c + 1) + lane;
+      for (; r + 7 * 32 < re; r += 8 * 32) {   // eight independent factor loads in flight per lane
+        T gv[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) gv[t] = __ldg(Gc + r + 32 * t);
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+#pragma unroll
+          for (int q = 0; q < RG; ++q) cfma(acc[q], gv[t], y[(r + 32 * t - rb) * RG + q]);
+      }
+      for (; r < re; r += 32) {
+        const T gv = __ldg(Gc + r);
+#pragma unroll
+        for (int q = 0; q < RG; ++q) cfma(acc[q], gv, y[(r - rb) * RG + q]);
+      }
+#pragma unroll
+      for (int q = 0; q < RG; ++q) {
+        for (int off = 16; off > 0; off >>= 1) {
+          acc[q].x += __shfl_xor_sync(0xffffffffu, acc[q].x, off);
+          acc[q].y += __shfl_xor_sync(0xffffffffu, acc[q].y, off);
+        }
+        if (lane == 0) sums[(c - c0) * RG + q] = cadd(sums[(c - c0) * RG + q], acc[q]);
+      }
     }
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int c = c0 + warp; c < tk.r1; c += nw) {
-    T acc[RG];
-#pragma unroll
-    for (int q = 0; q < RG; ++q) acc[q] = CplxTraits<T>::zero();
-    const T* Gc = G + (int64_t)c * ld;
-    int r = (lo > c + 1 ? lo : c + 1) + lane;
-    for (; r + 7 * 32 < hi; r += 8 * 32) {   // eight independent factor loads in flight per lane
-      T gv[8];
-#pragma unroll
-      for (int t = 0; t < 8; ++t) gv[t] = __ldg(Gc + r + 32 * t);
-#pragma unroll
-      for (int t = 0; t < 8; ++t)
-#pragma unroll
-        for (int q = 0; q < RG; ++q) cfma(acc[q], gv[t], y[(r + 32 * t - lo) * RG + q]);
-    }
-    for (; r < hi; r += 32) {
-      const T gv = __ldg(Gc + r);
-#pragma unroll
-      for (int q = 0; q < RG; ++q) cfma(acc[q], gv, y[(r - lo) * RG + q]);
-    }
+  for (int c = c0 + threadIdx.x; c < tk.r1; c += blockDim.x) {
 #pragma unroll
     for (int q = 0; q < RG; ++q) {
-      for (int off = 16; off > 0; off >>= 1) {
-        acc[q].x += __shfl_xor_sync(0xffffffffu, acc[q].x, off);
-        acc[q].y += __shfl_xor_sync(0xffffffffu, acc[q].y, off);
-      }
-    }
-    if (lane == 0) {
-#pragma unroll
-      for (int q = 0; q < RG; ++q) {
-        if (rhs0 + q >= cx.nrhs) continue;
-        const int64_t o = (int64_t)(rhs0 + q) * cx.n_loc + first + c;
-        if (!ext && phase == 0) {
-          cx.xf[o] = cadd(acc[q], __ldcg(cx.xf + o));   // t_c, read and written by this lane only
-        } else {
-          write_solution(cx, first, c, rhs0 + q, cadd(acc[q], y[(c - lo) * RG + q]));
-        }
-      }
+      if (rhs0 + q >= cx.nrhs) continue;
+      const int64_t o = (int64_t)(rhs0 + q) * cx.n_loc + first + c;
+      const T v = cadd(sums[(c - c0) * RG + q], __ldcg(cx.xf + o));   // + xf_c (z_c, or t_c in phase 1)
+      if (!ext && phase == 0) cx.xf[o] = v;                           // t_c: this thread's column only
+      else write_solution(cx, first, c, rhs0 + q, v);
     }
   }
 }
@@ -375,10 +392,11 @@ __device__ __forceinline__ void bwd_tri_task(const SolveTask tk, const int rhs0,
 }
 
 template <typename T, int RG>
-__global__ void __launch_bounds__(256) k_solve_bwd(const SolveTask* __restrict__ tasks, SolveCtx<T> cx, int phase) {
+__global__ void __launch_bounds__(256) k_solve_bwd(const SolveTask* __restrict__ tasks, SolveCtx<T> cx, int phase,
+                                                   int chunk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (phase == 1 && cx.si == PSP_SI_NONE) bwd_tri_task<T, RG>(tasks[blockIdx.x], blockIdx.y * RG, cx, smem_raw);
-  else bwd_task<T, RG>(tasks[blockIdx.x], blockIdx.y * RG, cx, smem_raw, phase);
+  else bwd_task<T, RG>(tasks[blockIdx.x], blockIdx.y * RG, cx, smem_raw, phase, chunk);
 }
 
 // rhs group size so that the shared-memory footprint stays below ~200 KB
@@ -562,9 +580,9 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs<T> a) {
     const bool tri = s_cx.si == PSP_SI_NONE;
     for (int g = 0; g < nrg; ++g) {
       if (dir == 0 && tri) fwd_tri_task<T, RG>(tk, g * RG, s_cx, smem_raw);
-      else if (dir == 0 || dir == kDirUpB) fwd_task<T, RG>(tk, g * RG, s_cx, s_R, smem_raw, dir == 0 ? 0 : 1);
+      else if (dir == 0 || dir == kDirUpB) fwd_task<T, RG>(tk, g * RG, s_cx, s_R, smem_raw, dir == 0 ? 0 : 1, a.chunk);
       else if (dir == kDirDownB && tri) bwd_tri_task<T, RG>(tk, g * RG, s_cx, smem_raw);
-      else bwd_task<T, RG>(tk, g * RG, s_cx, smem_raw, dir == 1 ? 0 : 1);
+      else bwd_task<T, RG>(tk, g * RG, s_cx, smem_raw, dir == 1 ? 0 : 1, a.chunk);
       __syncthreads();
     }
     if (threadIdx.x == 0) {
@@ -579,8 +597,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs<T> a) {
 }
 
 template <typename T, int RG>
-static int sweep_rg(const SweepArgs<T>& args, size_t per_rhs_bytes, int max_per_sm, cudaStream_t st) {
-  const size_t smem = per_rhs_bytes * RG;
+static int sweep_rg(const SweepArgs<T>& args, size_t smem, int max_per_sm, cudaStream_t st) {
   if (cudaFuncSetAttribute(k_sweep<T, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
     return -1;
@@ -603,22 +620,38 @@ static int sweep_rg(const SweepArgs<T>& args, size_t per_rhs_bytes, int max_per_
   return e == cudaSuccess ? 0 : (int)e;
 }
 
-// rhs_group > 0 caps the right-hand sides a CTA carries per pass over a factor block; 0 keeps the
-// group's shared memory within 64 KB so that several CTAs stay resident per SM (a CTA that waits
-// on a dependency then leaves the SM to the others)
+// A CTA carries RG right-hand sides through each pass over a factor block (as many as nrhs, at most 8,
+// or rhs_group when > 0), and the vectors of a task pass through shared memory in chunks sized so
+// that a CTA keeps within kSweepSmem (several CTAs stay resident per SM: a CTA that waits on a
+// dependency leaves the SM to the others).  Substitution tasks (fronts keeping L_TL) hold a front's
+// whole vector, so for them RG shrinks until that fits.
+constexpr size_t kSweepSmem = 64 * 1024;
+
 template <typename T>
-int launch_sweep(const SweepArgs<T>& args, size_t per_rhs_bytes, int max_per_sm, int rhs_group, cudaStream_t st) {
-  int rg = pick_rg<T>(args.cx.nrhs, per_rhs_bytes);
-  if (rhs_group > 0) {
+int launch_sweep(const SweepArgs<T>& args, int smax, int ldmax, int max_per_sm, int rhs_group, cudaStream_t st) {
+  const size_t es = sizeof(T);
+  int rg = 8;
+  while (rg > 1 && rg >= 2 * args.cx.nrhs) rg >>= 1;
+  if (rhs_group > 0)
     while (rg > 1 && rg > rhs_group) rg >>= 1;
+  const int full = (ldmax > smax ? ldmax : smax);
+  int chunk;
+  if (args.cx.si == PSP_SI_NONE) {
+    chunk = full;
+    while (rg > 1 && ((size_t)chunk + 256) * rg * es > 200 * 1024) rg >>= 1;
   } else {
-    while (rg > 1 && per_rhs_bytes * rg > 64 * 1024) rg >>= 1;
+    chunk = (int)((kSweepSmem / (rg * es) - 256) / 256 * 256);
+    if (chunk < 256) chunk = 256;
+    if (chunk >= full) chunk = full;   // one chunk: every task's vector at once
   }
+  SweepArgs<T> a = args;
+  a.chunk = chunk;
+  const size_t smem = ((size_t)chunk + 256) * rg * es;
   switch (rg) {
-    case 8: return sweep_rg<T, 8>(args, per_rhs_bytes, max_per_sm, st);
-    case 4: return sweep_rg<T, 4>(args, per_rhs_bytes, max_per_sm, st);
-    case 2: return sweep_rg<T, 2>(args, per_rhs_bytes, max_per_sm, st);
-    default: return sweep_rg<T, 1>(args, per_rhs_bytes, max_per_sm, st);
+    case 8: return sweep_rg<T, 8>(a, smem, max_per_sm, st);
+    case 4: return sweep_rg<T, 4>(a, smem, max_per_sm, st);
+    case 2: return sweep_rg<T, 2>(a, smem, max_per_sm, st);
+    default: return sweep_rg<T, 1>(a, smem, max_per_sm, st);
   }
 }
 
@@ -631,19 +664,19 @@ static void fwd_rg(const SolveTask* tasks, int ntasks, const SolveCtx<T>& cx, in
     attr_set = true;
   }
   dim3 grid(ntasks, (cx.nrhs + RG - 1) / RG);
-  k_solve_fwd<T, RG><<<grid, 256, smem, st>>>(tasks, cx, R, phase);
+  k_solve_fwd<T, RG><<<grid, 256, smem, st>>>(tasks, cx, R, phase, smax > 0 ? smax : 1);
 }
 
 template <typename T, int RG>
 static void bwd_rg(const SolveTask* tasks, int ntasks, const SolveCtx<T>& cx, int ldmax, int phase, cudaStream_t st) {
-  const size_t smem = (size_t)ldmax * RG * sizeof(T);
+  const size_t smem = ((size_t)ldmax + 64) * RG * sizeof(T);
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_solve_bwd<T, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     attr_set = true;
   }
   dim3 grid(ntasks, (cx.nrhs + RG - 1) / RG);
-  k_solve_bwd<T, RG><<<grid, 256, smem, st>>>(tasks, cx, phase);
+  k_solve_bwd<T, RG><<<grid, 256, smem, st>>>(tasks, cx, phase, ldmax > 0 ? ldmax : 1);
 }
 
 template <typename T>
@@ -662,7 +695,7 @@ void launch_solve_fwd(const SolveTask* tasks, int ntasks, const SolveCtx<T>& cx,
 template <typename T>
 void launch_solve_bwd(const SolveTask* tasks, int ntasks, const SolveCtx<T>& cx, int ldmax, int phase, cudaStream_t st) {
   if (ntasks <= 0) return;
-  const int rg = pick_rg<T>(cx.nrhs, (size_t)ldmax * sizeof(T));
+  const int rg = pick_rg<T>(cx.nrhs, ((size_t)ldmax + 64) * sizeof(T));
   switch (rg) {
     case 8: bwd_rg<T, 8>(tasks, ntasks, cx, ldmax, phase, st); break;
     case 4: bwd_rg<T, 4>(tasks, ntasks, cx, ldmax, phase, st); break;
@@ -675,7 +708,7 @@ template void launch_solve_fwd<double2>(const SolveTask*, int, const SolveCtx<do
 template void launch_solve_fwd<float2>(const SolveTask*, int, const SolveCtx<float2>&, int, int, int, cudaStream_t);
 template void launch_solve_bwd<double2>(const SolveTask*, int, const SolveCtx<double2>&, int, int, cudaStream_t);
 template void launch_solve_bwd<float2>(const SolveTask*, int, const SolveCtx<float2>&, int, int, cudaStream_t);
-template int launch_sweep<double2>(const SweepArgs<double2>&, size_t, int, int, cudaStream_t);
-template int launch_sweep<float2>(const SweepArgs<float2>&, size_t, int, int, cudaStream_t);
+template int launch_sweep<double2>(const SweepArgs<double2>&, int, int, int, int, cudaStream_t);
+template int launch_sweep<float2>(const SweepArgs<float2>&, int, int, int, int, cudaStream_t);
 
 }  // namespace psp

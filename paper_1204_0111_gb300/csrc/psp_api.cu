@@ -290,7 +290,7 @@ struct psp_ctx_s {
   SweepPlan plans[3];              // 0: Alg. 1.5 over the handle's panels; 1: its forward part; 2: its backward part
   DevBuf d_sweep_panels, d_sweep_sync;
   size_t sweep_sync_words = 0;     // counters of the largest plan (one sweep runs at a time per handle)
-  size_t sweep_rhs_bytes = 0;      // shared memory per right-hand side of the widest level
+  int sweep_smax = 0, sweep_ldmax = 0;   // the widest front's s and s + u (vector staging of the sweep)
   // block of panels [range_begin, range_end) this handle factors and sweeps (all of them unless the
   // handle is one block of a multi-GPU sweep)
   int range_begin = 0, range_count = 0, range_end = 0;
@@ -1103,7 +1103,6 @@ static void plan_solve(psp_ctx_s* X, cudaStream_t st) {
 
   // per shape: tasks per front, up and down
   std::vector<int> front_base(X->shapes.size() + 1, 0), ntask_up, ntask_down, ntask_upA, ntask_downA;
-  size_t per_rhs = 0;
   std::vector<double> shape_entries(X->shapes.size(), 0.0), shape_vec(X->shapes.size(), 0.0);
   std::vector<int> shape_tasks(X->shapes.size(), 0);
   for (size_t si = 0; si < X->shapes.size(); ++si) {
@@ -1118,7 +1117,6 @@ static void plan_solve(psp_ctx_s* X, cudaStream_t st) {
       for (int t = 0; t < P.nbwd; ++t) ntask_downA[front_base[si] + tasks[P.bwd_off + t].sn]++;
       for (int t = 0; t < P.nfwdB; ++t) ntask_up[front_base[si] + tasks[P.fwdB_off + t].sn]++;
       for (int t = 0; t < P.nbwdB; ++t) ntask_down[front_base[si] + tasks[P.bwdB_off + t].sn]++;
-      per_rhs = std::max(per_rhs, (size_t)std::max(P.smax + 256, P.ldmax));
       shape_entries[si] += 2 * P.entries;
       shape_vec[si] += 2 * P.vec;
       shape_tasks[si] += P.nfwd + P.nbwd + P.nfwdB + P.nbwdB;
@@ -1129,7 +1127,13 @@ static void plan_solve(psp_ctx_s* X, cudaStream_t st) {
     ntask_down[f] += ntask_downA[f];
   }
   front_base[X->shapes.size()] = (int)ntask_up.size();
-  X->sweep_rhs_bytes = per_rhs;
+  X->sweep_smax = 0;
+  X->sweep_ldmax = 0;
+  for (const auto& sp : X->splan)
+    for (const auto& P : sp) {
+      X->sweep_smax = std::max(X->sweep_smax, P.smax);
+      X->sweep_ldmax = std::max(X->sweep_ldmax, P.ldmax);
+    }
 
   // Persistent sweep plans: panel solves in Alg. 1.5 order and one task queue in topological order.
   // Plan 0 is the whole Alg. 1.5 over the handle's panels; plans 1 and 2 are its forward and its
@@ -1350,7 +1354,7 @@ static void apply_core(psp_ctx_s* X, double2* u, int nrhs, T* xf, T* xb, T* upd,
       PSP_CK(cudaMemsetAsync(sync, 0, words * 4, st));
       const double es = sizeof(T);
       X->stats.run("k_sweep", st, 1, 8.0 * SP.entries * nrhs, SP.entries * es + SP.vec * es * nrhs,
-                   [&] { rc = launch_sweep<T>(sa, X->sweep_rhs_bytes * sizeof(T), X->sweep_ctas_per_sm, X->sweep_rhs_group, st); });
+                   [&] { rc = launch_sweep<T>(sa, X->sweep_smax, X->sweep_ldmax, X->sweep_ctas_per_sm, X->sweep_rhs_group, st); });
       if (rc > 0) throw Error{PSP_ERR_CUDA, std::string("sweep launch: ") + cudaGetErrorString((cudaError_t)rc)};
     }
     if (rc != 0) {

@@ -305,10 +305,12 @@ struct SweepArgs {
   int nprobs;
   const ProblemSweep* probs;    // per problem; cx's vectors and work vectors are offset per problem
   const int* step_prev;         // per step: the step it follows (-1: none); nullptr: step - 1
+  int chunk;                    // vector entries a task stages in shared memory at a time (set by launch_sweep)
 };
-// returns 0 on success, -1 when a cooperative launch is not possible, else a cudaError_t
+// returns 0 on success, -1 when a cooperative launch is not possible, else a cudaError_t; smax / ldmax:
+// the widest front's s and s + u
 template <typename T>
-int launch_sweep(const SweepArgs<T>& args, size_t per_rhs_bytes, int max_per_sm, int rhs_group, cudaStream_t st);
+int launch_sweep(const SweepArgs<T>& args, int smax, int ldmax, int max_per_sm, int rhs_group, cudaStream_t st);
 
 // ---- GMRES helpers (complex128) ----
 // A block of vectors holds ncol columns (right-hand sides, and problems of a batch); column c of
