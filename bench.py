@@ -573,16 +573,20 @@ def gpu_main(a):
             dist.barrier()
 
     alu = measure_alu_peaks(dev)
-    # sweep schedule from the library's autotuner, once per precision, before any timed work
-    tuning = {}
+    # the library's autotuners, once per precision, before any timed work: the factor form and tensor-core
+    # threshold for the expected number of applications (psp_tune_setup), then the sweep schedule
+    tuning, setup_tuning = {}, {}
     for prec in () if a.no_tune else ("c128",) + (() if a.no_mixed else ("c64",)):
         P = psp.SweepingPreconditioner(c_dev, w.h, w.omega, w.gamma, w.panel_depth, pad=w.pad, leaf=w.leaf,
                                        pml_C=w.pml_C, alpha=w.alpha, precision=prec)
+        ts = P.tune_setup(nrhs=nrhs, expected_applies=a.expected_applies)
         t = P.tune_sweep(nrhs=nrhs, reps=3)
         P.close()
         tuning[prec] = t
+        setup_tuning[prec] = ts
         sched[prec] = {"sweep_level_tasks": t["sweep_level_tasks"], "sweep_ctas_per_sm": t["sweep_ctas_per_sm"],
-                       "sweep_rhs_group": t["sweep_rhs_group"]}
+                       "sweep_rhs_group": t["sweep_rhs_group"], "selective_inversion": ts["selective_inversion"],
+                       "tc_min_dim": ts["tc_min_dim"] if prec == "c64" else 0}
     for _ in range(a.warmup):
         step()
     torch.cuda.synchronize()
@@ -681,6 +685,35 @@ def gpu_main(a):
                  "host_setup_ms": mhost, "kernels": kernel_table(mkern)}
     roofs = rooflines({k: v for k, v in full_st.items() if not k.startswith("host:")}, mfull, alu)
 
+    # setup and application of each factor form (selective inversion, §2.2 and Table 2's trade)
+    si_forms = {}
+    if not a.no_mixed:
+        for prec in ("c128", "c64"):
+            for form in ("extended", "paper", "none"):
+                kw = {k: v for k, v in sched.get(prec, {}).items() if k != "selective_inversion"}
+                P = psp.SweepingPreconditioner(c_dev, w.h, w.omega, w.gamma, w.panel_depth, pad=w.pad, leaf=w.leaf,
+                                               pml_C=w.pml_C, alpha=w.alpha, precision=prec, collect_stats=1,
+                                               selective_inversion=form, **kw)
+                uu = torch.empty_like(f_dev)
+                P.apply(f_dev, uu)
+                P.stats(reset=True)
+                for _ in range(3):
+                    P.apply(f_dev, uu)
+                st = {k: v for k, v in P.stats().items() if not k.startswith("host:")}
+                fb = P.info()["factor_bytes"]
+                P.close()
+                P = psp.SweepingPreconditioner(c_dev, w.h, w.omega, w.gamma, w.panel_depth, pad=w.pad, leaf=w.leaf,
+                                               pml_C=w.pml_C, alpha=w.alpha, precision=prec, collect_stats=2,
+                                               selective_inversion=form, **kw)
+                su = {k: v for k, v in P.stats().items() if k in SETUP_KERNELS}
+                P.close()
+                sw = st.get("k_sweep", {"total_ms": 0.0})
+                si_forms[f"{prec}/{form}"] = {
+                    "setup_kernel_ms": sum(v["total_ms"] for v in su.values()),
+                    "setup_algorithmic_tflop": sum(v["flops"] for v in su.values()) / 1e12,
+                    "setup_si_tflop": sum(v["extra_flops"] for v in su.values()) / 1e12,
+                    "apply_ms": sw["total_ms"] / 3, "factor_bytes": fb}
+
     # the other configurations (rank 0 of a single-GPU run only)
     extras = {}
     if not a.no_extra and world == 1:
@@ -708,7 +741,9 @@ def gpu_main(a):
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": config_dict(w, nrhs, {"parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches // a.steps,
-                "clocks": clk, "peaks": alu, "rooflines": roofs, "detail": dict(detail, sweep_tuning=tuning),
+                "clocks": clk, "peaks": alu, "rooflines": roofs,
+                "detail": dict(detail, sweep_tuning=tuning, setup_tuning=setup_tuning, chosen=sched),
+                "si_forms": si_forms,
                 "mixed": mixed}
         line.update(extras)
         print(json.dumps(line))
@@ -882,6 +917,8 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="skip the sweep autotuner (library defaults); keeps the "
                     "first timed step the first launches of the run, for launch-list captures")
     ap.add_argument("--ref-iters", type=int, default=18, help="GMRES iterations assumed by the reference arm")
+    ap.add_argument("--expected-applies", type=int, default=18, help="applications per solve the setup autotuner "
+                    "weighs the setup against (lens100: 18 GMRES iterations, one application each)")
     ap.add_argument("--n", type=int, default=100, help="grid points per axis (100 = the benchmark workload; "
                     "smaller sizes are for profiling captures)")
     ap.add_argument("--workload", choices=["lens", "batch16"], default="lens",

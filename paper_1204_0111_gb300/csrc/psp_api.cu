@@ -694,8 +694,10 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
       for (int f = 0; f < nf; ++f) {
         const auto& ft = fronts[f0 + f];
         if (ft.s <= o) continue;
+        // rows below the diagonal block: the rest of F_TL, and without inversion all of F_BL too (its
+        // rows start at s, which the last block's o + nb may pass)
         const int rend = si == PSP_SI_NONE ? ft.s + ft.u : ft.s;
-        for (int r = o + nb; r < rend; r += 64) ctasks.push_back({f, r, std::min(r + 64, rend)});
+        for (int r = std::min(o + nb, ft.s); r < rend; r += 64) ctasks.push_back({f, r, std::min(r + 64, rend)});
       }
       Launch lr{PRIGHT, f0, pr0, (int)(ctasks.size() - pr0), kb};
       for (int64_t t = pr0; t < (int64_t)ctasks.size(); ++t) {
