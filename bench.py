@@ -558,7 +558,10 @@ def gpu_main(a):
 
     sched = {}
 
-    def step(precision="c128", stats=0):
+    main_prec = a.precision
+
+    def step(precision=None, stats=0):
+        precision = precision or main_prec
         P = psp.SweepingPreconditioner(c_dev, w.h, w.omega, w.gamma, w.panel_depth, pad=w.pad, leaf=w.leaf,
                                        pml_C=w.pml_C, alpha=w.alpha, precision=precision, collect_stats=stats,
                                        **sched.get(precision, {}))
@@ -572,11 +575,11 @@ def gpu_main(a):
         if world > 1:
             dist.barrier()
 
-    alu = measure_alu_peaks(dev)
+    alu = {} if a.no_peaks else measure_alu_peaks(dev)
     # the library's autotuners, once per precision, before any timed work: the factor form and tensor-core
     # threshold for the expected number of applications (psp_tune_setup), then the sweep schedule
     tuning, setup_tuning = {}, {}
-    for prec in () if a.no_tune else ("c128",) + (() if a.no_mixed else ("c64",)):
+    for prec in () if a.no_tune else (main_prec,) + (() if a.no_mixed or main_prec == "c64" else ("c64",)):
         P = psp.SweepingPreconditioner(c_dev, w.h, w.omega, w.gamma, w.panel_depth, pad=w.pad, leaf=w.leaf,
                                        pml_C=w.pml_C, alpha=w.alpha, precision=prec)
         ts = P.tune_setup(nrhs=nrhs, expected_applies=a.expected_applies)
@@ -624,24 +627,25 @@ def gpu_main(a):
     c_pin = torch.from_numpy(w.c).pin_memory()
     f_pin = torch.from_numpy(f_host).pin_memory()
     u_pin = torch.zeros_like(f_pin).pin_memory()
-    e2e_steps = max(1, min(a.steps, 5))
+    e2e_steps = 0 if a.no_e2e else max(1, min(a.steps, 5))
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         P = psp.SweepingPreconditioner(c_pin, w.h, w.omega, w.gamma, w.panel_depth, pad=w.pad, leaf=w.leaf,
-                                       pml_C=w.pml_C, alpha=w.alpha, **sched.get("c128", {}))
+                                       pml_C=w.pml_C, alpha=w.alpha, precision=main_prec,
+                                       **sched.get(main_prec, {}))
         P.solve(f_pin, u_pin, tol=w.tol, k=w.k, maxit=400)
         P.close()
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    e2e = {"value": job_rate(world, e2e_steps, max_over_ranks(t1 - t0, dev)), "unit": UNIT, "steps": e2e_steps,
-           "h2d_bytes_per_step": int(c_pin.numel() * 8 + f_pin.numel() * 16),
-           "d2h_bytes_per_step": int(u_pin.numel() * 16)}
+    e2e = None if a.no_e2e else {
+        "value": job_rate(world, e2e_steps, max_over_ranks(t1 - t0, dev)), "unit": UNIT, "steps": e2e_steps,
+        "h2d_bytes_per_step": int(c_pin.numel() * 8 + f_pin.numel() * 16), "d2h_bytes_per_step": int(u_pin.numel() * 16)}
 
     # mixed precision (complex64 fronts and sweeps, complex128 GMRES) on the same workload
     mixed, mfull = None, None
-    if not a.no_mixed:
+    if not a.no_mixed and main_prec == "c128":
         step("c64")
         torch.cuda.synchronize()
         m0 = torch.cuda.Event(enable_timing=True)
@@ -687,7 +691,7 @@ def gpu_main(a):
 
     # setup and application of each factor form (selective inversion, §2.2 and Table 2's trade)
     si_forms = {}
-    if not a.no_mixed:
+    if not a.no_mixed and main_prec == "c128":
         for prec in ("c128", "c64"):
             for form in ("extended", "paper", "none"):
                 kw = {k: v for k, v in sched.get(prec, {}).items() if k != "selective_inversion"}
@@ -738,7 +742,8 @@ def gpu_main(a):
             cpu = oracle_baseline(detail["gmres_iters"], w.k)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "vs_baseline": None, "dtype": "f64" if main_prec == "c128" else "c64 fronts/sweeps, f64 GMRES",
+                "data": "synthetic",
                 "config": config_dict(w, nrhs, {"parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches // a.steps,
                 "clocks": clk, "peaks": alu, "rooflines": roofs,
@@ -914,6 +919,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the salt256, layered200 and batch16 objects")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling captures)")
+    ap.add_argument("--no-peaks", action="store_true", help="skip the FP64/FP32 GEMM peak measurement (profiling "
+                    "captures; the derived peaks are used)")
+    ap.add_argument("--precision", choices=["c128", "c64"], default="c128",
+                    help="precision of the timed lens path (c128 = the benchmark; c64 for profiling captures)")
     ap.add_argument("--no-tune", action="store_true", help="skip the sweep autotuner (library defaults); keeps the "
                     "first timed step the first launches of the run, for launch-list captures")
     ap.add_argument("--ref-iters", type=int, default=18, help="GMRES iterations assumed by the reference arm")

@@ -57,6 +57,20 @@ __device__ __forceinline__ bool shared_gather(const SolveCtx<T>& cx, int s, int 
   return (cx.si == PSP_SI_EXTENDED ? s + u : s) >= 4 * R;
 }
 
+// Down the tree, a front with at least four column tasks (and a struct) has -x_U gathered once, by its
+// first task, into its own update-vector slot (free once the up pass has finished); its other tasks
+// read it from there, contiguous, instead of through the struct indices.
+template <typename T>
+__device__ __forceinline__ void gather_struct(const SolveCtx<T>& cx, int sn) {
+  const int u = cx.sh.u[sn];
+  const int32_t* sel = cx.sh.struct_elim + cx.sh.struct_ptr[sn];
+  const int64_t o = cx.sh.upd_off[sn];
+  for (int e = threadIdx.x; e < u * cx.nrhs; e += blockDim.x) {
+    const int q = e / u, r = e - q * u;
+    cx.upd[(int64_t)q * cx.upd_ld + o + r] = cneg(__ldcg(cx.xb + (int64_t)q * cx.n_loc + sel[r]));
+  }
+}
+
 // the whole w_S of front sn, every right-hand side, into wbuf (elimination order, ld n_loc)
 template <typename T>
 __device__ __forceinline__ void gather_front(const SolveCtx<T>& cx, int sn) {
@@ -297,7 +311,8 @@ __device__ __forceinline__ void write_solution(const SolveCtx<T>& cx, const int 
 //   paper's factors, phase 1: x_c = t_c + sum_{c < r < s} inv(L_TL)[r, c] t_r; writes the solution.
 template <typename T, int RG>
 __device__ __forceinline__ void bwd_task(const SolveTask tk, const int rhs0, const SolveCtx<T>& cx,
-                                         unsigned char* smem_raw, const int phase, const int chunk) {
+                                         unsigned char* smem_raw, const int phase, const int chunk,
+                                         const bool from_buf = false) {
   const int sn = tk.sn;
   const int s = cx.sh.s[sn], u = cx.sh.u[sn], ld = s + u;
   const int first = cx.sh.first[sn];
@@ -321,7 +336,9 @@ __device__ __forceinline__ void bwd_task(const SolveTask tk, const int rhs0, con
         T v = CplxTraits<T>::zero();
         if (rhs0 + q < cx.nrhs) {
           const int64_t base = (int64_t)(rhs0 + q) * cx.n_loc;
-          v = (r < s) ? __ldcg(cx.xf + base + first + r) : cneg(__ldcg(cx.xb + base + sel[r - s]));
+          if (r < s) v = __ldcg(cx.xf + base + first + r);
+          else if (from_buf) v = __ldcg(cx.upd + (int64_t)(rhs0 + q) * cx.upd_ld + cx.sh.upd_off[sn] + (r - s));
+          else v = cneg(__ldcg(cx.xb + base + sel[r - s]));
         }
         y[(r - rb) * RG + q] = v;
       }
@@ -596,9 +613,12 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs<T> a) {
       const unsigned* down = a.done_down + c_sfb;
       bool ok = true;
       const bool shared = ce.dir == 0 && shared_gather(cx, cx.sh.s[ctk.sn], cx.sh.u[ctk.sn], ce.R);
-      s_shared = shared;
+      const bool sdown = ce.dir == 1 && cx.sh.u[ctk.sn] > 0 && a.ntask_downA[c_fb + ctk.sn] >= 4;
+      s_shared = shared || sdown;
       if (shared && ctk.r0 > 0) {   // the front's first task gathers w_S for all of its tasks
         ok = wait_count(a.gathered + c_sfb + ctk.sn, 1u, a.status, a.sticky);
+      } else if (sdown && ctk.r0 > 0) {   // the front's first down task gathers -x_U for all of its tasks
+        ok = wait_count(a.gathered + c_sfb + ctk.sn, 2u, a.status, a.sticky);
       } else if (ce.dir == 0) {
         const int prev = a.step_prev ? a.step_prev[ce.step] : ce.step - 1;
         if (prev >= 0) ok = wait_count(a.step_done + prev, (unsigned)a.step_tasks[prev], a.status, a.sticky);
@@ -625,11 +645,12 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs<T> a) {
     const bool tri = s_cx.si == PSP_SI_NONE;
     const bool shared = s_shared;
     if (shared && tk.r0 == 0) {
-      gather_front(s_cx, tk.sn);
+      if (dir == 0) gather_front(s_cx, tk.sn);
+      else gather_struct(s_cx, tk.sn);
       __syncthreads();
       if (threadIdx.x == 0) {
         __threadfence();
-        atomicExch(a.gathered + c_sfb + tk.sn, 1u);
+        atomicExch(a.gathered + c_sfb + tk.sn, dir == 0 ? 1u : 2u);
       }
     }
     for (int g = 0; g < nrg; ++g) {
@@ -637,7 +658,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs<T> a) {
       else if (dir == 0 || dir == kDirUpB)
         fwd_task<T, RG>(tk, g * RG, s_cx, s_R, smem_raw, dir == 0 ? 0 : 1, a.chunk, shared);
       else if (dir == kDirDownB && tri) bwd_tri_task<T, RG>(tk, g * RG, s_cx, smem_raw);
-      else bwd_task<T, RG>(tk, g * RG, s_cx, smem_raw, dir == 1 ? 0 : 1, a.chunk);
+      else bwd_task<T, RG>(tk, g * RG, s_cx, smem_raw, dir == 1 ? 0 : 1, a.chunk, shared && dir == 1);
       __syncthreads();
     }
     if (threadIdx.x == 0) {
