@@ -227,7 +227,7 @@ psp_status psp_apply(psp_handle h, const double* rhs, double* out, int nrhs, voi
  * loop timed as one stream-ordered region in which a cudaMalloc would synchronise the device.
  * psp_apply grows its work vectors on demand; this call never calls cudaMalloc, cudaFree or any
  * other allocating routine.
- *  - Work vectors (three box vectors per panel and the fronts' update vectors, per right-hand side)
+ *  - Work vectors (two box vectors per panel and the fronts' update vectors, per right-hand side)
  *    live in one file-scope device array of 16 MiB that every GPU context loading the library
  *    reserves until the process exits.  When a problem needs more for the given nrhs the call
  *    returns PSP_ERR_ARG with the size it needs; use psp_apply then.

@@ -15,9 +15,6 @@
 
 namespace psp {
 
-// The box node id is x + nx y + nx ny k with k = 0 the first pad plane; the global index of a node
-// of the panel's own planes is then node + nx ny (z0 - lead), and only nodes of the panel's first
-// (forward sweep) or last (backward sweep) plane need their x and y, for the plane coupling.
 template <typename T>
 __device__ __forceinline__ T input_value(const SolveCtx<T>& cx, int node, int q) {
   const int nx = cx.sh.nx;
@@ -48,47 +45,6 @@ __device__ __forceinline__ T input_value(const SolveCtx<T>& cx, int node, int q)
   return CplxTraits<T>::from(v);
 }
 
-// A front whose up-the-tree tasks are many (its rows, or for factors keeping L_BL its S rows, span at
-// least four tasks of R rows) has its w_S gathered once, by its first task, into cx.wbuf; its other
-// tasks wait for that and read w_S from there instead of gathering it again.
-template <typename T>
-__device__ __forceinline__ bool shared_gather(const SolveCtx<T>& cx, int s, int u, int R) {
-  if (cx.si == PSP_SI_NONE) return false;
-  return (cx.si == PSP_SI_EXTENDED ? s + u : s) >= 4 * R;
-}
-
-// Down the tree, a front with at least four column tasks (and a struct) has -x_U gathered once, by its
-// first task, into its own update-vector slot (free once the up pass has finished); its other tasks
-// read it from there, contiguous, instead of through the struct indices.
-template <typename T>
-__device__ __forceinline__ void gather_struct(const SolveCtx<T>& cx, int sn) {
-  const int u = cx.sh.u[sn];
-  const int32_t* sel = cx.sh.struct_elim + cx.sh.struct_ptr[sn];
-  const int64_t o = cx.sh.upd_off[sn];
-  for (int e = threadIdx.x; e < u * cx.nrhs; e += blockDim.x) {
-    const int q = e / u, r = e - q * u;
-    cx.upd[(int64_t)q * cx.upd_ld + o + r] = cneg(__ldcg(cx.xb + (int64_t)q * cx.n_loc + sel[r]));
-  }
-}
-
-// the whole w_S of front sn, every right-hand side, into wbuf (elimination order, ld n_loc)
-template <typename T>
-__device__ __forceinline__ void gather_front(const SolveCtx<T>& cx, int sn) {
-  const int s = cx.sh.s[sn], first = cx.sh.first[sn];
-  const int32_t* pull = cx.sh.pull + 2 * cx.sh.pull_ptr[sn];
-  for (int e = threadIdx.x; e < s * cx.nrhs; e += blockDim.x) {
-    const int q = e / s, p = e - q * s;
-    T v = input_value(cx, cx.sh.order[first + p], q);
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      const int32_t o = pull[2 * p + t];
-      if (o < 0) break;
-      v = cadd(v, __ldcg(cx.upd + (int64_t)q * cx.upd_ld + o));
-    }
-    cx.wbuf[(int64_t)q * cx.n_loc + first + p] = v;
-  }
-}
-
 template <typename T, int RG>
 __device__ __forceinline__ void pull_add(const SolveCtx<T>& cx, const int32_t* pl, int rhs0, T* out) {
 #pragma unroll
@@ -108,8 +64,7 @@ __device__ __forceinline__ void pull_add(const SolveCtx<T>& cx, const int32_t* p
 // phase 1 (factors keeping L_BL) takes y_S from xb and writes the update w_U - L_BL y_S of rows r >= s.
 template <typename T, int RG>
 __device__ __forceinline__ void fwd_task(const SolveTask tk, const int rhs0, const SolveCtx<T>& cx, const int R,
-                                         unsigned char* smem_raw, const int phase, const int chunk,
-                                         const bool from_buf = false) {
+                                         unsigned char* smem_raw, const int phase, const int chunk) {
   const int sn = tk.sn;
   const int s = cx.sh.s[sn], u = cx.sh.u[sn], ld = s + u;
   const int first = cx.sh.first[sn];
@@ -132,15 +87,7 @@ __device__ __forceinline__ void fwd_task(const SolveTask tk, const int rhs0, con
   for (int j0 = 0; j0 < jend; j0 += chunk) {
     const int j1 = min(j0 + chunk, jend);
     if (j0 > 0) __syncthreads();   // the previous chunk is consumed
-    if (phase == 0 && from_buf) {
-      // w_S gathered once for the front (shared_gather)
-      const int n = j1 - j0;
-      for (int e = threadIdx.x; e < n * RG; e += blockDim.x) {
-        const int q = e / n, p = j0 + (e - q * n);   // consecutive threads: consecutive entries
-        w[(p - j0) * RG + q] =
-            (rhs0 + q < cx.nrhs) ? __ldcg(cx.wbuf + (int64_t)(rhs0 + q) * cx.n_loc + first + p) : CplxTraits<T>::zero();
-      }
-    } else if (phase == 0) {
+    if (phase == 0) {
       // w_S = (zero-extended input) + children's updates
       for (int p = j0 + threadIdx.x; p < j1; p += blockDim.x) {
         const int node = cx.sh.order[first + p];
@@ -311,8 +258,7 @@ __device__ __forceinline__ void write_solution(const SolveCtx<T>& cx, const int 
 //   paper's factors, phase 1: x_c = t_c + sum_{c < r < s} inv(L_TL)[r, c] t_r; writes the solution.
 template <typename T, int RG>
 __device__ __forceinline__ void bwd_task(const SolveTask tk, const int rhs0, const SolveCtx<T>& cx,
-                                         unsigned char* smem_raw, const int phase, const int chunk,
-                                         const bool from_buf = false) {
+                                         unsigned char* smem_raw, const int phase, const int chunk) {
   const int sn = tk.sn;
   const int s = cx.sh.s[sn], u = cx.sh.u[sn], ld = s + u;
   const int first = cx.sh.first[sn];
@@ -336,9 +282,7 @@ __device__ __forceinline__ void bwd_task(const SolveTask tk, const int rhs0, con
         T v = CplxTraits<T>::zero();
         if (rhs0 + q < cx.nrhs) {
           const int64_t base = (int64_t)(rhs0 + q) * cx.n_loc;
-          if (r < s) v = __ldcg(cx.xf + base + first + r);
-          else if (from_buf) v = __ldcg(cx.upd + (int64_t)(rhs0 + q) * cx.upd_ld + cx.sh.upd_off[sn] + (r - s));
-          else v = cneg(__ldcg(cx.xb + base + sel[r - s]));
+          v = (r < s) ? __ldcg(cx.xf + base + first + r) : cneg(__ldcg(cx.xb + base + sel[r - s]));
         }
         y[(r - rb) * RG + q] = v;
       }
@@ -532,7 +476,7 @@ constexpr int kSweepThreads = 256;
 template <typename T, int RG>
 __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int s_idx, s_next, s_ok, s_dir, s_R, s_shared;
+  __shared__ int s_idx, s_next, s_ok, s_dir, s_R;
   __shared__ SolveTask s_tk;
   __shared__ SolveCtx<T> s_cx;      // this task's panel solve, filled by thread 0
   __shared__ ShapeDev s_shape[kMaxSweepShapes];
@@ -598,7 +542,6 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs<T> a) {
         cx.inv_h2 = pr.inv_h2;
         cx.xf = a.cx.xf + (int64_t)sp.prob * a.cx.n_loc * a.cx.nrhs;
         cx.xb = a.cx.xb + (int64_t)sp.prob * a.cx.n_loc * a.cx.nrhs;
-        cx.wbuf = a.cx.wbuf + (int64_t)sp.prob * a.cx.n_loc * a.cx.nrhs;
         cx.upd = a.cx.upd + (int64_t)sp.prob * a.cx.upd_ld * a.cx.nrhs;
       }
       s_tk = ctk;
@@ -612,14 +555,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs<T> a) {
       const unsigned* up = a.done_up + c_sfb;
       const unsigned* down = a.done_down + c_sfb;
       bool ok = true;
-      const bool shared = ce.dir == 0 && shared_gather(cx, cx.sh.s[ctk.sn], cx.sh.u[ctk.sn], ce.R);
-      const bool sdown = ce.dir == 1 && cx.sh.u[ctk.sn] > 0 && a.ntask_downA[c_fb + ctk.sn] >= 4;
-      s_shared = shared || sdown;
-      if (shared && ctk.r0 > 0) {   // the front's first task gathers w_S for all of its tasks
-        ok = wait_count(a.gathered + c_sfb + ctk.sn, 1u, a.status, a.sticky);
-      } else if (sdown && ctk.r0 > 0) {   // the front's first down task gathers -x_U for all of its tasks
-        ok = wait_count(a.gathered + c_sfb + ctk.sn, 2u, a.status, a.sticky);
-      } else if (ce.dir == 0) {
+      if (ce.dir == 0) {
         const int prev = a.step_prev ? a.step_prev[ce.step] : ce.step - 1;
         if (prev >= 0) ok = wait_count(a.step_done + prev, (unsigned)a.step_tasks[prev], a.status, a.sticky);
         for (int c = cx.sh.child_ptr[ctk.sn]; ok && c < cx.sh.child_ptr[ctk.sn + 1]; ++c) {
@@ -643,22 +579,11 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs<T> a) {
     const SolveTask tk = s_tk;
     const int dir = s_dir;
     const bool tri = s_cx.si == PSP_SI_NONE;
-    const bool shared = s_shared;
-    if (shared && tk.r0 == 0) {
-      if (dir == 0) gather_front(s_cx, tk.sn);
-      else gather_struct(s_cx, tk.sn);
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        __threadfence();
-        atomicExch(a.gathered + c_sfb + tk.sn, dir == 0 ? 1u : 2u);
-      }
-    }
     for (int g = 0; g < nrg; ++g) {
       if (dir == 0 && tri) fwd_tri_task<T, RG>(tk, g * RG, s_cx, smem_raw);
-      else if (dir == 0 || dir == kDirUpB)
-        fwd_task<T, RG>(tk, g * RG, s_cx, s_R, smem_raw, dir == 0 ? 0 : 1, a.chunk, shared);
+      else if (dir == 0 || dir == kDirUpB) fwd_task<T, RG>(tk, g * RG, s_cx, s_R, smem_raw, dir == 0 ? 0 : 1, a.chunk);
       else if (dir == kDirDownB && tri) bwd_tri_task<T, RG>(tk, g * RG, s_cx, smem_raw);
-      else bwd_task<T, RG>(tk, g * RG, s_cx, smem_raw, dir == 1 ? 0 : 1, a.chunk, shared && dir == 1);
+      else bwd_task<T, RG>(tk, g * RG, s_cx, smem_raw, dir == 1 ? 0 : 1, a.chunk);
       __syncthreads();
     }
     if (threadIdx.x == 0) {

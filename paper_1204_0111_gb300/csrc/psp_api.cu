@@ -297,7 +297,7 @@ struct psp_ctx_s {
   bool partial = false;
   int64_t max_nloc = 0, max_upd = 0;
   // apply workspaces
-  DevBuf ws_xf, ws_xb, ws_upd, ws_w;
+  DevBuf ws_xf, ws_xb, ws_upd;
   int ws_nrhs = 0;
   DevBuf stage_in, stage_out;
   DevBuf d_status;
@@ -1217,9 +1217,8 @@ static void plan_solve(psp_ctx_s* X, cudaStream_t st) {
     meta.insert(meta.end(), step_prev.begin(), step_prev.end());
     upload_async(SP.meta, meta, st);
     SP.nfront_steps = step_front[steps.size()];
-    // counters zeroed before every sweep: head | status[4] | step_done[nsteps] | done_up | done_down |
-    // gathered
-    sync_words = std::max(sync_words, 1 + 4 + steps.size() + 3 * (size_t)SP.nfront_steps);
+    // counters zeroed before every sweep: head | status[4] | step_done[nsteps] | done_up | done_down
+    sync_words = std::max(sync_words, 1 + 4 + steps.size() + 2 * (size_t)SP.nfront_steps);
   }
   std::vector<ProblemSweep> pss;
   for (const auto& pr : X->probs) {
@@ -1248,7 +1247,6 @@ static void ensure_apply_ws(psp_ctx_s* X, int nrhs) {
   X->ws_xf.alloc((size_t)X->max_nloc * nrhs * np * sizeof(T));
   X->ws_xb.alloc((size_t)X->max_nloc * nrhs * np * sizeof(T));
   X->ws_upd.alloc((size_t)X->max_upd * nrhs * np * sizeof(T));
-  X->ws_w.alloc((size_t)X->max_nloc * nrhs * np * sizeof(T));
   X->ws_nrhs = nrhs;
 }
 
@@ -1256,7 +1254,7 @@ static void ensure_apply_ws(psp_ctx_s* X, int nrhs) {
 // device block u (N x nrhs, in place), with the box and update-vector work vectors given by the
 // caller.  `timed` allows CUDA-event timing of the launches.
 template <typename T>
-static void apply_core(psp_ctx_s* X, double2* u, int nrhs, T* xf, T* xb, T* upd, T* wb, bool timed, cudaStream_t st,
+static void apply_core(psp_ctx_s* X, double2* u, int nrhs, T* xf, T* xb, T* upd, bool timed, cudaStream_t st,
                        int plan_index = 0) {
   const psp_ctx_s::SweepPlan& SP = X->plans[plan_index];
   SolveCtx<T> cx{};
@@ -1267,7 +1265,6 @@ static void apply_core(psp_ctx_s* X, double2* u, int nrhs, T* xf, T* xb, T* upd,
     cx.xf = xf + (int64_t)q * X->max_nloc * nrhs;
     cx.xb = xb + (int64_t)q * X->max_nloc * nrhs;
     cx.upd = upd + (int64_t)q * X->max_upd * nrhs;
-    cx.wbuf = wb + (int64_t)q * X->max_nloc * nrhs;
     cx.u = u + pr.off1 * nrhs;
     cx.N = pr.N;
     cx.nz = pr.nz;
@@ -1285,7 +1282,6 @@ static void apply_core(psp_ctx_s* X, double2* u, int nrhs, T* xf, T* xb, T* upd,
   cx.xf = xf;
   cx.xb = xb;
   cx.upd = upd;
-  cx.wbuf = wb;
   cx.u = u;
   const SolveTask* tasks = X->d_stasks.as<SolveTask>();
   const bool was_timing = X->stats.timing;
@@ -1352,8 +1348,7 @@ static void apply_core(psp_ctx_s* X, double2* u, int nrhs, T* xf, T* xb, T* upd,
     sa.step_done = sync + 5;
     sa.done_up = sync + 5 + SP.nsteps;
     sa.done_down = sa.done_up + SP.nfront_steps;
-    sa.gathered = sa.done_down + SP.nfront_steps;
-    const size_t words = 5 + (size_t)SP.nsteps + 3 * (size_t)SP.nfront_steps;
+    const size_t words = 5 + (size_t)SP.nsteps + 2 * (size_t)SP.nfront_steps;
     int rc = -1;
     if (SP.nsteps == 0) rc = 0;   // an empty part (the backward part of a block holding the last panel alone)
     else if (X->persistent_sweep) {
@@ -1379,7 +1374,7 @@ static void apply_core(psp_ctx_s* X, double2* u, int nrhs, T* xf, T* xb, T* upd,
 template <typename T>
 static void apply_impl(psp_ctx_s* X, double2* u, int nrhs, cudaStream_t st) {
   ensure_apply_ws<T>(X, nrhs);
-  apply_core<T>(X, u, nrhs, X->ws_xf.as<T>(), X->ws_xb.as<T>(), X->ws_upd.as<T>(), X->ws_w.as<T>(), true, st);
+  apply_core<T>(X, u, nrhs, X->ws_xf.as<T>(), X->ws_xb.as<T>(), X->ws_upd.as<T>(), true, st);
 }
 
 // work-vector layout of apply_core inside one caller-provided buffer
@@ -1387,7 +1382,7 @@ static size_t round256(size_t b) { return (b + 255) / 256 * 256; }
 
 size_t apply_workspace_bytes(const psp_ctx_s* X, int nrhs) {
   const size_t e = X->elem_bytes, np = X->probs.size();
-  return 3 * round256((size_t)X->max_nloc * nrhs * np * e) + round256((size_t)X->max_upd * nrhs * np * e);
+  return 2 * round256((size_t)X->max_nloc * nrhs * np * e) + round256((size_t)X->max_upd * nrhs * np * e);
 }
 
 psp_status apply_with_workspace(psp_ctx_s* X, double2* u, int nrhs, void* ws, cudaStream_t st) {
@@ -1396,13 +1391,10 @@ psp_status apply_with_workspace(psp_ctx_s* X, double2* u, int nrhs, void* ws, cu
     char* p = static_cast<char*>(ws);
     const size_t e = X->elem_bytes;
     const size_t bx = round256((size_t)X->max_nloc * nrhs * X->probs.size() * e);
-    // box vectors xf | xb | w_S of shared gathers, then the update vectors
     if (X->prec == PSP_PREC_C64)
-      apply_core<float2>(X, u, nrhs, (float2*)p, (float2*)(p + bx), (float2*)(p + 3 * bx), (float2*)(p + 2 * bx), false,
-                         st);
+      apply_core<float2>(X, u, nrhs, (float2*)p, (float2*)(p + bx), (float2*)(p + 2 * bx), false, st);
     else
-      apply_core<double2>(X, u, nrhs, (double2*)p, (double2*)(p + bx), (double2*)(p + 3 * bx), (double2*)(p + 2 * bx),
-                          false, st);
+      apply_core<double2>(X, u, nrhs, (double2*)p, (double2*)(p + bx), (double2*)(p + 2 * bx), false, st);
   } catch (const Error& err) {
     g_last_error = err.msg;
     return err.st;
@@ -2297,9 +2289,9 @@ psp_status psp_solve(psp_handle X, const double* f, double* u, int nrhs, double 
   if (X->probs.size() == 1) {
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
-      const double ws = (3.0 * X->max_nloc + X->max_upd) * (double)X->elem_bytes;
+      const double ws = (2.0 * X->max_nloc + X->max_upd) * (double)X->elem_bytes;
       const double vec = (double)X->N * sizeof(double2);
-      const double held = (double)X->gm.bytes + X->ws_xf.bytes + X->ws_xb.bytes + X->ws_upd.bytes + X->ws_w.bytes;
+      const double held = (double)X->gm.bytes + X->ws_xf.bytes + X->ws_xb.bytes + X->ws_upd.bytes;
       const double avail = (double)free_b + held - 2.0e9;
       auto fit = [&](double per_rhs) {
         int g = std::max(1, std::min(nrhs, (int)(avail / per_rhs)));
@@ -2561,12 +2553,11 @@ psp_status psp_sweep_part(psp_handle X, double* u, int nrhs, int direction, void
   const int plan = direction == 0 ? 1 : 2;
   if (X->prec == PSP_PREC_C64) {
     ensure_apply_ws<float2>(X, nrhs);
-    apply_core<float2>(X, ud, nrhs, X->ws_xf.as<float2>(), X->ws_xb.as<float2>(), X->ws_upd.as<float2>(),
-                       X->ws_w.as<float2>(), true, st, plan);
+    apply_core<float2>(X, ud, nrhs, X->ws_xf.as<float2>(), X->ws_xb.as<float2>(), X->ws_upd.as<float2>(), true, st, plan);
   } else {
     ensure_apply_ws<double2>(X, nrhs);
-    apply_core<double2>(X, ud, nrhs, X->ws_xf.as<double2>(), X->ws_xb.as<double2>(), X->ws_upd.as<double2>(),
-                        X->ws_w.as<double2>(), true, st, plan);
+    apply_core<double2>(X, ud, nrhs, X->ws_xf.as<double2>(), X->ws_xb.as<double2>(), X->ws_upd.as<double2>(), true, st,
+                        plan);
   }
   if (!dev) {
     PSP_CK(cudaMemcpyAsync(u, ud, bytes, cudaMemcpyDeviceToHost, st));

@@ -222,7 +222,6 @@ struct SolveCtx {
   T* xf;                   // box vector after L^{-1} and D^{-1} (elimination order), ld = n_loc
   T* xb;                   // box vector after L^{-T}
   T* upd;                  // children's update vectors, ld = upd_ld
-  T* wbuf;                 // w_S of fronts gathered once for all their tasks (persistent sweep), ld = n_loc
   double2* u;              // global vector block, ld = N
   int64_t N, n_loc, upd_ld;
   int nrhs;
@@ -299,7 +298,6 @@ struct SweepArgs {
   unsigned* queue_head;         // dequeue counter (zeroed per sweep)
   unsigned* done_up;            // per step-front completed up tasks (zeroed per sweep)
   unsigned* done_down;
-  unsigned* gathered;           // per step-front: 1 once the front's w_S is in cx.wbuf (zeroed per sweep)
   unsigned* step_done;          // per step completed tasks (zeroed per sweep)
   int* status;                  // status[2] set when a wait gave up
   int* sticky;                  // also set then; kept until the host reads it (psp_check_status)

@@ -28,7 +28,8 @@ def test_summarize_picks_dominant_kernel_and_computes_rates(bench):
     roof, detail, launches = bench.summarize(timed, full, infos, 16e9, 2)
     assert roof["kernel"] == "k_gemm"
     assert roof["achieved"] == pytest.approx(1.0)              # 2e12 flop / 2 s
-    assert roof["frac"] == pytest.approx(1.0 / bench.FP64_DERIVED_TFLOPS)
+    # 3M complex products: the ceiling in counted flops is the FP64 peak x 8/6
+    assert roof["frac"] == pytest.approx(1.0 / (bench.FP64_DERIVED_TFLOPS * 8 / 6))
     assert roof["kernel_share"] == pytest.approx(1000.0 / 1450.0)
     assert launches == 2 * 129
     assert detail["apply_ms"] == pytest.approx(400.0 / 19)
@@ -78,8 +79,9 @@ def test_summarize_counts_algorithmic_flops_and_reports_si_beside(bench):
     full = {"k_gemm": rec(10, 1000.0, 1e12, 0, extra=2.5e11)}
     infos = [{"iterations": 3, "relres_max": 1e-6, "solve_ms": 1.0, "applies": 4}]
     roof, _, _ = bench.summarize(timed, full, infos, 1, 1, fp64_peak=1.25, fp64_source="x")
-    assert roof["achieved"] == pytest.approx(1.0) and roof["frac"] == pytest.approx(0.8)
+    assert roof["achieved"] == pytest.approx(1.0) and roof["frac"] == pytest.approx(0.8 * 6 / 8)
     assert roof["achieved_incl_si"] == pytest.approx(1.25)
+    assert roof["fp64_executed"] == pytest.approx(1.25 * 6 / 8) and roof["fp64_pipe_frac"] == pytest.approx(0.75)
 
 
 def test_rooflines_cover_the_metric_families(bench):
@@ -89,7 +91,8 @@ def test_rooflines_cover_the_metric_families(bench):
     alu = {"fp64_tflops": 1.2, "fp64_source": "m", "fp32_tflops": 70.0, "fp32_source": "m"}
     out = {(r["path"], r["kernel"]): r for r in bench.rooflines(full128, full64, alu)}
     g = out[("c128", "k_gemm")]
-    assert g["achieved"] == pytest.approx(1.0) and g["frac"] == pytest.approx(1.0 / 1.2)
+    assert g["achieved"] == pytest.approx(1.0) and g["frac"] == pytest.approx(1.0 / (1.2 * 8 / 6))
+    assert g["fp64_pipe_frac"] == pytest.approx(1.25 * 0.75 / 1.2)
     assert g["achieved_incl_si"] == pytest.approx(1.25)
     s64 = out[("c64", "k_sweep")]
     assert s64["bound"] == "hbm" and s64["achieved"] == pytest.approx(5e11 / 0.3 / 1e9)
