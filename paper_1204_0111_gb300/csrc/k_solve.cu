@@ -72,7 +72,8 @@ __device__ __forceinline__ void fwd_task(const SolveTask tk, const int rhs0, con
   const int32_t* pull = cx.sh.pull + 2 * cx.sh.pull_ptr[sn];
   // the vector w_S (or y_S) passes through shared memory in chunks of `chunk` entries (a multiple of
   // 256), so a CTA carries RG right-hand sides over a factor block of any width and reads it once
-  T* w = reinterpret_cast<T*>(smem_raw);        // chunk x RG
+  T* w = reinterpret_cast<T*>(smem_raw);        // RG x chunk (right-hand side major: no bank conflicts
+                                                 // when a warp spans several columns, R < 32)
   T* red = w + (int64_t)chunk * RG;              // blockDim x RG
 
   const int i = threadIdx.x % R, grp = threadIdx.x / R, ngrp = blockDim.x / R;
@@ -96,20 +97,20 @@ __device__ __forceinline__ void fwd_task(const SolveTask tk, const int rhs0, con
         for (int q = 0; q < RG; ++q) v[q] = (rhs0 + q < cx.nrhs) ? input_value(cx, node, rhs0 + q) : CplxTraits<T>::zero();
         pull_add<T, RG>(cx, pull + 2 * p, rhs0, v);
 #pragma unroll
-        for (int q = 0; q < RG; ++q) w[(p - j0) * RG + q] = v[q];
+        for (int q = 0; q < RG; ++q) w[q * chunk + (p - j0)] = v[q];
       }
     } else {
       for (int p = j0 + threadIdx.x; p < j1; p += blockDim.x)
 #pragma unroll
         for (int q = 0; q < RG; ++q)
-          w[(p - j0) * RG + q] = (rhs0 + q < cx.nrhs) ? __ldcg(cx.xb + (int64_t)(rhs0 + q) * cx.n_loc + first + p)
+          w[q * chunk + (p - j0)] = (rhs0 + q < cx.nrhs) ? __ldcg(cx.xb + (int64_t)(rhs0 + q) * cx.n_loc + first + p)
                                                       : CplxTraits<T>::zero();
     }
     __syncthreads();
     if (r < tk.r1) {
       if (r < s && r >= j0 && r < j1)
 #pragma unroll
-        for (int q = 0; q < RG; ++q) wr[q] = w[(r - j0) * RG + q];
+        for (int q = 0; q < RG; ++q) wr[q] = w[q * chunk + (r - j0)];
       // the same j sequence j = grp, grp + ngrp, ... in every chunking (j0 is a multiple of ngrp)
       const int jm = min(jmax, j1);
       int j = j0 + grp;
@@ -121,12 +122,12 @@ __device__ __forceinline__ void fwd_task(const SolveTask tk, const int rhs0, con
 #pragma unroll
         for (int t = 0; t < 8; ++t)
 #pragma unroll
-          for (int q = 0; q < RG; ++q) cfma(acc[q], gv[t], w[(j - j0 + t * ngrp) * RG + q]);
+          for (int q = 0; q < RG; ++q) cfma(acc[q], gv[t], w[q * chunk + (j - j0 + t * ngrp)]);
       }
       for (; j < jm; j += ngrp) {
         const T gv = __ldg(Gr + (int64_t)j * ld);
 #pragma unroll
-        for (int q = 0; q < RG; ++q) cfma(acc[q], gv, w[(j - j0) * RG + q]);
+        for (int q = 0; q < RG; ++q) cfma(acc[q], gv, w[q * chunk + (j - j0)]);
       }
     }
   }
@@ -171,7 +172,7 @@ __device__ __forceinline__ void fwd_tri_task(const SolveTask tk, const int rhs0,
   const int first = cx.sh.first[sn];
   const T* G = cx.G + cx.sh.g_off[sn];
   const int32_t* pull = cx.sh.pull + 2 * cx.sh.pull_ptr[sn];
-  T* w = reinterpret_cast<T*>(smem_raw);        // s x RG
+  T* w = reinterpret_cast<T*>(smem_raw);        // RG x s (right-hand side major)
   for (int p = threadIdx.x; p < s; p += blockDim.x) {
     const int node = cx.sh.order[first + p];
     T v[RG];
@@ -179,7 +180,7 @@ __device__ __forceinline__ void fwd_tri_task(const SolveTask tk, const int rhs0,
     for (int q = 0; q < RG; ++q) v[q] = (rhs0 + q < cx.nrhs) ? input_value(cx, node, rhs0 + q) : CplxTraits<T>::zero();
     pull_add<T, RG>(cx, pull + 2 * p, rhs0, v);
 #pragma unroll
-    for (int q = 0; q < RG; ++q) w[p * RG + q] = v[q];
+    for (int q = 0; q < RG; ++q) w[q * s + p] = v[q];
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -193,7 +194,7 @@ __device__ __forceinline__ void fwd_tri_task(const SolveTask tk, const int rhs0,
         __syncwarp();
         if (k > j && k < be)
 #pragma unroll
-          for (int q = 0; q < RG; ++q) cfms(w[k * RG + q], l, w[j * RG + q]);
+          for (int q = 0; q < RG; ++q) cfms(w[q * s + k], l, w[q * s + j]);
         __syncwarp();
       }
     }
@@ -206,10 +207,10 @@ __device__ __forceinline__ void fwd_tri_task(const SolveTask tk, const int rhs0,
       for (int j = b; j < be; ++j) {
         const T l = __ldg(G + (int64_t)j * ld + i);
 #pragma unroll
-        for (int q = 0; q < RG; ++q) cfma(acc[q], l, w[j * RG + q]);
+        for (int q = 0; q < RG; ++q) cfma(acc[q], l, w[q * s + j]);
       }
 #pragma unroll
-      for (int q = 0; q < RG; ++q) w[i * RG + q] = csub(w[i * RG + q], acc[q]);
+      for (int q = 0; q < RG; ++q) w[q * s + i] = csub(w[q * s + i], acc[q]);
     }
     __syncthreads();
   }
@@ -219,8 +220,8 @@ __device__ __forceinline__ void fwd_tri_task(const SolveTask tk, const int rhs0,
     for (int q = 0; q < RG; ++q)
       if (rhs0 + q < cx.nrhs) {
         const int64_t o = (int64_t)(rhs0 + q) * cx.n_loc + first + r;
-        cx.xb[o] = w[r * RG + q];
-        cx.xf[o] = cmul(w[r * RG + q], dinv);
+        cx.xb[o] = w[q * s + r];
+        cx.xf[o] = cmul(w[q * s + r], dinv);
       }
   }
 }
@@ -269,7 +270,9 @@ __device__ __forceinline__ void bwd_task(const SolveTask tk, const int rhs0, con
   // rows of the inner sums: [lo, hi), passed through shared memory in chunks of `chunk` rows
   const int lo = (ext || phase == 1) ? c0 : s;
   const int hi = (ext || phase == 0) ? ld : s;
-  T* y = reinterpret_cast<T*>(smem_raw);        // chunk x RG
+  // right-hand side major (y[q * chunk + row]): the lanes of a warp read consecutive rows, so the
+  // loads are free of bank conflicts whatever RG is
+  T* y = reinterpret_cast<T*>(smem_raw);        // RG x chunk
   T* sums = y + (int64_t)chunk * RG;            // (r1 - c0) x RG column sums (<= 64 columns)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int e = threadIdx.x; e < (tk.r1 - c0) * RG; e += blockDim.x) sums[e] = CplxTraits<T>::zero();
@@ -284,7 +287,7 @@ __device__ __forceinline__ void bwd_task(const SolveTask tk, const int rhs0, con
           const int64_t base = (int64_t)(rhs0 + q) * cx.n_loc;
           v = (r < s) ? __ldcg(cx.xf + base + first + r) : cneg(__ldcg(cx.xb + base + sel[r - s]));
         }
-        y[(r - rb) * RG + q] = v;
+        y[q * chunk + (r - rb)] = v;
       }
     }
     __syncthreads();
@@ -301,12 +304,12 @@ __device__ __forceinline__ void bwd_task(const SolveTask tk, const int rhs0, con
 #pragma unroll
         for (int t = 0; t < 8; ++t)
 #pragma unroll
-          for (int q = 0; q < RG; ++q) cfma(acc[q], gv[t], y[(r + 32 * t - rb) * RG + q]);
+          for (int q = 0; q < RG; ++q) cfma(acc[q], gv[t], y[q * chunk + (r + 32 * t - rb)]);
       }
       for (; r < re; r += 32) {
         const T gv = __ldg(Gc + r);
 #pragma unroll
-        for (int q = 0; q < RG; ++q) cfma(acc[q], gv, y[(r - rb) * RG + q]);
+        for (int q = 0; q < RG; ++q) cfma(acc[q], gv, y[q * chunk + (r - rb)]);
       }
 #pragma unroll
       for (int q = 0; q < RG; ++q) {
@@ -341,11 +344,11 @@ __device__ __forceinline__ void bwd_tri_task(const SolveTask tk, const int rhs0,
   const int s = cx.sh.s[sn], ld = s + cx.sh.u[sn];
   const int first = cx.sh.first[sn];
   const T* G = cx.G + cx.sh.g_off[sn];
-  T* x = reinterpret_cast<T*>(smem_raw);   // s x RG: t, overwritten by x block by block
+  T* x = reinterpret_cast<T*>(smem_raw);   // RG x s (right-hand side major): t, overwritten by x block by block
   for (int r = threadIdx.x; r < s; r += blockDim.x)
 #pragma unroll
     for (int q = 0; q < RG; ++q)
-      x[r * RG + q] = (rhs0 + q < cx.nrhs) ? __ldcg(cx.xf + (int64_t)(rhs0 + q) * cx.n_loc + first + r)
+      x[q * s + r] = (rhs0 + q < cx.nrhs) ? __ldcg(cx.xf + (int64_t)(rhs0 + q) * cx.n_loc + first + r)
                                            : CplxTraits<T>::zero();
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -360,7 +363,7 @@ __device__ __forceinline__ void bwd_tri_task(const SolveTask tk, const int rhs0,
       for (int r = be + lane; r < s; r += 32) {
         const T l = __ldg(G + (int64_t)c * ld + r);
 #pragma unroll
-        for (int q = 0; q < RG; ++q) cfma(acc[q], l, x[r * RG + q]);
+        for (int q = 0; q < RG; ++q) cfma(acc[q], l, x[q * s + r]);
       }
 #pragma unroll
       for (int q = 0; q < RG; ++q) {
@@ -368,7 +371,7 @@ __device__ __forceinline__ void bwd_tri_task(const SolveTask tk, const int rhs0,
           acc[q].x += __shfl_xor_sync(0xffffffffu, acc[q].x, off);
           acc[q].y += __shfl_xor_sync(0xffffffffu, acc[q].y, off);
         }
-        if (lane == 0) x[c * RG + q] = csub(x[c * RG + q], acc[q]);
+        if (lane == 0) x[q * s + c] = csub(x[q * s + c], acc[q]);
       }
     }
     __syncthreads();
@@ -380,7 +383,7 @@ __device__ __forceinline__ void bwd_tri_task(const SolveTask tk, const int rhs0,
         __syncwarp();
         if (k < c)
 #pragma unroll
-          for (int q = 0; q < RG; ++q) cfms(x[k * RG + q], l, x[c * RG + q]);
+          for (int q = 0; q < RG; ++q) cfms(x[q * s + k], l, x[q * s + c]);
         __syncwarp();
       }
     }
@@ -389,7 +392,7 @@ __device__ __forceinline__ void bwd_tri_task(const SolveTask tk, const int rhs0,
   for (int c = threadIdx.x; c < s; c += blockDim.x)
 #pragma unroll
     for (int q = 0; q < RG; ++q)
-      if (rhs0 + q < cx.nrhs) write_solution(cx, first, c, rhs0 + q, x[c * RG + q]);
+      if (rhs0 + q < cx.nrhs) write_solution(cx, first, c, rhs0 + q, x[q * s + c]);
 }
 
 template <typename T, int RG>
