@@ -328,7 +328,8 @@ class SweepingPreconditionerBatch(SweepingPreconditioner):
 
     def __init__(self, problems, pad=None, leaf=64, pml_C=4.0, alpha=2 * math.pi, precision="c128", faces=63,
                  mode="moving", stream=None, collect_stats=0, tensor_cores=True, tc_min_dim=0, sweep_level_tasks=0,
-                 sweep_ctas_per_sm=0, setup_temp_mb=0, sweep_rhs_group=0, solve_rhs_group=0):
+                 sweep_ctas_per_sm=0, setup_temp_mb=0, sweep_rhs_group=0, solve_rhs_group=0,
+                 selective_inversion="extended", factor_every_panel=False, allocator=None):
         n = len(problems)
         grids = (Grid * n)()
         cs = (_P * n)()
@@ -353,6 +354,12 @@ class SweepingPreconditionerBatch(SweepingPreconditioner):
         self.N = sum(self.points)
         o = _options(pad, leaf, pml_C, alpha, precision, faces, mode, collect_stats, tensor_cores, tc_min_dim,
                      sweep_level_tasks, sweep_ctas_per_sm, setup_temp_mb, sweep_rhs_group, solve_rhs_group)
+        o.selective_inversion = SI_MODES[selective_inversion]
+        o.factor_every_panel = 1 if factor_every_panel else 0
+        if allocator is not None:
+            self._alloc_cbs = _allocator_callbacks(*allocator)
+            o.dev_alloc = ctypes.cast(self._alloc_cbs[0], ctypes.c_void_p)
+            o.dev_free = ctypes.cast(self._alloc_cbs[1], ctypes.c_void_p)
         h_ = _P()
         st = lib().psp_setup_batch(n, grids, cs, om, ga, de, ctypes.byref(o), _stream(stream), ctypes.byref(h_))
         self._finish(h_, st)

@@ -74,11 +74,12 @@ def assert_same_factors(B, singles):
     assert B.info()["panels"] == panel
 
 
-@pytest.mark.parametrize("precision", ["c128", "c64"])
-def test_batch_equals_separate_handles(precision):
+@pytest.mark.parametrize("precision,si", [("c128", "extended"), ("c64", "extended"), ("c128", "paper"),
+                                          ("c64", "paper"), ("c128", "none")])
+def test_batch_equals_separate_handles(precision, si):
     prs = problems_small() if precision == "c128" else problems_tc()
-    B = batched(prs, precision=precision)
-    singles = [single(p, precision=precision) for p in prs]
+    B = batched(prs, precision=precision, selective_inversion=si)
+    singles = [single(p, precision=precision, selective_inversion=si) for p in prs]
     assert B.points == [p["c"].size for p in prs]
     assert_same_factors(B, singles)
     nrhs = 2
