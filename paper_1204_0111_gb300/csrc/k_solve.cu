@@ -57,6 +57,49 @@ __device__ __forceinline__ void pull_add(const SolveCtx<T>& cx, const int32_t* p
   }
 }
 
+// w_S entries [j0, j1) of front sn (zero-extended input + children's updates) for right-hand sides
+// [rhs0, rhs0 + RG) into w (right-hand side major, ld chunk).  Each thread first loads the node ids
+// and pull offsets of GU entries, then all of their values, so that a thread has GU independent
+// gathers in flight rather than one chain of dependent loads after another.
+template <typename T, int RG>
+__device__ __forceinline__ void gather_w(const SolveCtx<T>& cx, const int first, const int32_t* pull, const int j0,
+                                         const int j1, const int rhs0, T* w, const int chunk) {
+  constexpr int GU = RG >= 4 ? 1 : (RG == 2 ? 2 : 4);
+  for (int p0 = j0 + threadIdx.x; p0 < j1; p0 += GU * blockDim.x) {
+    int node[GU];
+    int32_t pa[GU], pb[GU];
+#pragma unroll
+    for (int t = 0; t < GU; ++t) {
+      const int p = p0 + t * blockDim.x;
+      const bool in = p < j1;
+      node[t] = in ? cx.sh.order[first + p] : 0;
+      pa[t] = in ? pull[2 * p] : -1;
+      pb[t] = in ? pull[2 * p + 1] : -1;
+    }
+    T v[GU][RG];
+#pragma unroll
+    for (int t = 0; t < GU; ++t)
+#pragma unroll
+      for (int q = 0; q < RG; ++q) {
+        T x = CplxTraits<T>::zero();
+        if (p0 + t * blockDim.x < j1 && rhs0 + q < cx.nrhs) {
+          x = input_value(cx, node[t], rhs0 + q);
+          const T* uq = cx.upd + (int64_t)(rhs0 + q) * cx.upd_ld;
+          if (pa[t] >= 0) x = cadd(x, __ldcg(uq + pa[t]));
+          if (pb[t] >= 0) x = cadd(x, __ldcg(uq + pb[t]));
+        }
+        v[t][q] = x;
+      }
+#pragma unroll
+    for (int t = 0; t < GU; ++t) {
+      const int p = p0 + t * blockDim.x;
+      if (p < j1)
+#pragma unroll
+        for (int q = 0; q < RG; ++q) w[q * chunk + (p - j0)] = v[t][q];
+    }
+  }
+}
+
 // up-the-tree task: rows [r0, r1) of front sn, right-hand sides [rhs0, rhs0 + RG).
 // phase 0 gathers w_S (zero-extended input + children's updates) and, for rows r < s, writes
 // x_r = D^{-1} y_r with y_S = inv(L_TL) w_S (and y_r itself into xb when the second phase needs it);
@@ -89,16 +132,7 @@ __device__ __forceinline__ void fwd_task(const SolveTask tk, const int rhs0, con
     const int j1 = min(j0 + chunk, jend);
     if (j0 > 0) __syncthreads();   // the previous chunk is consumed
     if (phase == 0) {
-      // w_S = (zero-extended input) + children's updates
-      for (int p = j0 + threadIdx.x; p < j1; p += blockDim.x) {
-        const int node = cx.sh.order[first + p];
-        T v[RG];
-#pragma unroll
-        for (int q = 0; q < RG; ++q) v[q] = (rhs0 + q < cx.nrhs) ? input_value(cx, node, rhs0 + q) : CplxTraits<T>::zero();
-        pull_add<T, RG>(cx, pull + 2 * p, rhs0, v);
-#pragma unroll
-        for (int q = 0; q < RG; ++q) w[q * chunk + (p - j0)] = v[q];
-      }
+      gather_w<T, RG>(cx, first, pull, j0, j1, rhs0, w, chunk);   // w_S = zero-extended input + children's updates
     } else {
       for (int p = j0 + threadIdx.x; p < j1; p += blockDim.x)
 #pragma unroll
