@@ -493,12 +493,24 @@ def rooflines(full128, full64, alu):
 # ---------------------------------------------------------------------------------------------
 # the other configurations, one object each (a single timed step after the kernels are warm)
 # ---------------------------------------------------------------------------------------------
-def extra_workload(name, w, precision, dev, sched=None, maxit=400, desc=""):
+def extra_workload(name, w, precision, dev, sched=None, maxit=400, desc="", tune_nrhs=0):
     import torch
 
     from paper_1204_0111_gb300 import psp
     stream = torch.cuda.current_stream(dev)
     c_dev = torch.from_numpy(w.c).to(dev)
+    tuning = None
+    if tune_nrhs > 0:
+        # the sweep autotuner on a handle of its own, before the timed step, for the right-hand sides one
+        # GMRES run carries
+        P = psp.SweepingPreconditioner(c_dev, w.h, w.omega, w.gamma, w.panel_depth, pad=w.pad, leaf=w.leaf,
+                                       pml_C=w.pml_C, alpha=w.alpha, precision=precision, **(sched or {}))
+        tuning = P.tune_sweep(nrhs=tune_nrhs, reps=1)
+        P.close()
+        torch.cuda.empty_cache()
+        sched = dict(sched or {}, sweep_level_tasks=tuning["sweep_level_tasks"],
+                     sweep_ctas_per_sm=tuning["sweep_ctas_per_sm"], sweep_rhs_group=tuning["sweep_rhs_group"],
+                     sweep_min_rows=tuning["sweep_min_rows"])
     f = w.rhs()
     f_dev = torch.from_numpy(f).to(dev)
     u_dev = torch.zeros_like(f_dev)
@@ -538,7 +550,7 @@ def extra_workload(name, w, precision, dev, sched=None, maxit=400, desc=""):
             "factor_bytes": pinfo["factor_bytes"],
             "apply_ms": sw["total_ms"] / max(info["applies"], 1),
             "sweep_gbs": sw["bytes"] / max(sw["total_ms"] * 1e-3, 1e-12) / 1e9,
-            "roofline": roof, "clocks": clk, "kernels": kernel_table(full),
+            "roofline": roof, "clocks": clk, "kernels": kernel_table(full), "sweep_tuning": tuning,
             "host_setup_ms": {k[5:]: v["total_ms"] for k, v in st.items() if k.startswith("host:")}}
 
 
@@ -740,13 +752,13 @@ def gpu_main(a):
         torch.cuda.empty_cache()
         ws = wl.cube_salt(256)
         extras["salt256"] = extra_workload(
-            "salt256", ws, "c64", dev, maxit=400,
+            "salt256", ws, "c64", dev, maxit=400, tune_nrhs=8,
             desc=f"salt256: 256^3 salt body in a 1.5-4.5 depth gradient, 8 points per wavelength, gamma 12, panels "
                  f"of 8 + pad 8, leaf 64, PML amplitude 4 relative to c_max, 32 shots on an 8 x 4 grid below the "
                  f"top PML, GMRES(30) to 1e-05, complex64 fronts and sweeps, complex128 GMRES")
         wly = wl.cube_layered(200)
         extras["layered200"] = extra_workload(
-            "layered200", wly, "c64", dev, maxit=600,
+            "layered200", wly, "c64", dev, maxit=600, tune_nrhs=1,
             desc="layered200: 200^3, 12 dipping layers c ~ U(1.5, 6) and 2 planar faults (seed 3), 10 points per "
                  "wavelength at c_min, gamma 10, panels of 4 + pad 10, PML amplitude 4 relative to c_max, one shot "
                  "at (0.5, 0.5, 0.1), GMRES(20) to 1e-05, complex64 fronts and sweeps, complex128 GMRES")

@@ -111,9 +111,13 @@ typedef struct {
                           (a level whose fronts need more is factored in several batches); <= 0: up
                           to 80 % of the device memory left after the factors and update matrices */
   int sweep_rhs_group; /* sweep schedule: most right-hand sides (1, 2, 4 or 8) one CTA carries through a
-                          pass over a factor block; <= 0: as many as keep its shared memory within 64 KB */
+                          pass over a factor block; <= 0: as many as the application has, at most 8 (the
+                          task's vector is staged through 64 KB of shared memory in chunks) */
   int solve_rhs_group; /* psp_solve: most right-hand sides per GMRES run; <= 0: as many as fit the free
                           device memory (single-problem handles) */
+  int sweep_min_rows;   /* sweep schedule: fewest rows (up) / columns (down) of a front per task, 8 .. 64;
+                           <= 0 selects the default (8).  Each task gathers its front's vector for every
+                           right-hand side, so with many right-hand sides wider tasks gather less */
   int test_sweep_stall; /* tests only: 1 makes one dependency of the persistent sweep impossible to
                            meet, so its bounded wait (about 2 s) gives up; psp_solve then returns
                            PSP_ERR_TIMEOUT and the device stays usable.  0 (default): off */
@@ -323,7 +327,8 @@ psp_status psp_stats(psp_handle h, psp_kernel_stat* out, int capacity, int* coun
  * sweep (the GPU's counterpart of the paper's choice of process grids, §2.1).  On this handle it
  * times psp_apply with nrhs right-hand sides (per problem of a batch) under candidate schedules
  * and keeps the fastest: the tasks a tree level is split into (152 .. 2432), the resident CTAs per
- * SM (2, 3, 4, 6, 8) and, for nrhs > 1, the right-hand sides per CTA pass (1 .. 8).  It searches one
+ * SM (2, 3, 4, 6, 8) and, for nrhs > 1, the right-hand sides per CTA pass (1 .. 8) and the floor on
+ * rows per task (8 .. 64).  It searches one
  * coordinate at a time, starting from the handle's current schedule, timing `reps` applications
  * (CUDA events on `stream`) per candidate after one untimed one.  Results do not change beyond
  * rounding (the schedule only regroups the same sums).  The work vectors are the handle's own; the
@@ -338,7 +343,8 @@ typedef struct {
   int candidates;         /* schedules timed */
   double initial_ms;      /* one application under the schedule the handle had */
   double best_ms;         /* one application under the chosen schedule */
-  int reserved[4];
+  int sweep_min_rows;     /* floor on rows / columns per task */
+  int reserved[3];
 } psp_sweep_tuning;
 
 psp_status psp_tune_sweep(psp_handle h, int nrhs, int reps, void* stream, psp_sweep_tuning* out);

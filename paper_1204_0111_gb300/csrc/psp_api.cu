@@ -314,7 +314,7 @@ struct psp_ctx_s {
   int device = -1;          // CUDA device current at setup; every later call must run with it current
   bool use_tc = true;
   int tc_min_dim = 64;
-  int sweep_level_tasks = 608, sweep_ctas_per_sm = 8, sweep_rhs_group = 0, solve_rhs_group = 0;
+  int sweep_level_tasks = 608, sweep_ctas_per_sm = 8, sweep_rhs_group = 0, solve_rhs_group = 0, sweep_min_rows = 8;
   int gmres_basis = 0;   // 0 auto, 1 keep z_j, 2 V only
   int si_mode = 0;       // psp_si_mode: what the factor of each front keeps (selective inversion, §2.2)
   bool test_sweep_stall = false;
@@ -1065,11 +1065,15 @@ static void plan_solve(psp_ctx_s* X, cudaStream_t st) {
         P.entries += ss * (ss - 1) / 2 + uu * ss;
         P.vec += 2 * ss + 2 * uu;
       }
+      // rows (columns) per task: 64, halved while the level has fewer than sweep_level_tasks tasks, but
+      // not below sweep_min_rows (a task gathers its front's vector for every right-hand side, so
+      // narrow tasks over wide fronts gather much and stream little)
+      const int rmin = std::max(8, std::min(64, X->sweep_min_rows));
       int R = 64;
-      while (R > 8 && rows / R < X->sweep_level_tasks) R >>= 1;
+      while (R > rmin && rows / R < X->sweep_level_tasks) R >>= 1;
       P.R = R;
       int Cc = 64;
-      while (Cc > 8 && cols / Cc < X->sweep_level_tasks) Cc >>= 1;
+      while (Cc > rmin && cols / Cc < X->sweep_level_tasks) Cc >>= 1;
       // extended factors: one pass per front and direction over all s + u rows; factors keeping L_BL:
       // up, rows r < s (one whole-front substitution task without inversion) then rows r >= s; down,
       // columns for L_BL^T then columns for the triangle (one whole-front task without inversion)
@@ -2103,6 +2107,7 @@ static void init_options(psp_ctx_s* X, const psp_options& o) {
   X->sweep_level_tasks = o.sweep_level_tasks > 0 ? o.sweep_level_tasks : 608;
   X->sweep_ctas_per_sm = o.sweep_ctas_per_sm > 0 ? o.sweep_ctas_per_sm : 8;
   X->sweep_rhs_group = o.sweep_rhs_group > 0 ? o.sweep_rhs_group : 0;
+  X->sweep_min_rows = o.sweep_min_rows > 0 ? o.sweep_min_rows : 8;
   X->solve_rhs_group = o.solve_rhs_group > 0 ? o.solve_rhs_group : 0;
   X->gmres_basis = o.gmres_basis;
   X->si_mode = o.selective_inversion;
@@ -2467,11 +2472,12 @@ psp_status psp_tune_sweep(psp_handle X, int nrhs, int reps, void* stream, psp_sw
   cudaEvent_t e0, e1;
   PSP_CK(cudaEventCreate(&e0));
   PSP_CK(cudaEventCreate(&e1));
-  struct Sched { int lt, cps, rg; };
+  struct Sched { int lt, cps, rg, mr; };
   int timed = 0;
   auto time_one = [&](const Sched& c) {
-    if (c.lt != X->sweep_level_tasks) {
+    if (c.lt != X->sweep_level_tasks || c.mr != X->sweep_min_rows) {
       X->sweep_level_tasks = c.lt;
+      X->sweep_min_rows = c.mr;
       plan_solve(X, st);
     }
     X->sweep_ctas_per_sm = c.cps;
@@ -2488,7 +2494,7 @@ psp_status psp_tune_sweep(psp_handle X, int nrhs, int reps, void* stream, psp_sw
   };
   const bool was_timing = X->stats.timing;
   X->stats.timing = false;
-  Sched best{X->sweep_level_tasks, X->sweep_ctas_per_sm, X->sweep_rhs_group};
+  Sched best{X->sweep_level_tasks, X->sweep_ctas_per_sm, X->sweep_rhs_group, X->sweep_min_rows};
   double best_ms = 0, initial_ms = 0;
   try {
     best_ms = initial_ms = time_one(best);
@@ -2500,12 +2506,15 @@ psp_status psp_tune_sweep(psp_handle X, int nrhs, int reps, void* stream, psp_sw
       }
     };
     for (int lt : {152, 304, 608, 1216, 2432})
-      if (lt != best.lt) consider({lt, best.cps, best.rg});
+      if (lt != best.lt) consider({lt, best.cps, best.rg, best.mr});
     for (int cps : {2, 3, 4, 6, 8})
-      if (cps != best.cps) consider({best.lt, cps, best.rg});
-    if (nrhs > 1)
+      if (cps != best.cps) consider({best.lt, cps, best.rg, best.mr});
+    if (nrhs > 1) {
       for (int rg : {1, 2, 4, 8})
-        if (rg <= nrhs && rg != best.rg) consider({best.lt, best.cps, rg});
+        if (rg <= nrhs && rg != best.rg) consider({best.lt, best.cps, rg, best.mr});
+      for (int mr : {8, 16, 32, 64})
+        if (mr != best.mr) consider({best.lt, best.cps, best.rg, mr});
+    }
   } catch (...) {
     X->stats.timing = was_timing;
     cudaEventDestroy(e0);
@@ -2515,8 +2524,9 @@ psp_status psp_tune_sweep(psp_handle X, int nrhs, int reps, void* stream, psp_sw
   X->stats.timing = was_timing;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (best.lt != X->sweep_level_tasks) {
+  if (best.lt != X->sweep_level_tasks || best.mr != X->sweep_min_rows) {
     X->sweep_level_tasks = best.lt;
+    X->sweep_min_rows = best.mr;
     plan_solve(X, st);
   }
   X->sweep_ctas_per_sm = best.cps;
@@ -2526,6 +2536,7 @@ psp_status psp_tune_sweep(psp_handle X, int nrhs, int reps, void* stream, psp_sw
     out->sweep_level_tasks = best.lt;
     out->sweep_ctas_per_sm = best.cps;
     out->sweep_rhs_group = best.rg;
+    out->sweep_min_rows = best.mr;
     out->candidates = timed;
     out->initial_ms = initial_ms;
     out->best_ms = best_ms;

@@ -36,7 +36,8 @@ class Options(ctypes.Structure):
                 ("tc_min_dim", ctypes.c_int),
                 ("sweep_level_tasks", ctypes.c_int), ("sweep_ctas_per_sm", ctypes.c_int),
                 ("setup_temp_mb", ctypes.c_int), ("sweep_rhs_group", ctypes.c_int),
-                ("solve_rhs_group", ctypes.c_int), ("test_sweep_stall", ctypes.c_int), ("gmres_basis", ctypes.c_int),
+                ("solve_rhs_group", ctypes.c_int), ("sweep_min_rows", ctypes.c_int), ("test_sweep_stall", ctypes.c_int),
+                ("gmres_basis", ctypes.c_int),
                 ("factor_every_panel", ctypes.c_int), ("panel_begin", ctypes.c_int), ("panel_count", ctypes.c_int),
                 ("dev_alloc", ctypes.c_void_p), ("dev_free", ctypes.c_void_p), ("alloc_ctx", ctypes.c_void_p),
                 ("selective_inversion", ctypes.c_int)]
@@ -65,7 +66,7 @@ class SolveInfo(ctypes.Structure):
 class SweepTuning(ctypes.Structure):
     _fields_ = [("sweep_level_tasks", ctypes.c_int), ("sweep_ctas_per_sm", ctypes.c_int),
                 ("sweep_rhs_group", ctypes.c_int), ("candidates", ctypes.c_int), ("initial_ms", ctypes.c_double),
-                ("best_ms", ctypes.c_double), ("reserved", ctypes.c_int * 4)]
+                ("best_ms", ctypes.c_double), ("sweep_min_rows", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -183,7 +184,7 @@ class SweepingPreconditioner:
                  precision="c128", faces=63, mode="moving", stream=None, collect_stats=0, tensor_cores=True,
                  tc_min_dim=0, sweep_level_tasks=0, sweep_ctas_per_sm=0, setup_temp_mb=0, sweep_rhs_group=0,
                  solve_rhs_group=0, test_sweep_stall=0, gmres_basis="auto", factor_every_panel=False,
-                 panels=None, allocator=None, selective_inversion="extended"):
+                 panels=None, allocator=None, selective_inversion="extended", sweep_min_rows=0):
         nz, ny, nx = c.shape
         self.nx, self.ny, self.nz = nx, ny, nz
         self.N = nx * ny * nz
@@ -192,6 +193,7 @@ class SweepingPreconditioner:
         o = _options(pad, leaf, pml_C, alpha, precision, faces, mode, collect_stats, tensor_cores, tc_min_dim,
                      sweep_level_tasks, sweep_ctas_per_sm, setup_temp_mb, sweep_rhs_group, solve_rhs_group)
         o.test_sweep_stall = int(test_sweep_stall)
+        o.sweep_min_rows = int(sweep_min_rows)
         o.gmres_basis = {"auto": 0, "z": 1, "v": 2}[gmres_basis]
         o.factor_every_panel = 1 if factor_every_panel else 0
         if panels is not None:                   # (first, count): one block of a multi-GPU sweep

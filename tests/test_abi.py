@@ -74,3 +74,35 @@ def test_batch_arguments_are_rejected_before_any_device_call(L):
 
 def test_tune_sweep_rejects_bad_arguments(L):
     assert L.psp_tune_sweep(None, 1, 1, None, None) == 1
+
+
+def _c_struct_fields(name):
+    """Field names, in order, of `typedef struct { ... } name;` in include/psp.h."""
+    import re
+    text = open(psp.HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    m = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + r"\s*;", text, flags=re.S)
+    assert m, name
+    fields = []
+    for decl in m.group(1).split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        fp = re.match(r".*\(\s*\*\s*(\w+)\s*\)\s*\(.*\)$", decl, flags=re.S)   # function pointer
+        if fp:
+            fields.append(fp.group(1))
+            continue
+        names = decl.split(None, 1)[1] if " " in decl else decl
+        for nm in names.split(","):
+            nm = nm.strip().lstrip("*").strip()
+            fields.append(re.sub(r"\[.*\]", "", nm))
+    return fields
+
+
+@pytest.mark.parametrize("cname,py", [("psp_options", psp.Options), ("psp_solve_info", psp.SolveInfo),
+                                      ("psp_kernel_stat", psp.KernelStat), ("psp_sweep_tuning", psp.SweepTuning),
+                                      ("psp_setup_tuning", psp.SetupTuning), ("psp_grid", psp.Grid)])
+def test_binding_structs_match_the_header(cname, py):
+    # the ctypes mirrors must list the C fields in the same order (a shifted field would silently
+    # pass the wrong option)
+    assert [f for f, _ in py._fields_] == _c_struct_fields(cname)
