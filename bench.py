@@ -877,17 +877,45 @@ def batch_object(dev, steps, warmup, with_e2e=False):
 
 
 def salt_main(a):
-    """The salt workload of --n as one line (a profiling aid; the default line carries salt256)."""
+    """The salt workload of --n as one line (a profiling aid; the default line carries salt256).  With
+    --apply-only: setup, then --steps timed applications to --apply-nrhs shots (after --warmup
+    untimed ones and, unless --no-tune, the sweep autotuner), no GMRES."""
     import torch
 
+    from paper_1204_0111_gb300 import psp
     from paper_1204_0111_gb300 import workloads as wl
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     w = wl.cube_salt(a.n)
+    if not a.apply_only:
+        for _ in range(a.warmup):
+            extra_workload("salt", w, "c64", dev)
+        o = extra_workload("salt", w, "c64", dev, desc=f"salt{a.n}")
+        print(json.dumps(o))
+        return
+    c_dev = torch.from_numpy(w.c).to(dev)
+    P = psp.SweepingPreconditioner(c_dev, w.h, w.omega, w.gamma, w.panel_depth, pad=w.pad, leaf=w.leaf,
+                                   pml_C=w.pml_C, alpha=w.alpha, precision="c64", collect_stats=1)
+    tuning = None if a.no_tune else P.tune_sweep(nrhs=a.apply_nrhs, reps=1)
+    f = torch.from_numpy(w.rhs()[:a.apply_nrhs].copy()).to(dev)
+    u = torch.empty_like(f)
     for _ in range(a.warmup):
-        extra_workload("salt", w, "c64", dev)
-    o = extra_workload("salt", w, "c64", dev, desc=f"salt{a.n}")
-    print(json.dumps(o))
+        P.apply(f, u)
+    P.stats(reset=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(a.steps):
+        P.apply(f, u)
+    e1.record()
+    torch.cuda.synchronize()
+    st = P.stats()
+    sw = st["k_sweep"]
+    print(json.dumps({"workload": f"salt{a.n} apply, {a.apply_nrhs} shots, complex64", "steps": a.steps,
+                      "apply_ms": e0.elapsed_time(e1) / a.steps, "sweep_ms": sw["total_ms"] / a.steps,
+                      "sweep_gbs": sw["bytes"] / max(sw["total_ms"] * 1e-3, 1e-12) / 1e9,
+                      "factor_bytes": P.info()["factor_bytes"], "sweep_tuning": tuning}))
+    P.close()
 
 
 def batch_main(a):
@@ -964,6 +992,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling captures)")
     ap.add_argument("--no-peaks", action="store_true", help="skip the FP64/FP32 GEMM peak measurement (profiling "
                     "captures; the derived peaks are used)")
+    ap.add_argument("--apply-only", action="store_true", help="--workload salt: time applications only")
+    ap.add_argument("--apply-nrhs", type=int, default=8, help="--workload salt --apply-only: shots per application")
     ap.add_argument("--si", choices=["auto", "extended", "paper", "none"], default="auto",
                     help="factor form (selective inversion) of the timed path: auto = psp_tune_setup's choice")
     ap.add_argument("--precision", choices=["c128", "c64"], default="c128",
