@@ -3,6 +3,7 @@
 // and GMRES(k) (§2.4).  All arithmetic of the path runs in the kernels of this library; the host
 // only plans (symbolic analysis, memory layout, task lists) and sequences launches.
 #include <algorithm>
+#include <climits>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -2288,28 +2289,46 @@ psp_status psp_solve(psp_handle X, const double* f, double* u, int nrhs, double 
   // fit the free device memory, else groups that do.  The columns iterate independently, so the
   // groups give the same result.  (Batches keep one run: their columns interleave problems.)
   // When not all of them fit with z_j = M^{-1} v_j kept (2k + 1 vectors each), GMRES keeps V only
-  // (k + 2 vectors each, one more application per cycle) if that needs fewer runs.
-  int group = nrhs;
+  // (k + 2 vectors each, one more application per cycle) if that needs fewer sweep passes.
+  // The runs get balanced sizes: a sweep carries up to `width` right-hand sides per pass over the
+  // factors, so of the run counts the memory allows, the one needing the fewest passes is taken
+  // (32 columns with room for 10 per run: four runs of 8, not 10, 10, 10 and 2).
+  int width = 8;
+  if (X->sweep_rhs_group > 0)
+    while (width > 1 && width > X->sweep_rhs_group) width >>= 1;
+  auto plan_runs = [&](int cap, int* best_passes) {
+    int best_r = nrhs, best_p = INT_MAX;
+    for (int r = (nrhs + cap - 1) / cap; r <= nrhs; ++r) {
+      const int q = nrhs / r, rem = nrhs % r;
+      const int p = rem * ((q + width) / width) + (r - rem) * ((q + width - 1) / width);
+      if (p < best_p) {
+        best_p = p;
+        best_r = r;
+      }
+      if (q <= width) break;   // one pass per run already: more runs only add passes
+    }
+    *best_passes = best_p;
+    return best_r;
+  };
+  int runs = 1;
   bool store_z = true;
   if (X->probs.size() == 1) {
+    const int cap = X->solve_rhs_group > 0 ? std::min(nrhs, X->solve_rhs_group) : nrhs;
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
       const double ws = (2.0 * X->max_nloc + X->max_upd) * (double)X->elem_bytes;
       const double vec = (double)X->N * sizeof(double2);
       const double held = (double)X->gm.bytes + X->ws_xf.bytes + X->ws_xb.bytes + X->ws_upd.bytes;
       const double avail = (double)free_b + held - 2.0e9;
-      auto fit = [&](double per_rhs) {
-        int g = std::max(1, std::min(nrhs, (int)(avail / per_rhs)));
-        if (X->solve_rhs_group > 0) g = std::min(g, X->solve_rhs_group);
-        return g;
-      };
-      const int gz = fit((2.0 * k + 6) * vec + ws), gv = fit((k + 7.0) * vec + ws);
-      const int runs_z = (nrhs + gz - 1) / gz, runs_v = (nrhs + gv - 1) / gv;
-      store_z = X->gmres_basis == 1 || (X->gmres_basis == 0 && runs_v >= runs_z);
-      group = store_z ? gz : gv;
+      auto fit = [&](double per_rhs) { return std::max(1, std::min(cap, (int)(avail / per_rhs))); };
+      int pz = 0, pv = 0;
+      const int rz = plan_runs(fit((2.0 * k + 6) * vec + ws), &pz), rv = plan_runs(fit((k + 7.0) * vec + ws), &pv);
+      store_z = X->gmres_basis == 1 || (X->gmres_basis == 0 && pv >= pz);
+      runs = store_z ? rz : rv;
     } else {
       cudaGetLastError();
-      if (X->solve_rhs_group > 0) group = std::min(group, X->solve_rhs_group);
+      int p = 0;
+      runs = plan_runs(cap, &p);
       store_z = X->gmres_basis != 2;
     }
   } else {
@@ -2333,8 +2352,8 @@ psp_status psp_solve(psp_handle X, const double* f, double* u, int nrhs, double 
     for (size_t r = src.size(); r < dst.size() && !src.empty(); ++r)
       for (int c = 0; c < nc; ++c) dst[r][c0 + c] = src.back()[c];
   };
-  for (int r0 = 0; r0 < nrhs; r0 += group) {
-    const int ng = std::min(group, nrhs - r0);
+  for (int run = 0, r0 = 0; run < runs; ++run) {
+    const int ng = nrhs / runs + (run < nrhs % runs ? 1 : 0);
     psp_solve_info gi{};
     std::vector<std::vector<double>> he, ht;
     try {
@@ -2353,6 +2372,7 @@ psp_status psp_solve(psp_handle X, const double* f, double* u, int nrhs, double 
     agg.relres_max = std::max(agg.relres_max, gi.relres_max);
     agg.solve_ms += gi.solve_ms;
     agg.groups += 1;
+    r0 += ng;
   }
   if (info) *info = agg;
   if (!dev_out) {

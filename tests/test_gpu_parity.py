@@ -254,6 +254,27 @@ def test_solve_in_groups_of_right_hand_sides_equals_one_run():
     assert i3["iterations"] == i1["iterations"] and i3["converged"] == 1
 
 
+def test_runs_of_right_hand_sides_are_balanced():
+    # seven columns with room for three per run: three runs (3, 2, 2), the same solutions as one run
+    # (to rounding: a sweep over 8, 4 or 2 columns stages its vectors in chunks of different lengths,
+    # which changes the order of the column sums down the tree)
+    case = CASES[0]
+    f = np.stack([wl.gaussian_source(case.nx, case.ny, case.nz, case.h, (0.2 + 0.1 * j, 0.5, 0.3 + 0.05 * j))
+                  for j in range(7)])
+    c = torch.from_numpy(case.c).cuda()
+    kw = dict(pad=case.pad, leaf=case.leaf, pml_C=case.C, alpha=case.alpha, faces=case.faces)
+    P = psp.SweepingPreconditioner(c, case.h, case.omega, case.gamma, case.depth, **kw)
+    Q = psp.SweepingPreconditioner(c, case.h, case.omega, case.gamma, case.depth, solve_rhs_group=3, **kw)
+    u1, u3 = np.zeros_like(f), np.zeros_like(f)
+    i1 = P.solve(f, u1, tol=1e-6, k=10, maxit=300)
+    i3 = Q.solve(f, u3, tol=1e-6, k=10, maxit=300)
+    assert i1["groups"] == 1 and i3["groups"] == 3
+    assert i3["iterations"] == i1["iterations"] and i3["converged"] == 1
+    assert np.linalg.norm(u3 - u1) / np.linalg.norm(u1) < 1e-10
+    P.close()
+    Q.close()
+
+
 def test_gmres_v_only_basis_matches_z_basis():
     # right preconditioning: x0 + M^{-1}(V y) equals x0 + Z y with z_j = M^{-1} v_j; keeping V only costs
     # one more application per restart cycle (k = 6 forces several cycles)
