@@ -448,13 +448,16 @@ static int pick_rg(int nrhs, size_t per_rhs_bytes) {
 // ---------------------------------------------------------------------------
 // The whole sweep of Alg. 1.5 in one cooperative launch, as a dataflow over the elimination trees.
 // CTAs take tasks from one queue in topological order.  An up-the-tree task of a front waits until
-// every task of its children has finished (and, for the first panel solve's dependence on the one
-// before it in its problem's chain, until that whole solve has finished; the chains of a batch of
-// independent problems are interleaved in the queue and run side by side); a down-the-tree task waits for its parent (the
-// root: for its own up-the-tree tasks).  A task only waits on tasks earlier in the queue, which are
-// held by running CTAs, and every CTA of a cooperative launch is resident, so the waits end.  Each
-// wait is bounded anyway: a CTA that gives up sets status[2] and stops; the others then give up
-// at their next wait.
+// every task of its children has finished (one counter per front, which its children's tasks
+// increment); a front without children waits for the previous panel solve of its problem's chain
+// (the chains of a batch of independent problems are interleaved in the queue and run side by
+// side), so every front does, through its descendants.  A down-the-tree task waits for its parent
+// (the root: for its own up-the-tree tasks).  A task only waits on tasks earlier in the queue.  A
+// CTA claims its tasks in queue order, one ahead of the task it runs; the earliest unfinished task
+// is therefore the one some CTA runs (a CTA holding it only as its next task would be running an
+// earlier unfinished one), every task it waits for has finished, and since every CTA of a
+// cooperative launch is resident, the sweep progresses.  Each wait is bounded anyway: a CTA that
+// gives up sets status[2] and stops; the others then give up at their next wait.
 // ---------------------------------------------------------------------------
 constexpr long long kWaitCycles = 4000000000LL;   // SM clock cycles: about two seconds at 2 GHz
 constexpr long long kWaitSpins = 400000000LL;     // and a hard cap on polls, whatever the clock does
@@ -510,11 +513,18 @@ __device__ __forceinline__ void prefetch_task(const SolveTask tk, const int dir,
 constexpr int kMaxSweepShapes = 4, kMaxSweepSteps = 512, kMaxSweepPanels = 256;
 constexpr int kSweepThreads = 256;
 
+// one 16-byte asynchronous copy global -> shared (completed by cp_async_wait_all of the same thread)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 template <typename T, int RG>
 __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int s_idx, s_next, s_ok, s_dir, s_R;
-  __shared__ SolveTask s_tk;
+  __shared__ __align__(16) QueueEntry s_q[2];   // the current task's queue entry and the next one's
+  __shared__ int s_idx, s_ok;
   __shared__ SolveCtx<T> s_cx;      // this task's panel solve, filled by thread 0
   __shared__ ShapeDev s_shape[kMaxSweepShapes];
   __shared__ SweepStep s_step[kMaxSweepSteps];
@@ -527,111 +537,96 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs<T> a) {
     for (int i = threadIdx.x; i < a.nsteps; i += blockDim.x) s_step[i] = a.steps[i];
     for (int i = threadIdx.x; i < a.npanels; i += blockDim.x) s_panel[i] = a.panels[i];
   }
+  unsigned* head = a.ctr;
+  unsigned* step_done = a.ctr + kSweepStepCounters;
+  const int nrg = (a.cx.nrhs + RG - 1) / RG;
+  // Thread 0 holds the index of this CTA's current task and of its next one: the one after is claimed
+  // while the current one waits and runs, and the next one's queue entry is copied into the other
+  // shared-memory slot asynchronously, so that taking a task costs no dependent global load.
+  int cur = 0, nxt = 0, buf = 0;
   if (threadIdx.x == 0) {
-    s_next = (int)atomicAdd(a.queue_head, 1u);
+    cur = (int)atomicAdd(head, 1u);
+    nxt = (int)atomicAdd(head, 1u);
+    if (cur < a.nqueue) s_q[0] = a.queue[cur];
     s_cx = a.cx;   // fields common to every task; thread 0 sets the per-task ones below
   }
-  __syncthreads();
-  const int nrg = (a.cx.nrhs + RG - 1) / RG;
-  // thread 0 only: the current task's queue entry, task, front base and step counter base.  They
-  // are loaded for the next task while this one signals its completion, so a task's dependency
-  // check starts without a chain of dependent global loads.
-  QueueEntry ce{};
-  SolveTask ctk{};
-  int c_fb = 0, c_sfb = 0, c_idx = -1;
-  auto fetch = [&](int i) {
-    ce = a.queue[i];
-    ctk = a.tasks[ce.task];
-    const int panel = tab_smem ? s_step[ce.step].panel : a.steps[ce.step].panel;
-    const int shape = tab_smem ? s_panel[panel].shape : a.panels[panel].shape;
-    c_fb = a.front_base[shape];
-    c_sfb = a.step_front_base[ce.step];
-    c_idx = i;
-  };
   for (;;) {
-    if (threadIdx.x == 0) s_idx = s_next;
-    __syncthreads();
-    const int idx = s_idx;
-    if (idx >= a.nqueue) break;
     if (threadIdx.x == 0) {
-      if (c_idx != idx) fetch(idx);
-      s_next = (int)atomicAdd(a.queue_head, 1u);   // next task, fetched while this one runs
-      const SweepStep sp = tab_smem ? s_step[ce.step] : a.steps[ce.step];
-      const PanelSweep pi = tab_smem ? s_panel[sp.panel] : a.panels[sp.panel];
-      SolveCtx<T>& cx = s_cx;
-      cx.sh = tab_smem ? s_shape[pi.shape] : a.shapes[pi.shape];
-      cx.G = a.factor + pi.gbase;
-      cx.z0 = pi.z0;
-      cx.z1 = pi.z1;
-      cx.lead = pi.lead;
-      cx.has_prev = pi.has_prev;
-      cx.has_next = pi.has_next;
-      cx.mode = sp.mode;
-      if (a.nprobs > 1) {
-        // the problem's own vector block, coupling tables and work vectors
-        const ProblemSweep& pr = a.probs[sp.prob];
-        cx.u = a.cx.u + pr.off1 * a.cx.nrhs;
-        cx.N = pr.N;
-        cx.nz = pr.nz;
-        cx.s1n = pr.s1n;
-        cx.s2n = pr.s2n;
-        cx.s3h = pr.s3h;
-        cx.inv_h2 = pr.inv_h2;
-        cx.xf = a.cx.xf + (int64_t)sp.prob * a.cx.n_loc * a.cx.nrhs;
-        cx.xb = a.cx.xb + (int64_t)sp.prob * a.cx.n_loc * a.cx.nrhs;
-        cx.upd = a.cx.upd + (int64_t)sp.prob * a.cx.upd_ld * a.cx.nrhs;
+      s_idx = cur;
+      if (cur < a.nqueue) {
+        const QueueEntry& e = s_q[buf];
+        const SweepStep sp = tab_smem ? s_step[e.step] : a.steps[e.step];
+        const PanelSweep pi = tab_smem ? s_panel[sp.panel] : a.panels[sp.panel];
+        SolveCtx<T>& cx = s_cx;
+        cx.sh = tab_smem ? s_shape[pi.shape] : a.shapes[pi.shape];
+        cx.G = a.factor + pi.gbase;
+        cx.z0 = pi.z0;
+        cx.z1 = pi.z1;
+        cx.lead = pi.lead;
+        cx.has_prev = pi.has_prev;
+        cx.has_next = pi.has_next;
+        cx.mode = sp.mode;
+        if (a.nprobs > 1) {
+          // the problem's own vector block, coupling tables and work vectors
+          const ProblemSweep& pr = a.probs[sp.prob];
+          cx.u = a.cx.u + pr.off1 * a.cx.nrhs;
+          cx.N = pr.N;
+          cx.nz = pr.nz;
+          cx.s1n = pr.s1n;
+          cx.s2n = pr.s2n;
+          cx.s3h = pr.s3h;
+          cx.inv_h2 = pr.inv_h2;
+          cx.xf = a.cx.xf + (int64_t)sp.prob * a.cx.n_loc * a.cx.nrhs;
+          cx.xb = a.cx.xb + (int64_t)sp.prob * a.cx.n_loc * a.cx.nrhs;
+          cx.upd = a.cx.upd + (int64_t)sp.prob * a.cx.upd_ld * a.cx.nrhs;
+        }
       }
-      s_tk = ctk;
-      s_dir = ce.dir;
-      s_R = ce.R;
     }
     __syncthreads();
-    prefetch_task<T>(s_tk, s_dir, s_cx);
+    if (s_idx >= a.nqueue) break;
+    const QueueEntry& e = s_q[buf];
+    const SolveTask tk{e.sn, e.r0, e.r1};
+    const int dir = e.dir, R = e.R;
+    int after = 0;
     if (threadIdx.x == 0) {
-      const SolveCtx<T>& cx = s_cx;
-      const unsigned* up = a.done_up + c_sfb;
-      const unsigned* down = a.done_down + c_sfb;
-      bool ok = true;
-      if (ce.dir == 0) {
-        const int prev = a.step_prev ? a.step_prev[ce.step] : ce.step - 1;
-        if (prev >= 0) ok = wait_count(a.step_done + prev, (unsigned)a.step_tasks[prev], a.status, a.sticky);
-        for (int c = cx.sh.child_ptr[ctk.sn]; ok && c < cx.sh.child_ptr[ctk.sn + 1]; ++c) {
-          const int ch = cx.sh.child_idx[c];
-          ok = wait_count(up + ch, (unsigned)a.ntask_up[c_fb + ch], a.status, a.sticky);
-        }
-      } else if (ce.dir == kDirUpB) {   // the front's own first phase up
-        ok = wait_count(up + ctk.sn, (unsigned)a.ntask_upA[c_fb + ctk.sn], a.status, a.sticky);
-      } else if (ce.dir == kDirDownB) {   // the front's own first phase down
-        ok = wait_count(down + ctk.sn, (unsigned)a.ntask_downA[c_fb + ctk.sn], a.status, a.sticky);
-      } else {
-        const int par = cx.sh.parent[ctk.sn];
-        ok = par >= 0 ? wait_count(down + par, (unsigned)a.ntask_down[c_fb + par], a.status, a.sticky)
-                      : wait_count(up + ctk.sn, (unsigned)a.ntask_up[c_fb + ctk.sn], a.status, a.sticky);
+      after = (int)atomicAdd(head, 1u);   // the task after the next one (its index is read at the end)
+      if (nxt < a.nqueue) {
+        const char* src = reinterpret_cast<const char*>(a.queue + nxt);
+        char* dst = reinterpret_cast<char*>(&s_q[buf ^ 1]);
+        cp_async16(dst, src);
+        cp_async16(dst + 16, src + 16);
+        cp_async16(dst + 32, src + 32);
       }
+    }
+    prefetch_task<T>(tk, dir, s_cx);
+    if (threadIdx.x == 0) {
+      const bool ok = e.wait < 0 || wait_count(a.ctr + e.wait, e.target, a.status, a.sticky);
       __threadfence();
       s_ok = ok;
     }
     __syncthreads();
     if (!s_ok) break;
-    const SolveTask tk = s_tk;
-    const int dir = s_dir;
     const bool tri = s_cx.si == PSP_SI_NONE;
     for (int g = 0; g < nrg; ++g) {
       if (dir == 0 && tri) fwd_tri_task<T, RG>(tk, g * RG, s_cx, smem_raw);
-      else if (dir == 0 || dir == kDirUpB) fwd_task<T, RG>(tk, g * RG, s_cx, s_R, smem_raw, dir == 0 ? 0 : 1, a.chunk);
+      else if (dir == 0 || dir == kDirUpB) fwd_task<T, RG>(tk, g * RG, s_cx, R, smem_raw, dir == 0 ? 0 : 1, a.chunk);
       else if (dir == kDirDownB && tri) bwd_tri_task<T, RG>(tk, g * RG, s_cx, smem_raw);
       else bwd_task<T, RG>(tk, g * RG, s_cx, smem_raw, dir == 1 ? 0 : 1, a.chunk);
       __syncthreads();
     }
     if (threadIdx.x == 0) {
-      // completion counters of this task's step and front, then the next task's tables
+      // completion counters of this task's front (and of its parent's children, up the tree) and step
       __threadfence();
-      atomicAdd((dir == 0 || dir == kDirUpB ? a.done_up : a.done_down) + c_sfb + tk.sn, 1u);
-      atomicAdd(a.step_done + ce.step, 1u);
-      const int nx = s_next;
-      if (nx < a.nqueue) fetch(nx);
+      atomicAdd(a.ctr + e.done, 1u);
+      if (e.kids >= 0) atomicAdd(a.ctr + e.kids, 1u);
+      atomicAdd(step_done + e.step, 1u);
+      cp_async_wait_all();   // the next task's entry has landed
+      cur = nxt;
+      nxt = after;
     }
+    buf ^= 1;   // every thread: the next task's entry is in the other slot
   }
+  if (threadIdx.x == 0) cp_async_wait_all();
 }
 
 template <typename T, int RG>

@@ -280,12 +280,10 @@ struct psp_ctx_s {
   DevBuf d_stasks;
   // persistent sweep plan
   struct SweepPlan {
-    DevBuf steps, queue, meta;
+    DevBuf steps, queue;
     std::vector<SweepStep> hsteps;
     int nsteps = 0, nqueue = 0;
-    // meta layout: front_base | ntask_up | ntask_down | step_front | step_tasks | step_prev
-    int64_t o_up = 0, o_down = 0, o_upA = 0, o_downA = 0, o_step_front = 0, o_step_tasks = 0, o_step_prev = 0;
-    int64_t nfront_steps = 0;                 // fronts summed over the steps (counter words per direction)
+    int64_t nfront_steps = 0;                 // fronts summed over the steps
     double entries = 0, vec = 0;              // algorithmic factor entries / vector words per sweep
   };
   SweepPlan plans[3];              // 0: Alg. 1.5 over the handle's panels; 1: its forward part; 2: its backward part
@@ -1173,7 +1171,6 @@ static void plan_solve(psp_ctx_s* X, cudaStream_t st) {
           lastq[q] = (int)steps.size();
           steps.push_back(chain[q][t]);
         }
-    std::vector<QueueEntry> queue;
     std::vector<int> step_front(steps.size() + 1, 0), step_tasks(steps.size(), 0);
     SP.entries = 0;
     SP.vec = 0;
@@ -1183,17 +1180,68 @@ static void plan_solve(psp_ctx_s* X, cudaStream_t st) {
       step_tasks[k] = shape_tasks[si];
       SP.entries += shape_entries[si];
       SP.vec += shape_vec[si];
+    }
+    const int64_t nfs = step_front[steps.size()];
+    // counter words: head | status[4] | step_done[nsteps] | done_up[nfs] | done_down[nfs] | kids_up[nfs]
+    const int64_t o_step = kSweepStepCounters, o_up = o_step + (int64_t)steps.size(), o_down = o_up + nfs,
+                  o_kids = o_down + nfs, words = o_kids + nfs;
+    if (words > INT_MAX) throw Error{PSP_ERR_ARG, "sweep plan too large"};
+    std::vector<QueueEntry> queue;
+    for (size_t k = 0; k < steps.size(); ++k) {
+      const int si = X->shape_of[steps[k].panel];
+      const Shape& sh = X->shapes[si];
+      const int fb = front_base[si], sfb = step_front[k];
+      const int prev = step_prev[k];
+      // a front without children waits for the previous panel solve of its chain (the tasks of a
+      // front with children wait for those, which waited for it)
+      const unsigned prev_target =
+          prev >= 0 ? (unsigned)step_tasks[prev] + (X->test_sweep_stall && prev == 0 ? 1u : 0u) : 0u;
+      auto entry = [&](const SolveTask& tk, int dir, int R) {
+        QueueEntry e{};
+        e.step = (int)k;
+        e.sn = tk.sn;
+        e.r0 = tk.r0;
+        e.r1 = tk.r1;
+        e.dir = (short)dir;
+        e.R = (short)R;
+        const int sn = tk.sn, par = sh.parent[sn];
+        const bool up = dir == 0 || dir == kDirUpB;
+        e.done = (int)((up ? o_up : o_down) + sfb + sn);
+        e.kids = up && par >= 0 ? (int)(o_kids + sfb + par) : -1;
+        e.wait = -1;
+        if (dir == 0) {
+          unsigned kids = 0;
+          for (int c = sh.child_ptr[sn]; c < sh.child_ptr[sn + 1]; ++c) kids += (unsigned)ntask_up[fb + sh.child_idx[c]];
+          if (kids > 0) {
+            e.wait = (int)(o_kids + sfb + sn);
+            e.target = kids;
+          } else if (prev >= 0) {
+            e.wait = (int)(o_step + prev);
+            e.target = prev_target;
+          }
+        } else if (dir == kDirUpB) {   // the front's own first phase up
+          e.wait = (int)(o_up + sfb + sn);
+          e.target = (unsigned)ntask_upA[fb + sn];
+        } else if (dir == kDirDownB) {   // the front's own first phase down
+          e.wait = (int)(o_down + sfb + sn);
+          e.target = (unsigned)ntask_downA[fb + sn];
+        } else if (par >= 0) {   // down: the parent's down tasks
+          e.wait = (int)(o_down + sfb + par);
+          e.target = (unsigned)ntask_down[fb + par];
+        } else {   // the root, down: its own up tasks
+          e.wait = (int)(o_up + sfb + sn);
+          e.target = (unsigned)ntask_up[fb + sn];
+        }
+        queue.push_back(e);
+      };
       const auto& plan = X->splan[si];
       for (size_t lv = 0; lv < plan.size(); ++lv) {
-        for (int t = 0; t < plan[lv].nfwd; ++t)
-          queue.push_back({(int)k, (int)(plan[lv].fwd_off + t), 0, (short)plan[lv].R});
-        for (int t = 0; t < plan[lv].nfwdB; ++t)
-          queue.push_back({(int)k, (int)(plan[lv].fwdB_off + t), (short)kDirUpB, (short)plan[lv].R});
+        for (int t = 0; t < plan[lv].nfwd; ++t) entry(tasks[plan[lv].fwd_off + t], 0, plan[lv].R);
+        for (int t = 0; t < plan[lv].nfwdB; ++t) entry(tasks[plan[lv].fwdB_off + t], kDirUpB, plan[lv].R);
       }
       for (int lv = (int)plan.size() - 1; lv >= 0; --lv) {
-        for (int t = 0; t < plan[lv].nbwd; ++t) queue.push_back({(int)k, (int)(plan[lv].bwd_off + t), 1, 0});
-        for (int t = 0; t < plan[lv].nbwdB; ++t)
-          queue.push_back({(int)k, (int)(plan[lv].bwdB_off + t), (short)kDirDownB, 0});
+        for (int t = 0; t < plan[lv].nbwd; ++t) entry(tasks[plan[lv].bwd_off + t], 1, 0);
+        for (int t = 0; t < plan[lv].nbwdB; ++t) entry(tasks[plan[lv].bwdB_off + t], kDirDownB, 0);
       }
     }
     SP.hsteps = steps;
@@ -1201,29 +1249,8 @@ static void plan_solve(psp_ctx_s* X, cudaStream_t st) {
     SP.nqueue = (int)queue.size();
     upload_async(SP.steps, steps, st);
     upload_async(SP.queue, queue, st);
-    // metadata: front_base | ntask_up | ntask_down | ntask_upA | ntask_downA | step_front | step_tasks |
-    // step_prev
-    std::vector<int> meta;
-    meta.insert(meta.end(), front_base.begin(), front_base.end());
-    SP.o_up = (int64_t)meta.size();
-    meta.insert(meta.end(), ntask_up.begin(), ntask_up.end());
-    SP.o_down = (int64_t)meta.size();
-    meta.insert(meta.end(), ntask_down.begin(), ntask_down.end());
-    SP.o_upA = (int64_t)meta.size();
-    meta.insert(meta.end(), ntask_upA.begin(), ntask_upA.end());
-    SP.o_downA = (int64_t)meta.size();
-    meta.insert(meta.end(), ntask_downA.begin(), ntask_downA.end());
-    SP.o_step_front = (int64_t)meta.size();
-    meta.insert(meta.end(), step_front.begin(), step_front.end());
-    SP.o_step_tasks = (int64_t)meta.size();
-    meta.insert(meta.end(), step_tasks.begin(), step_tasks.end());
-    if (X->test_sweep_stall && steps.size() > 1) meta[SP.o_step_tasks] += 1;   // step 0 never "completes"
-    SP.o_step_prev = (int64_t)meta.size();
-    meta.insert(meta.end(), step_prev.begin(), step_prev.end());
-    upload_async(SP.meta, meta, st);
-    SP.nfront_steps = step_front[steps.size()];
-    // counters zeroed before every sweep: head | status[4] | step_done[nsteps] | done_up | done_down
-    sync_words = std::max(sync_words, 1 + 4 + steps.size() + 2 * (size_t)SP.nfront_steps);
+    SP.nfront_steps = nfs;
+    sync_words = std::max(sync_words, (size_t)words);
   }
   std::vector<ProblemSweep> pss;
   for (const auto& pr : X->probs) {
@@ -1331,29 +1358,16 @@ static void apply_core(psp_ctx_s* X, double2* u, int nrhs, T* xf, T* xb, T* upd,
     sa.steps = SP.steps.as<SweepStep>();
     sa.panels = X->d_sweep_panels.as<PanelSweep>();
     sa.shapes = X->d_shapes.as<ShapeDev>();
-    sa.tasks = tasks;
     sa.factor = X->d_factor.as<T>();
     sa.queue = SP.queue.as<QueueEntry>();
     sa.nqueue = SP.nqueue;
-    const int* meta = SP.meta.as<int>();
-    sa.front_base = meta;
-    sa.ntask_up = meta + SP.o_up;
-    sa.ntask_down = meta + SP.o_down;
-    sa.ntask_upA = meta + SP.o_upA;
-    sa.ntask_downA = meta + SP.o_downA;
-    sa.step_front_base = meta + SP.o_step_front;
-    sa.step_tasks = meta + SP.o_step_tasks;
     sa.nprobs = np;
     sa.probs = X->d_sweep_probs.as<ProblemSweep>();
-    sa.step_prev = np > 1 ? meta + SP.o_step_prev : nullptr;
     unsigned* sync = X->d_sweep_sync.as<unsigned>();
-    sa.queue_head = sync;
+    sa.ctr = sync;
     sa.status = reinterpret_cast<int*>(sync + 1);
     sa.sticky = X->d_status.as<int>() + 2;
-    sa.step_done = sync + 5;
-    sa.done_up = sync + 5 + SP.nsteps;
-    sa.done_down = sa.done_up + SP.nfront_steps;
-    const size_t words = 5 + (size_t)SP.nsteps + 2 * (size_t)SP.nfront_steps;
+    const size_t words = kSweepStepCounters + (size_t)SP.nsteps + 3 * (size_t)SP.nfront_steps;
     int rc = -1;
     if (SP.nsteps == 0) rc = 0;   // an empty part (the backward part of a block holding the last panel alone)
     else if (X->persistent_sweep) {

@@ -266,16 +266,27 @@ struct LevelSweep {
   int nfwd, nbwd, R, pad_;
 };
 // one entry of the sweep's task queue (topological order: panel solves in Alg. 1.5 order; inside
-// one, the up-the-tree tasks level by level, then the down-the-tree tasks from the root)
+// one, the up-the-tree tasks level by level, then the down-the-tree tasks from the root).  An entry
+// carries its one dependency and the counters it signals, so that a CTA takes a task with a single
+// 48-byte read.  Counters are words of the sweep's counter array (zeroed before every sweep):
+//   [0] dequeue head, [1, 5) status, then per step the tasks completed, then per step and front the
+//   up tasks completed, the down tasks completed and the up tasks of the front's children completed.
 struct QueueEntry {
   int step;                     // panel solve index
-  int task;                     // index into the shape's SolveTask list
+  int sn, r0, r1;               // the task: rows (up) or columns (down) [r0, r1) of front sn
+  int wait;                     // counter the task waits for (-1: none) ...
+  unsigned target;              // ... until it reaches this count
+  int done;                     // counter of the front's own completed tasks (this direction)
+  int kids;                     // counter of the parent's children's completed up tasks (-1: none)
   short dir;                    // 0 up the tree, 1 down the tree; 2 / 3 the second phase up / down of a front
                                 // whose factor keeps L_BL (the first phase is then 0 / 1)
   short R;                      // rows per up-the-tree task
+  int pad_[3];
 };
+static_assert(sizeof(QueueEntry) == 48, "queue entries are copied as three 16-byte words");
 // second phases of a front (factors that keep L_BL rather than L_BL inv(L_TL))
 constexpr int kDirUpB = 2, kDirDownB = 3;
+constexpr int kSweepStepCounters = 5;   // first word of the per-step counters
 template <typename T>
 struct SweepArgs {
   SolveCtx<T> cx;               // fields common to every panel (vectors, sizes, coupling tables); for a batch
@@ -284,27 +295,15 @@ struct SweepArgs {
   const SweepStep* steps;
   const PanelSweep* panels;
   const ShapeDev* shapes;
-  const SolveTask* tasks;
   const T* factor;
   const QueueEntry* queue;
   int nqueue;
-  const int* ntask_up;          // per shape-front: number of up / down tasks (shape offset: front_base)
-  const int* ntask_down;
-  const int* ntask_upA;         // per shape-front: tasks of the first phase up / down (two-phase fronts)
-  const int* ntask_downA;
-  const int* front_base;        // per shape: offset of its fronts in ntask_up / ntask_down
-  const int* step_front_base;   // per step: offset of its fronts in the done counters
-  const int* step_tasks;        // per step: number of tasks
-  unsigned* queue_head;         // dequeue counter (zeroed per sweep)
-  unsigned* done_up;            // per step-front completed up tasks (zeroed per sweep)
-  unsigned* done_down;
-  unsigned* step_done;          // per step completed tasks (zeroed per sweep)
-  int* status;                  // status[2] set when a wait gave up
+  unsigned* ctr;                // counter array (layout above)
+  int* status;                  // status[2] set when a wait gave up (= ctr + 1)
   int* sticky;                  // also set then; kept until the host reads it (psp_check_status)
   // batches of independent problems (nprobs > 1): each problem's steps form their own chain
   int nprobs;
   const ProblemSweep* probs;    // per problem; cx's vectors and work vectors are offset per problem
-  const int* step_prev;         // per step: the step it follows (-1: none); nullptr: step - 1
   int chunk;                    // vector entries a task stages in shared memory at a time (set by launch_sweep)
 };
 // returns 0 on success, -1 when a cooperative launch is not possible, else a cudaError_t; smax / ldmax:
