@@ -19,7 +19,8 @@ the line carries:
   batch16      16 independent problems of uneven size in one batched handle, 8 shots each, complex64;
   cpu_baseline the CPU oracle on all host cores, a bounded sample extrapolated to one solve.
 `--no-mixed`, `--no-extra` (skip salt256 / layered200 / batch16) and `--no-cpu-baseline` skip parts.
-`--workload batch16` prints a full line for the batch instead.  `--impl reference` times the
+`--workload batch16` prints a full line for the batch instead; `--workload gamma` prints the waveguide
+model's GMRES iterations against PML thickness (§3).  `--impl reference` times the
 complex128 CPU oracle on a bounded sample of the default workload per step (see reference_main).
 """
 from __future__ import annotations
@@ -613,7 +614,8 @@ def gpu_main(a):
         tuning[prec] = t
         setup_tuning[prec] = ts
         sched[prec] = {"sweep_level_tasks": t["sweep_level_tasks"], "sweep_ctas_per_sm": t["sweep_ctas_per_sm"],
-                       "sweep_rhs_group": t["sweep_rhs_group"], "selective_inversion": ts["selective_inversion"],
+                       "sweep_rhs_group": t["sweep_rhs_group"], "sweep_min_rows": t["sweep_min_rows"],
+                       "selective_inversion": ts["selective_inversion"],
                        "tc_min_dim": ts["tc_min_dim"] if prec == "c64" else 0}
     if a.no_tune and a.si != "auto":
         for prec in ("c128", "c64"):
@@ -918,6 +920,45 @@ def salt_main(a):
     P.close()
 
 
+def gamma_main(a):
+    """PML thickness (§3): the waveguide model with the paper's settings (4-plane panels, damping 7,
+    PML amplitude 2 relative to its fastest speed, its four forcing functions, 10 points per
+    wavelength), GMRES(20) to 1e-5 on all four, for gamma = 5, 6, 8, 10 PML points at --n and at
+    twice --n (twice the frequency at the same resolution per wavelength).  The paper reports 52
+    iterations with 5 points at 500^3 and 27 with 6, and that half the frequency needs the 27 with 5
+    points.  One JSON object; complex64 fronts and sweeps, complex128 GMRES."""
+    import torch
+
+    from paper_1204_0111_gb300 import psp
+    from paper_1204_0111_gb300 import workloads as wl
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    rows = []
+    for n in (a.n, 2 * a.n):
+        for gamma in (5, 6, 8, 10):
+            w = wl.cube_paper("waveguide", n, gamma=gamma)
+            c_dev = torch.from_numpy(w.c).to(dev)
+            f = torch.from_numpy(w.forcing).to(dev)
+            u = torch.zeros_like(f)
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record()
+            P = psp.SweepingPreconditioner(c_dev, w.h, w.omega, w.gamma, w.panel_depth, pad=w.pad, leaf=w.leaf,
+                                           pml_C=w.pml_C, alpha=w.alpha, precision="c64")
+            e1.record()
+            info = P.solve(f, u, tol=1e-5, k=20, maxit=400)
+            e2.record()
+            torch.cuda.synchronize()
+            rows.append({"n": n, "gamma": gamma, "iterations": info["iterations"], "converged": info["converged"],
+                         "relres_max": info["relres_max"], "setup_ms": e0.elapsed_time(e1),
+                         "solve_ms": e1.elapsed_time(e2), "panels": P.info()["panels"]})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+            P.close()
+            del c_dev, f, u
+            torch.cuda.empty_cache()
+    print(json.dumps({"workload": "waveguide (paper §3), PML thickness sweep", "precision": "c64 fronts, c128 GMRES",
+                      "rhs": "the paper's four forcing functions", "gmres_k": 20, "tol": 1e-5, "rows": rows}))
+
+
 def batch_main(a):
     import torch
     dev = torch.device("cuda", 0)
@@ -1005,10 +1046,11 @@ def main():
                     "weighs the setup against (lens100: 18 GMRES iterations, one application each)")
     ap.add_argument("--n", type=int, default=100, help="grid points per axis (100 = the benchmark workload; "
                     "smaller sizes are for profiling captures)")
-    ap.add_argument("--workload", choices=["lens", "batch16", "salt"], default="lens",
+    ap.add_argument("--workload", choices=["lens", "batch16", "salt", "gamma"], default="lens",
                     help="lens: the converging-lens problem of --n (default); batch16: 16 independent problems "
                          "in one batched handle, complex64; salt: the salt-body workload of --n alone (32 shots, "
-                         "GMRES(30), complex64), for profiling captures")
+                         "GMRES(30), complex64), for profiling captures; gamma: the waveguide model's iterations "
+                         "against PML thickness at --n and 2 --n")
     a = ap.parse_args()
     global GRID_N, WORKLOAD
     GRID_N = a.n
@@ -1021,6 +1063,8 @@ def main():
         batch_main(a)
     elif a.workload == "salt":
         salt_main(a)
+    elif a.workload == "gamma":
+        gamma_main(a)
     else:
         gpu_main(a)
 

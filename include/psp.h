@@ -143,6 +143,10 @@ typedef struct {
   void (*dev_free)(void* ptr, void* ctx);
   void* alloc_ctx;
   int selective_inversion; /* psp_si_mode, default PSP_SI_EXTENDED */
+  int c64_diag_fp64;    /* complex64 factors only: 1 factors each 32 x 32 diagonal block of F_TL, and
+                           solves against it (the rows of L_BL and the block rows of inv(L_TL), §2.2),
+                           in complex128 arithmetic, rounding to complex64 only when storing; the
+                           products between blocks stay complex64.  0 (default): all complex64 */
 } psp_options;
 
 /* Per-solve report filled by psp_solve (host struct). */

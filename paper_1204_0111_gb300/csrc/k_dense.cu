@@ -17,11 +17,11 @@ constexpr int kNB = 32;  // diagonal block size of the blocked LDL^T and inverse
 // pivots is kept in status[4..5] as the bitwise complement of its double (atomicMax of the
 // complement = minimum of the non-negative value; 0 = no pivot yet).
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, typename C>
 __global__ void __launch_bounds__(256) k_diag_ldlt(const FrontTask<T>* __restrict__ fronts, const int* __restrict__ list,
                                                    int kb, double tiny, int* status) {
-  __shared__ T S[kNB][kNB + 1];  // S[col][row]
-  __shared__ T colv[kNB];
+  __shared__ C S[kNB][kNB + 1];  // S[col][row], in the compute precision C
+  __shared__ C colv[kNB];
   const FrontTask<T> ft = fronts[list[blockIdx.x]];
   const int ld = ft.s + ft.u;
   const int o = kb * kNB;
@@ -29,19 +29,19 @@ __global__ void __launch_bounds__(256) k_diag_ldlt(const FrontTask<T>* __restric
   T* B = ft.G + (int64_t)o * ld + o;
   for (int e = threadIdx.x; e < bs * bs; e += blockDim.x) {
     const int r = e % bs, c = e / bs;
-    if (r >= c) S[c][r] = B[(int64_t)c * ld + r];
+    if (r >= c) S[c][r] = CplxTraits<C>::from(to_c128(B[(int64_t)c * ld + r]));
   }
   __syncthreads();
   double dmin = INFINITY;
   for (int j = 0; j < bs; ++j) {
-    const T d = S[j][j];
+    const C d = S[j][j];
     if (threadIdx.x == 0) {
       if (fmax(fabs((double)d.x), fabs((double)d.y)) < tiny) atomicCAS(status, 0, (int)(1 + ft.gfid));
       dmin = fmin(dmin, hypot((double)d.x, (double)d.y));
     }
-    const T dinv = cdiv(CplxTraits<T>::one(), d);
+    const C dinv = cdiv(CplxTraits<C>::one(), d);
     for (int i = j + 1 + threadIdx.x; i < bs; i += blockDim.x) {
-      const T a = S[j][i];
+      const C a = S[j][i];
       colv[i] = a;
       S[j][i] = cmul(a, dinv);
     }
@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(256) k_diag_ldlt(const FrontTask<T>* __restric
   }
   for (int e = threadIdx.x; e < bs * bs; e += blockDim.x) {
     const int r = e % bs, c = e / bs;
-    if (r >= c) B[(int64_t)c * ld + r] = S[c][r];
+    if (r >= c) B[(int64_t)c * ld + r] = CplxTraits<T>::from(to_c128(S[c][r]));
   }
   if (threadIdx.x == 0 && dmin == dmin)   // a NaN pivot leaves the minimum alone (status[0] reports it if tiny)
     atomicMax(reinterpret_cast<unsigned long long*>(status + 4), ~(unsigned long long)__double_as_longlong(dmin));
@@ -66,11 +66,11 @@ __global__ void __launch_bounds__(256) k_diag_ldlt(const FrontTask<T>* __restric
 // Rows of F_TL below diagonal block kb:  X L_kk^T = F(r, block)  ->  F(r, block) := X D^{-1}.
 // One thread per row; L_kk and D in shared memory.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, typename C>
 __global__ void __launch_bounds__(64) k_panel_right(const FrontTask<T>* __restrict__ fronts,
                                                     const ColTask* __restrict__ tasks, int kb) {
-  __shared__ T L[kNB][kNB + 1];  // L[col][row]
-  __shared__ T dinv[kNB];
+  __shared__ C L[kNB][kNB + 1];  // L[col][row]
+  __shared__ C dinv[kNB];
   const ColTask tk = tasks[blockIdx.x];
   const FrontTask<T> ft = fronts[tk.front];
   const int ld = ft.s + ft.u;
@@ -79,36 +79,36 @@ __global__ void __launch_bounds__(64) k_panel_right(const FrontTask<T>* __restri
   const T* Bd = ft.G + (int64_t)o * ld + o;
   for (int e = threadIdx.x; e < bs * bs; e += blockDim.x) {
     const int r = e % bs, c = e / bs;
-    L[c][r] = (r > c) ? Bd[(int64_t)c * ld + r] : CplxTraits<T>::zero();
+    L[c][r] = (r > c) ? CplxTraits<C>::from(to_c128(Bd[(int64_t)c * ld + r])) : CplxTraits<C>::zero();
   }
-  for (int c = threadIdx.x; c < bs; c += blockDim.x) dinv[c] = cdiv(CplxTraits<T>::one(), Bd[(int64_t)c * ld + c]);
+  for (int c = threadIdx.x; c < bs; c += blockDim.x) dinv[c] = cdiv(CplxTraits<C>::one(), CplxTraits<C>::from(to_c128(Bd[(int64_t)c * ld + c])));
   __syncthreads();
   const int r = tk.c0 + threadIdx.x;
   if (r >= tk.c1) return;
   T* row = ft.G + (int64_t)o * ld + r;
-  T x[kNB];
+  C x[kNB];
 #pragma unroll
   for (int c = 0; c < kNB; ++c) {
     if (c < bs) {
-      T v = row[(int64_t)c * ld];
+      C v = CplxTraits<C>::from(to_c128(row[(int64_t)c * ld]));
       for (int k = 0; k < c; ++k) cfms(v, x[k], L[k][c]);
       x[c] = v;
     }
   }
 #pragma unroll
   for (int c = 0; c < kNB; ++c)
-    if (c < bs) row[(int64_t)c * ld] = cmul(x[c], dinv[c]);
+    if (c < bs) row[(int64_t)c * ld] = CplxTraits<T>::from(to_c128(cmul(x[c], dinv[c])));
 }
 
 // ---------------------------------------------------------------------------
 // Block row kb of W (the inverse of L_TL under construction): W(kb, cols) := L_kk^{-1} W(kb, cols).
 // A 32 x 64 tile is staged through shared memory; one thread per column.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, typename C>
 __global__ void __launch_bounds__(64) k_panel_left(const FrontTask<T>* __restrict__ fronts,
                                                    const ColTask* __restrict__ tasks, int kb) {
-  __shared__ T L[kNB][kNB + 1];   // L[col][row]
-  __shared__ T Wt[64][kNB + 1];   // Wt[col][row]
+  __shared__ C L[kNB][kNB + 1];   // L[col][row]
+  __shared__ C Wt[64][kNB + 1];   // Wt[col][row]
   const ColTask tk = tasks[blockIdx.x];
   const FrontTask<T> ft = fronts[tk.front];
   const int ld = ft.s + ft.u;
@@ -118,18 +118,18 @@ __global__ void __launch_bounds__(64) k_panel_left(const FrontTask<T>* __restric
   const T* Bd = ft.G + (int64_t)o * ld + o;
   for (int e = threadIdx.x; e < bs * bs; e += blockDim.x) {
     const int r = e % bs, c = e / bs;
-    L[c][r] = (r > c) ? Bd[(int64_t)c * ld + r] : CplxTraits<T>::zero();
+    L[c][r] = (r > c) ? CplxTraits<C>::from(to_c128(Bd[(int64_t)c * ld + r])) : CplxTraits<C>::zero();
   }
   T* W0 = ft.W + (int64_t)tk.c0 * ft.s + o;
   for (int e = threadIdx.x; e < bs * ncol; e += blockDim.x) {
     const int r = e % bs, c = e / bs;
-    Wt[c][r] = W0[(int64_t)c * ft.s + r];
+    Wt[c][r] = CplxTraits<C>::from(to_c128(W0[(int64_t)c * ft.s + r]));
   }
   __syncthreads();
   const int c = threadIdx.x;
   if (c < ncol) {
     for (int r = 1; r < bs; ++r) {
-      T v = Wt[c][r];
+      C v = Wt[c][r];
       for (int k = 0; k < r; ++k) cfms(v, L[k][r], Wt[c][k]);
       Wt[c][r] = v;
     }
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(64) k_panel_left(const FrontTask<T>* __restric
   __syncthreads();
   for (int e = threadIdx.x; e < bs * ncol; e += blockDim.x) {
     const int r = e % bs, cc = e / bs;
-    W0[(int64_t)cc * ft.s + r] = Wt[cc][r];
+    W0[(int64_t)cc * ft.s + r] = CplxTraits<T>::from(to_c128(Wt[cc][r]));
   }
 }
 
@@ -308,18 +308,28 @@ __global__ void __launch_bounds__(256) k_scale_zd(const FrontTask<T>* __restrict
   }
 }
 
+// wide: the diagonal blocks' LDL^T and the solves against them in complex128 whatever the storage
+// precision (the complex64 factors' FP64 refinement of the diagonal blocks)
 template <typename T>
 void launch_diag_ldlt(const FrontTask<T>* fronts, const int* list, int nlist, int kb, double tiny, int* status,
-                      cudaStream_t st) {
-  if (nlist > 0) k_diag_ldlt<T><<<nlist, 256, 0, st>>>(fronts, list, kb, tiny, status);
+                      bool wide, cudaStream_t st) {
+  if (nlist <= 0) return;
+  if (wide) k_diag_ldlt<T, double2><<<nlist, 256, 0, st>>>(fronts, list, kb, tiny, status);
+  else k_diag_ldlt<T, T><<<nlist, 256, 0, st>>>(fronts, list, kb, tiny, status);
 }
 template <typename T>
-void launch_panel_right(const FrontTask<T>* fronts, const ColTask* tasks, int ntasks, int kb, cudaStream_t st) {
-  if (ntasks > 0) k_panel_right<T><<<ntasks, 64, 0, st>>>(fronts, tasks, kb);
+void launch_panel_right(const FrontTask<T>* fronts, const ColTask* tasks, int ntasks, int kb, bool wide,
+                        cudaStream_t st) {
+  if (ntasks <= 0) return;
+  if (wide) k_panel_right<T, double2><<<ntasks, 64, 0, st>>>(fronts, tasks, kb);
+  else k_panel_right<T, T><<<ntasks, 64, 0, st>>>(fronts, tasks, kb);
 }
 template <typename T>
-void launch_panel_left(const FrontTask<T>* fronts, const ColTask* tasks, int ntasks, int kb, cudaStream_t st) {
-  if (ntasks > 0) k_panel_left<T><<<ntasks, 64, 0, st>>>(fronts, tasks, kb);
+void launch_panel_left(const FrontTask<T>* fronts, const ColTask* tasks, int ntasks, int kb, bool wide,
+                       cudaStream_t st) {
+  if (ntasks <= 0) return;
+  if (wide) k_panel_left<T, double2><<<ntasks, 64, 0, st>>>(fronts, tasks, kb);
+  else k_panel_left<T, T><<<ntasks, 64, 0, st>>>(fronts, tasks, kb);
 }
 template <typename T>
 void launch_gemm(const GemmTask<T>* tasks, int ntasks, cudaStream_t st) {
@@ -335,9 +345,9 @@ void launch_scale_zd(const FrontTask<T>* fronts, const ColTask* tasks, int ntask
 }
 
 #define PSP_INST(T)                                                                                           \
-  template void launch_diag_ldlt<T>(const FrontTask<T>*, const int*, int, int, double, int*, cudaStream_t);    \
-  template void launch_panel_right<T>(const FrontTask<T>*, const ColTask*, int, int, cudaStream_t);            \
-  template void launch_panel_left<T>(const FrontTask<T>*, const ColTask*, int, int, cudaStream_t);             \
+  template void launch_diag_ldlt<T>(const FrontTask<T>*, const int*, int, int, double, int*, bool, cudaStream_t);    \
+  template void launch_panel_right<T>(const FrontTask<T>*, const ColTask*, int, int, bool, cudaStream_t);            \
+  template void launch_panel_left<T>(const FrontTask<T>*, const ColTask*, int, int, bool, cudaStream_t);             \
   template void launch_gemm<T>(const GemmTask<T>*, int, cudaStream_t);                                         \
   template void launch_copy_linv<T>(const FrontTask<T>*, const ColTask*, int, cudaStream_t);                 \
   template void launch_scale_zd<T>(const FrontTask<T>*, const ColTask*, int, cudaStream_t);

@@ -312,6 +312,7 @@ struct psp_ctx_s {
   bool has_history = false;
   int device = -1;          // CUDA device current at setup; every later call must run with it current
   bool use_tc = true;
+  bool diag_fp64 = false;   // complex64: diagonal blocks factored and applied in complex128
   int tc_min_dim = 64;
   int sweep_level_tasks = 608, sweep_ctas_per_sm = 8, sweep_rhs_group = 0, solve_rhs_group = 0, sweep_min_rows = 8;
   int gmres_basis = 0;   // 0 auto, 1 keep z_j, 2 V only
@@ -581,6 +582,7 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
     for (size_t li = lb; li < launches.size(); ++li) {
       const Launch& l = launches[li];
       if (l.count <= 0) continue;
+      const bool wide = X->prec == PSP_PREC_C64 && X->diag_fp64;
       const FrontTask<T>* Fl = F + (l.front_off - (int64_t)f0);
       X->stats.run(names[l.kind], st, 1, l.flops, l.bytes, [&] {
         switch (l.kind) {
@@ -589,9 +591,9 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
                                     X->d_boxops.as<BoxOp>(), d_upd_ptr.as<T*>(), d_upd_tile.as<int32_t>(),
                                     X->d_panel_shape.as<int32_t>(), st);
             break;
-          case DIAG: launch_diag_ldlt<T>(Fl, DL + (l.off - (int64_t)d0), l.count, l.kb, tiny, status, st); break;
-          case PRIGHT: launch_panel_right<T>(Fl, CT + (l.off - (int64_t)c0), l.count, l.kb, st); break;
-          case PLEFT: launch_panel_left<T>(Fl, CT + (l.off - (int64_t)c0), l.count, l.kb, st); break;
+          case DIAG: launch_diag_ldlt<T>(Fl, DL + (l.off - (int64_t)d0), l.count, l.kb, tiny, status, wide, st); break;
+          case PRIGHT: launch_panel_right<T>(Fl, CT + (l.off - (int64_t)c0), l.count, l.kb, wide, st); break;
+          case PLEFT: launch_panel_left<T>(Fl, CT + (l.off - (int64_t)c0), l.count, l.kb, wide, st); break;
           case GEMM: launch_gemm<T>(GT + (l.off - (int64_t)g0), l.count, st); break;
           case COPY: launch_copy_linv<T>(Fl, CT + (l.off - (int64_t)c0), l.count, st); break;
           case TCGEMM: launch_tc_gemm(TT + (l.off - (int64_t)t0), l.count, status, st); break;
@@ -2094,7 +2096,8 @@ static psp_status check_options(const psp_options* opt, psp_options* o) {
       (o->precision != PSP_PREC_C128 && o->precision != PSP_PREC_C64) ||
       (o->aux_mode != PSP_AUX_MOVING_PML && o->aux_mode != PSP_AUX_EXACT) || !(o->alpha >= 0) || !(o->pml_C >= 0) ||
       o->gmres_basis < 0 || o->gmres_basis > 2 || o->panel_begin < 0 || o->panel_count < 0 ||
-      (o->dev_alloc == nullptr) != (o->dev_free == nullptr) || o->selective_inversion < 0 || o->selective_inversion > 2)
+      (o->dev_alloc == nullptr) != (o->dev_free == nullptr) || o->selective_inversion < 0 || o->selective_inversion > 2 ||
+      o->c64_diag_fp64 < 0 || o->c64_diag_fp64 > 1)
     return fail(PSP_ERR_ARG, "bad options");
   return PSP_OK;
 }
@@ -2117,6 +2120,7 @@ static void init_options(psp_ctx_s* X, const psp_options& o) {
   X->stats.timing = o.collect_stats != 0;
   X->stats.mode = o.collect_stats;
   X->use_tc = o.tensor_cores != 0;
+  X->diag_fp64 = o.c64_diag_fp64 != 0;
   X->tc_min_dim = o.tc_min_dim > 0 ? o.tc_min_dim : 64;
   // measured on lens100: both precisions' sweeps are fastest at about 608 tasks per level
   X->sweep_level_tasks = o.sweep_level_tasks > 0 ? o.sweep_level_tasks : 608;

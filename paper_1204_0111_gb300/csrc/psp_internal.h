@@ -172,12 +172,12 @@ void launch_assemble_impl(const FrontTask<T>* fronts, const ColTask* tasks, int 
                           const BoxOp* boxops, T* const* upd_ptr, const int32_t* upd_tile, const int32_t* panel_shape,
                           cudaStream_t st);
 template <typename T>
-void launch_diag_ldlt(const FrontTask<T>* fronts, const int* list, int nlist, int kb, double tiny, int* status,
+void launch_diag_ldlt(const FrontTask<T>* fronts, const int* list, int nlist, int kb, double tiny, int* status, bool wide,
                       cudaStream_t st);
 template <typename T>
-void launch_panel_right(const FrontTask<T>* fronts, const ColTask* tasks, int ntasks, int kb, cudaStream_t st);
+void launch_panel_right(const FrontTask<T>* fronts, const ColTask* tasks, int ntasks, int kb, bool wide, cudaStream_t st);
 template <typename T>
-void launch_panel_left(const FrontTask<T>* fronts, const ColTask* tasks, int ntasks, int kb, cudaStream_t st);
+void launch_panel_left(const FrontTask<T>* fronts, const ColTask* tasks, int ntasks, int kb, bool wide, cudaStream_t st);
 template <typename T>
 void launch_gemm(const GemmTask<T>* tasks, int ntasks, cudaStream_t st);
 // tensor-core path (complex64): operands packed once per front into TF32 planes, then tiles

@@ -40,7 +40,7 @@ class Options(ctypes.Structure):
                 ("gmres_basis", ctypes.c_int),
                 ("factor_every_panel", ctypes.c_int), ("panel_begin", ctypes.c_int), ("panel_count", ctypes.c_int),
                 ("dev_alloc", ctypes.c_void_p), ("dev_free", ctypes.c_void_p), ("alloc_ctx", ctypes.c_void_p),
-                ("selective_inversion", ctypes.c_int)]
+                ("selective_inversion", ctypes.c_int), ("c64_diag_fp64", ctypes.c_int)]
 
 
 # psp_options.dev_alloc / dev_free callback types
@@ -184,7 +184,8 @@ class SweepingPreconditioner:
                  precision="c128", faces=63, mode="moving", stream=None, collect_stats=0, tensor_cores=True,
                  tc_min_dim=0, sweep_level_tasks=0, sweep_ctas_per_sm=0, setup_temp_mb=0, sweep_rhs_group=0,
                  solve_rhs_group=0, test_sweep_stall=0, gmres_basis="auto", factor_every_panel=False,
-                 panels=None, allocator=None, selective_inversion="extended", sweep_min_rows=0):
+                 panels=None, allocator=None, selective_inversion="extended", sweep_min_rows=0,
+                 diag_fp64=False):
         nz, ny, nx = c.shape
         self.nx, self.ny, self.nz = nx, ny, nz
         self.N = nx * ny * nz
@@ -194,6 +195,7 @@ class SweepingPreconditioner:
                      sweep_level_tasks, sweep_ctas_per_sm, setup_temp_mb, sweep_rhs_group, solve_rhs_group)
         o.test_sweep_stall = int(test_sweep_stall)
         o.sweep_min_rows = int(sweep_min_rows)
+        o.c64_diag_fp64 = 1 if diag_fp64 else 0
         o.gmres_basis = {"auto": 0, "z": 1, "v": 2}[gmres_basis]
         o.factor_every_panel = 1 if factor_every_panel else 0
         if panels is not None:                   # (first, count): one block of a multi-GPU sweep

@@ -180,6 +180,43 @@ def test_complex64_path_solves_to_tolerance(case):
     assert np.linalg.norm(b - A @ u[0]) / np.linalg.norm(b) < 1e-5 and info["converged"] == 1
 
 
+@pytest.mark.parametrize("case", CASES[1:], ids=IDS[1:])
+def test_complex64_diagonal_blocks_in_fp64(case):
+    # complex64 factors whose diagonal blocks (their LDL^T and the solves against them) are computed in
+    # complex128: every stored front and the application stay within complex64 accuracy of the
+    # oracle, and on the fronts without children (whose inputs both paths round alike) the pivots of
+    # the first diagonal block agree with the oracle's more closely, on average, than the
+    # all-complex64 factorisation's do
+    c = torch.from_numpy(case.c).cuda()
+    kw = dict(pad=case.pad, leaf=case.leaf, pml_C=case.C, alpha=case.alpha, precision="c64", faces=case.faces)
+    Pw = psp.SweepingPreconditioner(c, case.h, case.omega, case.gamma, case.depth, diag_fp64=True, **kw)
+    Pn = psp.SweepingPreconditioner(c, case.h, case.omega, case.gamma, case.depth, **kw)
+    O = oracle_for(case)
+    worst, dw, dn = 0.0, [], []
+    for i in range(O.m):
+        sns = O.sym[i].supernodes
+        for f, fr in enumerate(O.fronts[i]):
+            Gw, s, u = Pw.export_front(i, f)
+            Gn, _, _ = Pn.export_front(i, f)
+            Linv = sla.solve_triangular(fr.L_TL, np.eye(s), lower=True, unit_diagonal=True)
+            exp = np.vstack([np.tril(Linv, -1) + np.diag(fr.d), fr.L_BL @ Linv])
+            got = Gw.copy()
+            got[:s] = np.tril(got[:s])
+            worst = max(worst, rel(got, exp))
+            if not sns[f].children:
+                b = min(s, 32)
+                dw.append(rel(np.diag(Gw[:b, :b]), fr.d[:b]))
+                dn.append(rel(np.diag(Gn[:b, :b]), fr.d[:b]))
+    assert worst < 1e-3, worst
+    assert dw and np.mean(dw) < np.mean(dn), (np.mean(dw), np.mean(dn))
+    r = wl.random_vector(case.N, 1, seed=5)
+    out = np.zeros_like(r)
+    Pw.apply(r, out)
+    assert rel(out, O.apply(r)) < 1e-3
+    Pw.close()
+    Pn.close()
+
+
 def test_single_panel_and_zero_pivot_free_small_grid():
     # panel depth >= nz: one auxiliary problem, M^{-1} = J^{-1}
     case = Case(np.ones((7, 5, 6)), 1.0 / 8, 5.0, 1, 50, leaf=8)
