@@ -77,8 +77,14 @@ typedef enum {
                           each front is one matrix-vector product per sweep direction (default) */
   PSP_SI_PAPER = 1,    /* G = [inv(L_TL); L_BL]: the paper's selective inversion; each front takes two dependent
                           products per direction, and setup skips the u s^2 / 2 products of L_BL inv(L_TL) */
-  PSP_SI_NONE = 2      /* G = [L_TL; L_BL]: no inversion; the sweep solves with L_TL by substitution, one CTA
+  PSP_SI_NONE = 2,     /* G = [L_TL; L_BL]: no inversion; the sweep solves with L_TL by substitution, one CTA
                           per front (complex64 fronts stay on CUDA cores) */
+  PSP_SI_TWO = 3       /* the paper's G = [inv(L_TL); L_BL] plus a second inverse of L_TL (§2.2, last
+                          paragraph: one inverse by columns, one by rows).  The first is built column by
+                          column (forward substitution, L X = I) and applied up the tree as inv(L_TL) w;
+                          the second row by row (backward substitution, X L = I) and applied down the
+                          tree as inv(L_TL)^T t, so each direction applies an inverse whose vectors were
+                          computed by a backward-stable solve.  s x s more factor storage per front */
 } psp_si_mode;
 
 typedef enum {
@@ -305,6 +311,15 @@ psp_status psp_info(psp_handle h, int* panels, int64_t* fronts, int64_t* factor_
 psp_status psp_export_front(psp_handle h, int panel, int supernode, double* buf, int* s, int* u);
 
 /*
+ * psp_export_second_inverse - for a handle in the form PSP_SI_TWO, copy one front's second inverse of
+ * L_TL (built row by row, X L_TL = I) to host memory: s x s column-major, complex128, unit lower (the
+ * diagonal and the upper part are written as stored: one and zero).  Call with buf = NULL to get s.
+ * Errors: PSP_ERR_ARG (bad panel or supernode, a front outside the handle's block of panels),
+ * PSP_ERR_STATE (the handle is not in the form PSP_SI_TWO or has no factorisation).
+ */
+psp_status psp_export_second_inverse(psp_handle h, int panel, int supernode, double* buf, int* s);
+
+/*
  * Per-kernel accounting of one handle (setup, applies, matvecs and solves issued through it).
  * Launch counts and algorithmic work are always kept; total_ms is filled for the kernels that the
  * handle's collect_stats selects (CUDA events around each such launch, on the launch stream).
@@ -357,7 +372,8 @@ psp_status psp_tune_sweep(psp_handle h, int nrhs, int reps, void* stream, psp_sw
  * psp_tune_setup - the paper has no counterpart: an autotuner for what the setup builds.  The paper
  * weighs selective inversion's dearer setup against its faster solves (§2.2, §3 Table 2); this call
  * measures that trade on the handle's own problem.  It re-factors the handle under each candidate
- * (the three psp_si_mode forms and, for complex64 tensor-core fronts, tc_min_dim 32 / 64 / 128),
+ * (the forms PSP_SI_EXTENDED, PSP_SI_PAPER and PSP_SI_NONE; the two-inverse form is a choice for
+ * accuracy, not speed, and is not among them; for complex64 tensor-core fronts tc_min_dim 32 / 64 / 128),
  * timing the setup (host clock, the factorisation synchronises) and one application to nrhs
  * right-hand sides (CUDA events on `stream`, after an untimed one), and keeps the candidate with
  * the least setup_ms + expected_applies x apply_ms; the handle ends factored that way.  Results

@@ -142,6 +142,48 @@ __global__ void __launch_bounds__(64) k_panel_left(const FrontTask<T>* __restric
 }
 
 // ---------------------------------------------------------------------------
+// Block column kb of the second inverse X of L_TL (two-inverse form, X L_TL = I row by row):
+// X(r, block) := X(r, block) L_kk^{-1} for rows r of the task, i.e. x L_kk = b by backward
+// substitution along each row.  One thread per row; L_kk in shared memory.
+// ---------------------------------------------------------------------------
+template <typename T, typename C>
+__global__ void __launch_bounds__(64) k_panel_rsolve(const FrontTask<T>* __restrict__ fronts,
+                                                     const ColTask* __restrict__ tasks, int kb) {
+  __shared__ C L[kNB][kNB + 1];  // L[col][row], strictly lower part of L_kk
+  const ColTask tk = tasks[blockIdx.x];
+  const FrontTask<T> ft = fronts[tk.front];
+  const int ld = ft.s + ft.u;
+  const int o = kb * kNB;
+  const int bs = min(kNB, ft.s - o);
+  const T* Bd = ft.G + (int64_t)o * ld + o;
+  for (int e = threadIdx.x; e < bs * bs; e += blockDim.x) {
+    const int r = e % bs, c = e / bs;
+    L[c][r] = (r > c) ? CplxTraits<C>::from(to_c128(Bd[(int64_t)c * ld + r])) : CplxTraits<C>::zero();
+  }
+  __syncthreads();
+  const int r = tk.c0 + threadIdx.x;
+  if (r >= tk.c1) return;
+  T* row = ft.W2 + (int64_t)o * ft.s + r;   // X(r, o + c) at row[c * s]
+  C x[kNB];
+#pragma unroll
+  for (int c = 0; c < kNB; ++c) x[c] = c < bs ? CplxTraits<C>::from(to_c128(row[(int64_t)c * ft.s])) : CplxTraits<C>::zero();
+  // x_c = b_c - sum_{k > c} x_k L(k, c), from the last column
+#pragma unroll
+  for (int c = kNB - 1; c >= 0; --c) {
+    if (c < bs) {
+      C v = x[c];
+#pragma unroll
+      for (int k = c + 1; k < kNB; ++k)
+        if (k < bs) cfms(v, x[k], L[c][k]);
+      x[c] = v;
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < kNB; ++c)
+    if (c < bs) row[(int64_t)c * ft.s] = CplxTraits<T>::from(to_c128(x[c]));
+}
+
+// ---------------------------------------------------------------------------
 // Batched complex GEMM, one 64 x 64 output tile per CTA (16 x 16 threads, 4 x 4 each; thread
 // (tx, ty) owns rows ty + 16 a and columns tx + 16 b, so each 16 x 16 block (a, b) is spread over
 // the whole CTA and can be skipped as a unit).
@@ -289,6 +331,11 @@ __global__ void __launch_bounds__(256) k_copy_linv(const FrontTask<T>* __restric
   for (int c = tk.c0; c < tk.c1; ++c)
     for (int r = c + 1 + threadIdx.x; r < ft.s; r += blockDim.x)
       ft.G[(int64_t)c * ld + r] = ft.W[(int64_t)c * ft.s + r];
+  if (ft.W2) {   // the second inverse, whole (unit lower, zero above), after G
+    T* G2 = ft.G + second_inverse_offset(ft.s, ft.u);
+    for (int c = tk.c0; c < tk.c1; ++c)
+      for (int r = threadIdx.x; r < ft.s; r += blockDim.x) G2[(int64_t)c * ft.s + r] = ft.W2[(int64_t)c * ft.s + r];
+  }
 }
 
 // ZD = Z D^{-1}, column by column, once per front: the Schur update and the M_BL product then
@@ -332,6 +379,13 @@ void launch_panel_left(const FrontTask<T>* fronts, const ColTask* tasks, int nta
   else k_panel_left<T, T><<<ntasks, 64, 0, st>>>(fronts, tasks, kb);
 }
 template <typename T>
+void launch_panel_rsolve(const FrontTask<T>* fronts, const ColTask* tasks, int ntasks, int kb, bool wide,
+                         cudaStream_t st) {
+  if (ntasks <= 0) return;
+  if (wide) k_panel_rsolve<T, double2><<<ntasks, 64, 0, st>>>(fronts, tasks, kb);
+  else k_panel_rsolve<T, T><<<ntasks, 64, 0, st>>>(fronts, tasks, kb);
+}
+template <typename T>
 void launch_gemm(const GemmTask<T>* tasks, int ntasks, cudaStream_t st) {
   if (ntasks > 0) k_gemm<T><<<ntasks, 256, 0, st>>>(tasks);
 }
@@ -348,6 +402,7 @@ void launch_scale_zd(const FrontTask<T>* fronts, const ColTask* tasks, int ntask
   template void launch_diag_ldlt<T>(const FrontTask<T>*, const int*, int, int, double, int*, bool, cudaStream_t);    \
   template void launch_panel_right<T>(const FrontTask<T>*, const ColTask*, int, int, bool, cudaStream_t);            \
   template void launch_panel_left<T>(const FrontTask<T>*, const ColTask*, int, int, bool, cudaStream_t);             \
+  template void launch_panel_rsolve<T>(const FrontTask<T>*, const ColTask*, int, int, bool, cudaStream_t);     \
   template void launch_gemm<T>(const GemmTask<T>*, int, cudaStream_t);                                         \
   template void launch_copy_linv<T>(const FrontTask<T>*, const ColTask*, int, cudaStream_t);                 \
   template void launch_scale_zd<T>(const FrontTask<T>*, const ColTask*, int, cudaStream_t);

@@ -102,13 +102,17 @@ __global__ void __launch_bounds__(256) k_assemble(const FrontTask<T>* __restrict
   const int32_t* sel = sh.struct_elim + sh.struct_ptr[ft.sn];
   const T zero = CplxTraits<T>::zero();
 
-  // 1. zero the owned columns; W = identity (when the inverse of L_TL is built)
+  // 1. zero the owned columns; W (and W2) = identity (when inverses of L_TL are built)
   for (int c = c0; c < c1; ++c) {
     if (c < s) {
       T* col = ft.G + (int64_t)c * ld;
       for (int r = threadIdx.x; r < ld; r += blockDim.x) col[r] = zero;
       if (ft.W) {
         T* wc = ft.W + (int64_t)c * s;
+        for (int r = threadIdx.x; r < s; r += blockDim.x) wc[r] = (r == c) ? CplxTraits<T>::one() : zero;
+      }
+      if (ft.W2) {
+        T* wc = ft.W2 + (int64_t)c * s;
         for (int r = threadIdx.x; r < s; r += blockDim.x) wc[r] = (r == c) ? CplxTraits<T>::one() : zero;
       }
     } else {

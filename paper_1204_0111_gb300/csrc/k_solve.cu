@@ -304,6 +304,11 @@ __device__ __forceinline__ void bwd_task(const SolveTask tk, const int rhs0, con
   // rows of the inner sums: [lo, hi), passed through shared memory in chunks of `chunk` rows
   const int lo = (ext || phase == 1) ? c0 : s;
   const int hi = (ext || phase == 0) ? ld : s;
+  // the columns the inner sums read: G's, or in the two-inverse form's second phase the second
+  // inverse of L_TL (s x s after G), which was built row by row for this direction
+  const bool second = phase == 1 && cx.si == PSP_SI_TWO;
+  const T* Gs = second ? G + second_inverse_offset(s, u) : G;
+  const int lds = second ? s : ld;
   // right-hand side major (y[q * chunk + row]): the lanes of a warp read consecutive rows, so the
   // loads are free of bank conflicts whatever RG is
   T* y = reinterpret_cast<T*>(smem_raw);        // RG x chunk
@@ -329,7 +334,7 @@ __device__ __forceinline__ void bwd_task(const SolveTask tk, const int rhs0, con
       T acc[RG];
 #pragma unroll
       for (int q = 0; q < RG; ++q) acc[q] = CplxTraits<T>::zero();
-      const T* Gc = G + (int64_t)c * ld;
+      const T* Gc = Gs + (int64_t)c * lds;
       int r = (rb > c + 1 ? rb : c + 1) + lane;
       for (; r + 7 * 32 < re; r += 8 * 32) {   // eight independent factor loads in flight per lane
         T gv[8];
@@ -499,9 +504,12 @@ __device__ __forceinline__ void prefetch_task(const SolveTask tk, const int dir,
       if (a < col + seg) asm volatile("prefetch.L2 [%0];" ::"l"(a));
     }
   } else {
+    const bool second = dir == kDirDownB && cx.si == PSP_SI_TWO;   // the second inverse after G
+    const char* Gs = second ? G + second_inverse_offset(s, ld - s) * sizeof(T) : G;
+    const int lds = second ? s : ld;
     for (int c = tk.r0; c < tk.r1; ++c) {
-      const char* col = G + ((int64_t)c * ld + c + 1) * sizeof(T);
-      const int64_t seg = (int64_t)(ld - c - 1) * sizeof(T);
+      const char* col = Gs + ((int64_t)c * lds + c + 1) * sizeof(T);
+      const int64_t seg = (int64_t)(lds - c - 1) * sizeof(T);
       for (int64_t off = (int64_t)threadIdx.x * kLine; off < seg; off += (int64_t)blockDim.x * kLine)
         asm volatile("prefetch.L2 [%0];" ::"l"(col + off));
     }

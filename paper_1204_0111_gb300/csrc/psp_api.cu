@@ -408,9 +408,9 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
   auto packed_elems = [&](int64_t s_, int64_t u_) {   // F_BL, Z D^-1, Z (u x s) and two inv(L) (s x s)
     return TBLK * (3 * nrb(u_) * nkb16(s_) + 2 * nrb(s_) * nkb16(s_));
   };
-  auto front_temp = [&](int64_t s_, int64_t u_) {     // W (s x s), Z (u x s), Z D^-1 or packed operands
-    if (si == PSP_SI_NONE) return (int64_t)0;
-    return pad16(s_ * s_) + pad16(u_ * s_) +
+  auto front_temp = [&](int64_t s_, int64_t u_) {     // W (s x s), Z (u x s), Z D^-1 or packed operands,
+    if (si == PSP_SI_NONE) return (int64_t)0;         // the second inverse under construction (s x s)
+    return pad16(s_ * s_) + pad16(u_ * s_) + (si == PSP_SI_TWO ? pad16(s_ * s_) : 0) +
            (use_tc(s_, u_) ? packed_elems(s_, u_) : si == PSP_SI_EXTENDED ? pad16(u_ * s_) : 0);
   };
   int64_t arena[2] = {0, 0}, temp_level_max = 0, temp_front_max = 16;
@@ -498,7 +498,7 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
   std::vector<unsigned char*> packs;     // per front: base of its packed operands (tensor-core fronts)
   std::vector<TcPackTask> ptasks;
   std::vector<TcGemmTask> ttasks;
-  enum Kind { ASSEMBLE, DIAG, PRIGHT, PLEFT, GEMM, COPY, TCGEMM, TCPACK, SCALE };
+  enum Kind { ASSEMBLE, DIAG, PRIGHT, PLEFT, GEMM, COPY, TCGEMM, TCPACK, SCALE, RSOLVE };
   struct Launch {
     Kind kind;
     int64_t front_off;
@@ -534,7 +534,7 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
   // [4..5] ~bits of the smallest |pivot| (0: none yet)
   PSP_CK(cudaMemsetAsync(status, 0, 8 * sizeof(int), st));
   static const char* names[] = {"k_assemble", "k_diag_ldlt", "k_panel_right", "k_panel_left", "k_gemm", "k_copy_linv",
-                                "k_tc_gemm", "k_tc_pack", "k_scale_zd"};
+                                "k_tc_gemm", "k_tc_pack", "k_scale_zd", "k_panel_rsolve"};
   std::vector<void*> chunks;
   const Allocator* chunk_alloc = g_alloc && g_alloc->alloc ? g_alloc : nullptr;
   struct ChunkGuard {
@@ -599,6 +599,7 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
           case TCGEMM: launch_tc_gemm(TT + (l.off - (int64_t)t0), l.count, status, st); break;
           case TCPACK: launch_tc_pack(PT + (l.off - (int64_t)p0), l.count, st); break;
           case SCALE: launch_scale_zd<T>(Fl, CT + (l.off - (int64_t)c0), l.count, st); break;
+          case RSOLVE: launch_panel_rsolve<T>(Fl, CT + (l.off - (int64_t)c0), l.count, l.kb, wide, st); break;
         }
       }, true, l.extra);
     }
@@ -621,7 +622,7 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
       ft.G = fbase + X->panel_fbase[p] + sh.g_off[sn];
       ft.U = upd_ptr[ft.gfid];
       ft.ut = upd_tile[ft.gfid];
-      ft.W = ft.Z = ft.ZD = nullptr;
+      ft.W = ft.Z = ft.ZD = ft.W2 = nullptr;
       ft.ldzd = ft.u;
       packs.push_back(nullptr);
       if (si != PSP_SI_NONE) {
@@ -636,9 +637,13 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
           ft.ZD = tbase + toff;
           toff += pad16((int64_t)ft.u * ft.s);
         }
-        if (si == PSP_SI_PAPER) {   // L_BL = Z D^{-1} is the factor's bottom block
+        if (si == PSP_SI_PAPER || si == PSP_SI_TWO) {   // L_BL = Z D^{-1} is the factor's bottom block
           ft.ZD = ft.G + ft.s;
           ft.ldzd = ft.s + ft.u;
+        }
+        if (si == PSP_SI_TWO) {
+          ft.W2 = tbase + toff;
+          toff += pad16((int64_t)ft.s * ft.s);
         }
       }
       fronts.push_back(ft);
@@ -788,7 +793,54 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
       gemm_work(g0, lg.flops, lg.extra, lg.bytes);
       launches.push_back(lg);
     }
-    // inv(L_TL) into F_TL's strict lower part
+    // The two-inverse form: the second inverse X of L_TL row by row, X L_TL = I, by block columns from
+    // the last: X(:, kb) := X(:, kb) L_kk^{-1}, then X(:, j) -= X(:, kb) L(kb, j) for the blocks j < kb
+    // (X is unit lower: only rows from the block's first row down take part).
+    if (si == PSP_SI_TWO) {
+      for (int kb = nblk - 1; kb >= 0; --kb) {
+        const int o = kb * nb;
+        const int64_t r0 = (int64_t)ctasks.size();
+        for (int f = 0; f < nf; ++f) {
+          const auto& ft = fronts[f0 + f];
+          if (ft.s <= o) continue;
+          for (int r = o; r < ft.s; r += 64) ctasks.push_back({f, r, std::min(r + 64, ft.s)});
+        }
+        Launch lr{RSOLVE, f0, r0, (int)(ctasks.size() - r0), kb};
+        for (int64_t q = r0; q < (int64_t)ctasks.size(); ++q) {
+          const double rows = ctasks[q].c1 - ctasks[q].c0, bs = std::min(nb, fronts[f0 + ctasks[q].front].s - o);
+          lr.extra += 8.0 * rows * bs * (bs - 1) / 2;
+          lr.bytes += es * 2 * rows * bs;
+        }
+        launches.push_back(lr);
+        if (kb == 0) break;
+        const int64_t g0 = (int64_t)gtasks.size();
+        for (int f : ord) {
+          const auto& ft = fronts[f0 + f];
+          if (ft.s <= o) continue;
+          const int ld = ft.s + ft.u;
+          const int bs = std::min(nb, ft.s - o);
+          for (int tj = 0; tj < o; tj += 64)
+            for (int ti = o; ti < ft.s; ti += 64) {
+              GemmTask<T> g{};
+              g.C = ft.W2 + (int64_t)tj * ft.s + ti;
+              g.ldc = ft.s;
+              g.A = ft.W2 + (int64_t)o * ft.s + ti;   // A(m, k) = X[ti + m, o + k]
+              g.lda = ft.s;
+              g.B = ft.G + (int64_t)tj * ld + o;      // B(n, k) = L[o + k, tj + n]
+              g.ldb = ld;
+              g.m = std::min(64, ft.s - ti);
+              g.n = std::min(64, o - tj);
+              g.k = bs;
+              g.flags = GF_NEG | GF_B_NN | GF_SI;
+              gtasks.push_back(g);
+            }
+        }
+        Launch lg{GEMM, f0, g0, (int)(gtasks.size() - g0), kb};
+        gemm_work(g0, lg.flops, lg.extra, lg.bytes);
+        launches.push_back(lg);
+      }
+    }
+    // inv(L_TL) into F_TL's strict lower part (and the second inverse after G)
     if (si != PSP_SI_NONE) {
       const int64_t c0 = (int64_t)ctasks.size();
       for (int f = 0; f < nf; ++f) {
@@ -1697,6 +1749,17 @@ static void build_problem(psp_ctx_s* X, const double* c, cudaStream_t st) {
 static void finish_setup(psp_ctx_s* X, cudaStream_t st) {
   auto t_start = std::chrono::steady_clock::now();
   upload(X->d_boxops, X->h_boxops);
+  // factor blocks per front: G ((s + u) x s), and in the two-inverse form the second inverse of L_TL
+  // (s x s) right after it, each padded to 16 elements
+  for (auto& sh : X->shapes) {
+    int64_t go = 0;
+    for (int f = 0; f < sh.nsn; ++f) {
+      sh.g_off[f] = go;
+      go += second_inverse_offset(sh.s[f], sh.u[f]);
+      if (X->si_mode == PSP_SI_TWO) go += ((int64_t)sh.s[f] * sh.s[f] + 15) / 16 * 16;
+    }
+    sh.g_total = go;
+  }
 
   // shapes to the device
   X->shape_bufs.clear();
@@ -2096,7 +2159,7 @@ static psp_status check_options(const psp_options* opt, psp_options* o) {
       (o->precision != PSP_PREC_C128 && o->precision != PSP_PREC_C64) ||
       (o->aux_mode != PSP_AUX_MOVING_PML && o->aux_mode != PSP_AUX_EXACT) || !(o->alpha >= 0) || !(o->pml_C >= 0) ||
       o->gmres_basis < 0 || o->gmres_basis > 2 || o->panel_begin < 0 || o->panel_count < 0 ||
-      (o->dev_alloc == nullptr) != (o->dev_free == nullptr) || o->selective_inversion < 0 || o->selective_inversion > 2 ||
+      (o->dev_alloc == nullptr) != (o->dev_free == nullptr) || o->selective_inversion < 0 || o->selective_inversion > 3 ||
       o->c64_diag_fp64 < 0 || o->c64_diag_fp64 > 1)
     return fail(PSP_ERR_ARG, "bad options");
   return PSP_OK;
@@ -2457,6 +2520,30 @@ psp_status psp_export_front(psp_handle X, int panel, int sn, double* buf, int* s
   check_device(X);
   const int64_t n = (int64_t)(sh.s[sn] + sh.u[sn]) * sh.s[sn];
   const char* src = X->d_factor.as<char>() + (X->panel_fbase[panel] + sh.g_off[sn]) * (int64_t)X->elem_bytes;
+  if (X->elem_bytes == 16) {
+    PSP_CK(cudaMemcpy(buf, src, n * 16, cudaMemcpyDeviceToHost));
+  } else {
+    std::vector<float> tmp(2 * n);
+    PSP_CK(cudaMemcpy(tmp.data(), src, n * 8, cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < 2 * n; ++i) buf[i] = tmp[i];
+  }
+  return PSP_OK;
+  PSP_CATCH
+}
+
+psp_status psp_export_second_inverse(psp_handle X, int panel, int sn, double* buf, int* s) {
+  if (!X || panel < 0 || panel >= X->m) return fail(PSP_ERR_ARG, "bad panel");
+  const Shape& sh = X->shapes[X->shape_of[panel]];
+  if (sn < 0 || sn >= sh.nsn) return fail(PSP_ERR_ARG, "bad supernode");
+  if (X->owner.empty() || X->owner[panel] < 0) return fail(PSP_ERR_ARG, "the panel is outside this handle's block");
+  if (X->si_mode != PSP_SI_TWO || !X->d_factor.p) return fail(PSP_ERR_STATE, "the handle keeps no second inverse");
+  if (s) *s = sh.s[sn];
+  if (!buf) return PSP_OK;
+  PSP_TRY
+  check_device(X);
+  const int64_t n = (int64_t)sh.s[sn] * sh.s[sn];
+  const int64_t off = X->panel_fbase[panel] + sh.g_off[sn] + second_inverse_offset(sh.s[sn], sh.u[sn]);
+  const char* src = X->d_factor.as<char>() + off * (int64_t)X->elem_bytes;
   if (X->elem_bytes == 16) {
     PSP_CK(cudaMemcpy(buf, src, n * 16, cudaMemcpyDeviceToHost));
   } else {

@@ -150,11 +150,17 @@ struct FrontTask {
   T* Z;        // u x s work: F_BL L^{-T}
   T* ZD;       // u x s: Z D^{-1}, leading dimension ldzd (a work block for the extended selective
                // inversion of CUDA-core fronts, G's bottom block when L_BL itself is stored; else nullptr)
+  T* W2;       // s x s work: the second inverse of L_TL under construction (two-inverse form), else nullptr
   int s, u;
   int panel, sn;
   int64_t gfid;
   int ut, ldzd;   // tile size of U; leading dimension of ZD
 };
+
+// elements from a front's G block to its second inverse of L_TL (two-inverse form): G padded to 16
+__host__ __device__ __forceinline__ int64_t second_inverse_offset(int64_t s, int64_t u) {
+  return ((s + u) * s + 15) / 16 * 16;
+}
 
 struct ColTask {   // a chunk of columns / rows of one front
   int front;       // index into the level's FrontTask array
@@ -178,6 +184,8 @@ template <typename T>
 void launch_panel_right(const FrontTask<T>* fronts, const ColTask* tasks, int ntasks, int kb, bool wide, cudaStream_t st);
 template <typename T>
 void launch_panel_left(const FrontTask<T>* fronts, const ColTask* tasks, int ntasks, int kb, bool wide, cudaStream_t st);
+template <typename T>
+void launch_panel_rsolve(const FrontTask<T>* fronts, const ColTask* tasks, int ntasks, int kb, bool wide, cudaStream_t st);
 template <typename T>
 void launch_gemm(const GemmTask<T>* tasks, int ntasks, cudaStream_t st);
 // tensor-core path (complex64): operands packed once per front into TF32 planes, then tiles

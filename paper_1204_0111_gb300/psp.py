@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "lib", "libpsp.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "psp.h")
 
 PREC_C128, PREC_C64 = 0, 1
-SI_MODES = {"extended": 0, "paper": 1, "none": 2}   # psp_si_mode
+SI_MODES = {"extended": 0, "paper": 1, "none": 2, "two": 3}   # psp_si_mode
 AUX_MOVING_PML, AUX_EXACT = 0, 1
 STATUS = {0: "PSP_OK", 1: "PSP_ERR_ARG", 2: "PSP_ERR_OOM", 3: "PSP_ERR_CUDA", 4: "PSP_ERR_ZERO_PIVOT",
           5: "PSP_ERR_NOT_CONVERGED", 6: "PSP_ERR_TIMEOUT", 7: "PSP_ERR_STATE"}
@@ -123,6 +123,7 @@ def lib():
         "psp_symbolic_export": (_I, [_P, _I, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_size_t)]),
         "psp_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
         "psp_export_front": (_I, [_P, _I, _I, _P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+        "psp_export_second_inverse": (_I, [_P, _I, _I, _P, ctypes.POINTER(_I)]),
         "psp_stats": (_I, [_P, ctypes.POINTER(KernelStat), _I, ctypes.POINTER(_I), _I]),
         "psp_tune_sweep": (_I, [_P, _I, _I, _P, ctypes.POINTER(SweepTuning)]),
         "psp_check_status": (_I, [_P, _P]),
@@ -321,6 +322,14 @@ class SweepingPreconditioner:
         out = np.zeros(((s.value + u.value) * s.value,), dtype=np.complex128)
         _check(lib().psp_export_front(self._h, int(panel), int(sn), out.ctypes.data, ctypes.byref(s), ctypes.byref(u)))
         return out.reshape(s.value, s.value + u.value).T, s.value, u.value
+
+    def export_second_inverse(self, panel, sn):
+        """The two-inverse form's second inverse of L_TL of one front (s x s, built row by row)."""
+        s = _I()
+        _check(lib().psp_export_second_inverse(self._h, int(panel), int(sn), None, ctypes.byref(s)))
+        out = np.zeros((s.value * s.value,), dtype=np.complex128)
+        _check(lib().psp_export_second_inverse(self._h, int(panel), int(sn), out.ctypes.data, ctypes.byref(s)))
+        return out.reshape(s.value, s.value).T
 
 
 class SweepingPreconditionerBatch(SweepingPreconditioner):

@@ -2,9 +2,10 @@
 
 After the partial LDL^T of a front, F_TL = L_TL D L_TL^T and L_BL = F_BL L_TL^{-T} D^{-1}.  The
 handle keeps, per front, G = [inv(L_TL); L_BL inv(L_TL)] (extended, the default), the paper's
-G = [inv(L_TL); L_BL], or G = [L_TL; L_BL] without inversion, D on the top block's diagonal.  All
-three apply the same preconditioner: the sweep takes one pass per front and direction for the first,
-two dependent phases for the second, and triangular substitution for the third.
+G = [inv(L_TL); L_BL], or G = [L_TL; L_BL] without inversion, D on the top block's diagonal, or the
+paper's G with a second inverse of L_TL built row by row for the down sweep (§2.2's two inverses).
+All four apply the same preconditioner: the sweep takes one pass per front and direction for the
+first, two dependent phases for the second and fourth, and triangular substitution for the third.
 """
 import numpy as np
 import pytest
@@ -24,7 +25,7 @@ if not torch.cuda.is_available():
 from paper_1204_0111_gb300 import psp  # noqa: E402
 
 CASES = small_cases()
-MODES = ["paper", "none"]
+MODES = ["paper", "none", "two"]
 _oracles = {}
 
 
@@ -55,7 +56,7 @@ def test_front_factors_in_each_form(case, si):
     for i in range(O.m):
         for f, fr in enumerate(O.fronts[i]):
             G, s, u = P.export_front(i, f)
-            if si == "paper":
+            if si in ("paper", "two"):
                 top = sla.solve_triangular(fr.L_TL, np.eye(s), lower=True, unit_diagonal=True)
             else:
                 top = fr.L_TL
@@ -65,6 +66,35 @@ def test_front_factors_in_each_form(case, si):
             worst = max(worst, rel(got, exp))
     P.close()
     assert worst < 1e-10, worst
+
+
+@pytest.mark.parametrize("precision,tol", [("c128", 1e-10), ("c64", 1e-4)])
+@pytest.mark.parametrize("case", CASES, ids=lambda c: c.name)
+def test_second_inverse_by_rows(case, precision, tol):
+    # the two-inverse form keeps a second inverse of L_TL, built row by row (X L_TL = I), besides the
+    # first (built column by column): both equal the oracle's inv(L_TL); they are separate
+    # computations (their rounding differs somewhere), and the first stays the paper's form's
+    O = oracle_for(case)
+    P = gpu_for(case, "two", precision=precision)
+    Q = gpu_for(case, "paper", precision=precision)
+    worst, differ = 0.0, False
+    for i in range(O.m):
+        for f, fr in enumerate(O.fronts[i]):
+            X = P.export_second_inverse(i, f)
+            G, s, _ = P.export_front(i, f)
+            Gq, _, _ = Q.export_front(i, f)
+            assert np.array_equal(G, Gq)
+            inv = sla.solve_triangular(fr.L_TL, np.eye(s), lower=True, unit_diagonal=True)
+            worst = max(worst, rel(X, inv))
+            assert np.array_equal(np.triu(X, 1), np.zeros_like(X)) and np.all(np.diag(X) == 1)
+            differ = differ or not np.array_equal(np.tril(X, -1), np.tril(G[:s], -1))
+    assert worst < tol, worst
+    assert differ
+    with pytest.raises(psp.PSPError) as e:
+        Q.export_second_inverse(0, 0)
+    assert e.value.name == "PSP_ERR_STATE"
+    P.close()
+    Q.close()
 
 
 @pytest.mark.parametrize("si", MODES)
@@ -98,7 +128,10 @@ def test_forms_solve_like_the_extended_one(si):
     ss = {k: v for k, v in S.stats().items() if not k.startswith("host:")}
     ex = sum(v["extra_flops"] for v in se.values())
     sx = sum(v["extra_flops"] for v in ss.values())
-    assert sx < ex and (si == "paper" or sx == 0)
+    if si == "two":   # the second inverse costs about what the first does
+        assert ss["k_panel_rsolve"]["launches"] > 0 and sx > 0
+    else:
+        assert sx < ex and (si == "paper" or sx == 0)
     E.close()
     S.close()
 
