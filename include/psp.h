@@ -153,6 +153,10 @@ typedef struct {
                            solves against it (the rows of L_BL and the block rows of inv(L_TL), §2.2),
                            in complex128 arithmetic, rounding to complex64 only when storing; the
                            products between blocks stay complex64.  0 (default): all complex64 */
+  int sweep_max_rows;   /* sweep schedule: most rows (up the tree) or columns (down) of a front per task,
+                           64 .. 256: a level whose fronts outnumber the CTAs takes whole fronts of up
+                           to this many rows per task, gathering each front's vector once; <= 0
+                           selects the default (256) */
 } psp_options;
 
 /* Per-solve report filled by psp_solve (host struct). */
@@ -346,8 +350,8 @@ psp_status psp_stats(psp_handle h, psp_kernel_stat* out, int capacity, int* coun
  * sweep (the GPU's counterpart of the paper's choice of process grids, §2.1).  On this handle it
  * times psp_apply with nrhs right-hand sides (per problem of a batch) under candidate schedules
  * and keeps the fastest: the tasks a tree level is split into (152 .. 2432), the resident CTAs per
- * SM (2, 3, 4, 6, 8) and, for nrhs > 1, the right-hand sides per CTA pass (1 .. 8) and the floor on
- * rows per task (8 .. 64).  It searches one
+ * SM (2, 3, 4, 6, 8), the cap on rows / columns per task (64 .. 256) and, for nrhs > 1, the
+ * right-hand sides per CTA pass (1 .. 8) and the floor on rows per task (8 .. 64).  It searches one
  * coordinate at a time, starting from the handle's current schedule, timing `reps` applications
  * (CUDA events on `stream`) per candidate after one untimed one.  Results do not change beyond
  * rounding (the schedule only regroups the same sums).  The work vectors are the handle's own; the
@@ -363,7 +367,8 @@ typedef struct {
   double initial_ms;      /* one application under the schedule the handle had */
   double best_ms;         /* one application under the chosen schedule */
   int sweep_min_rows;     /* floor on rows / columns per task */
-  int reserved[3];
+  int sweep_max_rows;     /* cap on rows / columns per task */
+  int reserved[2];
 } psp_sweep_tuning;
 
 psp_status psp_tune_sweep(psp_handle h, int nrhs, int reps, void* stream, psp_sweep_tuning* out);

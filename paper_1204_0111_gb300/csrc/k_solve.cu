@@ -312,7 +312,7 @@ __device__ __forceinline__ void bwd_task(const SolveTask tk, const int rhs0, con
   // right-hand side major (y[q * chunk + row]): the lanes of a warp read consecutive rows, so the
   // loads are free of bank conflicts whatever RG is
   T* y = reinterpret_cast<T*>(smem_raw);        // RG x chunk
-  T* sums = y + (int64_t)chunk * RG;            // (r1 - c0) x RG column sums (<= 64 columns)
+  T* sums = y + (int64_t)chunk * RG;            // (r1 - c0) x RG column sums (<= 256 columns)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int e = threadIdx.x; e < (tk.r1 - c0) * RG; e += blockDim.x) sums[e] = CplxTraits<T>::zero();
   for (int rb = lo; rb < hi; rb += chunk) {
@@ -710,7 +710,7 @@ static void fwd_rg(const SolveTask* tasks, int ntasks, const SolveCtx<T>& cx, in
 
 template <typename T, int RG>
 static void bwd_rg(const SolveTask* tasks, int ntasks, const SolveCtx<T>& cx, int ldmax, int phase, cudaStream_t st) {
-  const size_t smem = ((size_t)ldmax + 64) * RG * sizeof(T);
+  const size_t smem = ((size_t)ldmax + 256) * RG * sizeof(T);
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_solve_bwd<T, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
@@ -736,7 +736,7 @@ void launch_solve_fwd(const SolveTask* tasks, int ntasks, const SolveCtx<T>& cx,
 template <typename T>
 void launch_solve_bwd(const SolveTask* tasks, int ntasks, const SolveCtx<T>& cx, int ldmax, int phase, cudaStream_t st) {
   if (ntasks <= 0) return;
-  const int rg = pick_rg<T>(cx.nrhs, ((size_t)ldmax + 64) * sizeof(T));
+  const int rg = pick_rg<T>(cx.nrhs, ((size_t)ldmax + 256) * sizeof(T));
   switch (rg) {
     case 8: bwd_rg<T, 8>(tasks, ntasks, cx, ldmax, phase, st); break;
     case 4: bwd_rg<T, 4>(tasks, ntasks, cx, ldmax, phase, st); break;

@@ -315,6 +315,7 @@ struct psp_ctx_s {
   bool diag_fp64 = false;   // complex64: diagonal blocks factored and applied in complex128
   int tc_min_dim = 64;
   int sweep_level_tasks = 608, sweep_ctas_per_sm = 8, sweep_rhs_group = 0, solve_rhs_group = 0, sweep_min_rows = 8;
+  int sweep_max_rows = 256;
   int gmres_basis = 0;   // 0 auto, 1 keep z_j, 2 V only
   int si_mode = 0;       // psp_si_mode: what the factor of each front keeps (selective inversion, §2.2)
   bool test_sweep_stall = false;
@@ -1118,14 +1119,16 @@ static void plan_solve(psp_ctx_s* X, cudaStream_t st) {
         P.entries += ss * (ss - 1) / 2 + uu * ss;
         P.vec += 2 * ss + 2 * uu;
       }
-      // rows (columns) per task: 64, halved while the level has fewer than sweep_level_tasks tasks, but
-      // not below sweep_min_rows (a task gathers its front's vector for every right-hand side, so
-      // narrow tasks over wide fronts gather much and stream little)
+      // rows per up task and columns per down task: sweep_max_rows (64 .. 256), halved while the
+      // level has fewer than sweep_level_tasks tasks, but not below sweep_min_rows (a task gathers
+      // its front's vector for every right-hand side, so narrow tasks over wide fronts gather much and
+      // stream little, and at the bottom of the tree, where tasks far outnumber CTAs, one task per
+      // front gathers once)
       const int rmin = std::max(8, std::min(64, X->sweep_min_rows));
-      int R = 64;
+      int R = X->sweep_max_rows;
       while (R > rmin && rows / R < X->sweep_level_tasks) R >>= 1;
       P.R = R;
-      int Cc = 64;
+      int Cc = X->sweep_max_rows;
       while (Cc > rmin && cols / Cc < X->sweep_level_tasks) Cc >>= 1;
       // extended factors: one pass per front and direction over all s + u rows; factors keeping L_BL:
       // up, rows r < s (one whole-front substitution task without inversion) then rows r >= s; down,
@@ -2190,6 +2193,7 @@ static void init_options(psp_ctx_s* X, const psp_options& o) {
   X->sweep_ctas_per_sm = o.sweep_ctas_per_sm > 0 ? o.sweep_ctas_per_sm : 8;
   X->sweep_rhs_group = o.sweep_rhs_group > 0 ? o.sweep_rhs_group : 0;
   X->sweep_min_rows = o.sweep_min_rows > 0 ? o.sweep_min_rows : 8;
+  X->sweep_max_rows = o.sweep_max_rows > 0 ? std::min(256, std::max(64, o.sweep_max_rows)) : 256;
   X->solve_rhs_group = o.solve_rhs_group > 0 ? o.solve_rhs_group : 0;
   X->gmres_basis = o.gmres_basis;
   X->si_mode = o.selective_inversion;
@@ -2597,12 +2601,13 @@ psp_status psp_tune_sweep(psp_handle X, int nrhs, int reps, void* stream, psp_sw
   cudaEvent_t e0, e1;
   PSP_CK(cudaEventCreate(&e0));
   PSP_CK(cudaEventCreate(&e1));
-  struct Sched { int lt, cps, rg, mr; };
+  struct Sched { int lt, cps, rg, mr, xr; };
   int timed = 0;
   auto time_one = [&](const Sched& c) {
-    if (c.lt != X->sweep_level_tasks || c.mr != X->sweep_min_rows) {
+    if (c.lt != X->sweep_level_tasks || c.mr != X->sweep_min_rows || c.xr != X->sweep_max_rows) {
       X->sweep_level_tasks = c.lt;
       X->sweep_min_rows = c.mr;
+      X->sweep_max_rows = c.xr;
       plan_solve(X, st);
     }
     X->sweep_ctas_per_sm = c.cps;
@@ -2619,7 +2624,7 @@ psp_status psp_tune_sweep(psp_handle X, int nrhs, int reps, void* stream, psp_sw
   };
   const bool was_timing = X->stats.timing;
   X->stats.timing = false;
-  Sched best{X->sweep_level_tasks, X->sweep_ctas_per_sm, X->sweep_rhs_group, X->sweep_min_rows};
+  Sched best{X->sweep_level_tasks, X->sweep_ctas_per_sm, X->sweep_rhs_group, X->sweep_min_rows, X->sweep_max_rows};
   double best_ms = 0, initial_ms = 0;
   try {
     best_ms = initial_ms = time_one(best);
@@ -2630,15 +2635,17 @@ psp_status psp_tune_sweep(psp_handle X, int nrhs, int reps, void* stream, psp_sw
         best = c;
       }
     };
+    for (int xr : {64, 128, 256})
+      if (xr != best.xr) consider({best.lt, best.cps, best.rg, best.mr, xr});
     for (int lt : {152, 304, 608, 1216, 2432})
-      if (lt != best.lt) consider({lt, best.cps, best.rg, best.mr});
+      if (lt != best.lt) consider({lt, best.cps, best.rg, best.mr, best.xr});
     for (int cps : {2, 3, 4, 6, 8})
-      if (cps != best.cps) consider({best.lt, cps, best.rg, best.mr});
+      if (cps != best.cps) consider({best.lt, cps, best.rg, best.mr, best.xr});
     if (nrhs > 1) {
       for (int rg : {1, 2, 4, 8})
-        if (rg <= nrhs && rg != best.rg) consider({best.lt, best.cps, rg, best.mr});
+        if (rg <= nrhs && rg != best.rg) consider({best.lt, best.cps, rg, best.mr, best.xr});
       for (int mr : {8, 16, 32, 64})
-        if (mr != best.mr) consider({best.lt, best.cps, best.rg, mr});
+        if (mr != best.mr) consider({best.lt, best.cps, best.rg, mr, best.xr});
     }
   } catch (...) {
     X->stats.timing = was_timing;
@@ -2649,9 +2656,10 @@ psp_status psp_tune_sweep(psp_handle X, int nrhs, int reps, void* stream, psp_sw
   X->stats.timing = was_timing;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (best.lt != X->sweep_level_tasks || best.mr != X->sweep_min_rows) {
+  if (best.lt != X->sweep_level_tasks || best.mr != X->sweep_min_rows || best.xr != X->sweep_max_rows) {
     X->sweep_level_tasks = best.lt;
     X->sweep_min_rows = best.mr;
+    X->sweep_max_rows = best.xr;
     plan_solve(X, st);
   }
   X->sweep_ctas_per_sm = best.cps;
@@ -2662,6 +2670,7 @@ psp_status psp_tune_sweep(psp_handle X, int nrhs, int reps, void* stream, psp_sw
     out->sweep_ctas_per_sm = best.cps;
     out->sweep_rhs_group = best.rg;
     out->sweep_min_rows = best.mr;
+    out->sweep_max_rows = best.xr;
     out->candidates = timed;
     out->initial_ms = initial_ms;
     out->best_ms = best_ms;

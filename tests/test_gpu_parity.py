@@ -112,6 +112,22 @@ def test_apply_matches_oracle(case, nrhs):
     assert rel(host_out, ref) < 1e-10
 
 
+@pytest.mark.parametrize("si", ["extended", "paper", "two"])
+@pytest.mark.parametrize("max_rows", [128, 256])
+def test_whole_front_up_tasks_match_oracle(max_rows, si):
+    # up-the-tree tasks of up to 128 or 256 rows (a whole front per task at the bottom of the tree)
+    case = CASES[2]
+    c = torch.from_numpy(case.c).cuda()
+    P = psp.SweepingPreconditioner(c, case.h, case.omega, case.gamma, case.depth, pad=case.pad, leaf=case.leaf,
+                                   pml_C=case.C, alpha=case.alpha, faces=case.faces, sweep_max_rows=max_rows,
+                                   selective_inversion=si)
+    r = wl.random_vector(case.N, 3, seed=33)
+    out = np.zeros_like(r)
+    P.apply(r, out)
+    assert rel(out, oracle_for(case).apply(r)) < 1e-10
+    P.close()
+
+
 def test_exact_mode_is_inverse_of_J():
     case = CASES[1]
     P = gpu_for(case, mode="exact")
@@ -265,6 +281,7 @@ def test_sweep_autotuner_keeps_results():
     t = P.tune_sweep(nrhs=2, reps=1)
     assert t["sweep_level_tasks"] in (152, 304, 608, 1216, 2432)
     assert t["sweep_ctas_per_sm"] in (2, 3, 4, 6, 8) and t["sweep_rhs_group"] in (0, 1, 2)
+    assert t["sweep_max_rows"] in (64, 128, 256)
     assert t["candidates"] >= 10 and 0 < t["best_ms"] <= t["initial_ms"]
     r = wl.random_vector(case.N, 2, seed=44)
     out = np.zeros_like(r)
