@@ -196,8 +196,12 @@ constexpr int GT = 64, GK = 8;
 template <typename T>
 __global__ void __launch_bounds__(256) k_gemm(const GemmTask<T>* __restrict__ tasks) {
   using R = typename CplxTraits<T>::real;
-  __shared__ R Ar[GK][GT + 1], Ai[GK][GT + 1], As[GK][GT + 1];
-  __shared__ R Br[GK][GT + 1], Bi[GK][GT + 1], Bs[GK][GT + 1];
+  // single precision: rows of 68 floats (16-byte aligned, so a thread reads its 4 consecutive rows
+  // or columns with one 128-bit load); double precision: 65 (no bank conflicts in the staging)
+  constexpr bool kSingle = sizeof(R) == 4;
+  constexpr int GP = kSingle ? GT + 4 : GT + 1;
+  __shared__ __align__(16) R Ar[GK][GP], Ai[GK][GP], As[GK][GP];
+  __shared__ __align__(16) R Br[GK][GP], Bi[GK][GP], Bs[GK][GP];
   const GemmTask<T> tk = tasks[blockIdx.x];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const T zero = CplxTraits<T>::zero();
@@ -242,24 +246,19 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTask<T>* __restrict__ ta
       Bs[kk][j] = v.x + v.y;
     }
     __syncthreads();
-    if constexpr (sizeof(R) == 4) {
+    if constexpr (kSingle) {
       // single precision: the FP32 pipe is fast enough that issue slots, not FMAs, bound the
-      // loop, so all 16 blocks run, with operands kept in registers across the block row
+      // loop, so all 16 blocks run; thread (tx, ty) owns rows 4 ty .. 4 ty + 3 and columns
+      // 4 tx .. 4 tx + 3, each operand quadruple one 128-bit shared load (six loads per 48 FMAs)
 #pragma unroll
       for (int kk = 0; kk < GK; ++kk) {
         R ar[4], ai[4], as[4], br[4], bi[4], bs[4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          ar[a] = Ar[kk][ty + 16 * a];
-          ai[a] = Ai[kk][ty + 16 * a];
-          as[a] = As[kk][ty + 16 * a];
-        }
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          br[b] = Br[kk][tx + 16 * b];
-          bi[b] = Bi[kk][tx + 16 * b];
-          bs[b] = Bs[kk][tx + 16 * b];
-        }
+        *reinterpret_cast<float4*>(ar) = *reinterpret_cast<const float4*>(&Ar[kk][4 * ty]);
+        *reinterpret_cast<float4*>(ai) = *reinterpret_cast<const float4*>(&Ai[kk][4 * ty]);
+        *reinterpret_cast<float4*>(as) = *reinterpret_cast<const float4*>(&As[kk][4 * ty]);
+        *reinterpret_cast<float4*>(br) = *reinterpret_cast<const float4*>(&Br[kk][4 * tx]);
+        *reinterpret_cast<float4*>(bi) = *reinterpret_cast<const float4*>(&Bi[kk][4 * tx]);
+        *reinterpret_cast<float4*>(bs) = *reinterpret_cast<const float4*>(&Bs[kk][4 * tx]);
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -305,11 +304,11 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTask<T>* __restrict__ ta
   const bool neg = tk.flags & GF_NEG, beta0 = tk.flags & GF_BETA0;
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
-    const int i = ty + 16 * a;
+    const int i = kSingle ? 4 * ty + a : ty + 16 * a;
     if (i >= tk.m) continue;
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
-      const int j = tx + 16 * b;
+      const int j = kSingle ? 4 * tx + b : tx + 16 * b;
       if (j >= tk.n || (lower && i < j)) continue;
       T v;
       v.x = t1[a][b] - t2[a][b];
