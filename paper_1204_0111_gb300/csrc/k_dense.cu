@@ -18,7 +18,7 @@ constexpr int kNB = 32;  // diagonal block size of the blocked LDL^T and inverse
 // complement = minimum of the non-negative value; 0 = no pivot yet).
 // ---------------------------------------------------------------------------
 template <typename T, typename C>
-__global__ void __launch_bounds__(256) k_diag_ldlt(const FrontTask<T>* __restrict__ fronts, const int* __restrict__ list,
+__global__ void __launch_bounds__(128) k_diag_ldlt(const FrontTask<T>* __restrict__ fronts, const int* __restrict__ list,
                                                    int kb, double tiny, int* status) {
   __shared__ C S[kNB][kNB + 1];  // S[col][row], in the compute precision C
   __shared__ C colv[kNB];
@@ -343,14 +343,18 @@ __global__ void __launch_bounds__(256) k_copy_linv(const FrontTask<T>* __restric
 template <typename T>
 __global__ void __launch_bounds__(256) k_scale_zd(const FrontTask<T>* __restrict__ fronts,
                                                   const ColTask* __restrict__ tasks) {
+  __shared__ T dinv[64];   // the task's pivots' reciprocals, one division each (at most 64 columns)
   const ColTask tk = tasks[blockIdx.x];
   const FrontTask<T> ft = fronts[tk.front];
   const int ld = ft.s + ft.u;
-  for (int c = tk.c0; c < tk.c1; ++c) {
-    const T dinv = cdiv(CplxTraits<T>::one(), ft.G[(int64_t)c * (ld + 1)]);
-    const T* z = ft.Z + (int64_t)c * ft.u;
-    T* zd = ft.ZD + (int64_t)c * ft.ldzd;
-    for (int r = threadIdx.x; r < ft.u; r += blockDim.x) zd[r] = cmul(z[r], dinv);
+  const int nc = tk.c1 - tk.c0;
+  for (int c = threadIdx.x; c < nc; c += blockDim.x)
+    dinv[c] = cdiv(CplxTraits<T>::one(), ft.G[(int64_t)(tk.c0 + c) * (ld + 1)]);
+  __syncthreads();
+  // every (column, row) of the task over all threads
+  for (int64_t e = threadIdx.x; e < (int64_t)nc * ft.u; e += blockDim.x) {
+    const int c = (int)(e / ft.u), r = (int)(e % ft.u);
+    ft.ZD[(int64_t)(tk.c0 + c) * ft.ldzd + r] = cmul(ft.Z[(int64_t)(tk.c0 + c) * ft.u + r], dinv[c]);
   }
 }
 
@@ -360,8 +364,9 @@ template <typename T>
 void launch_diag_ldlt(const FrontTask<T>* fronts, const int* list, int nlist, int kb, double tiny, int* status,
                       bool wide, cudaStream_t st) {
   if (nlist <= 0) return;
-  if (wide) k_diag_ldlt<T, double2><<<nlist, 256, 0, st>>>(fronts, list, kb, tiny, status);
-  else k_diag_ldlt<T, T><<<nlist, 256, 0, st>>>(fronts, list, kb, tiny, status);
+  // 128 threads: a 32 x 32 block keeps few busy, and smaller CTAs let more fronts' blocks share an SM
+  if (wide) k_diag_ldlt<T, double2><<<nlist, 128, 0, st>>>(fronts, list, kb, tiny, status);
+  else k_diag_ldlt<T, T><<<nlist, 128, 0, st>>>(fronts, list, kb, tiny, status);
 }
 template <typename T>
 void launch_panel_right(const FrontTask<T>* fronts, const ColTask* tasks, int ntasks, int kb, bool wide,
