@@ -186,17 +186,27 @@ __global__ void __launch_bounds__(256) k_assemble(const FrontTask<T>* __restrict
       while (lo < hi) { int mid = (lo + hi) >> 1; if (rel[mid] < c1) lo = mid + 1; else hi = mid; }
       b1 = lo;
     }
-    for (int b = b0; b < b1; ++b) {
+    // one warp per child column (the columns land in distinct target columns, so the warps never
+    // touch the same entry), four independent entries in flight per lane
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int b = b0 + warp; b < b1; b += nw) {
       const int tc = rel[b];
-      if (tc < s) {
-        T* dst = ft.G + (int64_t)tc * ld;
-        for (int a = b + threadIdx.x; a < uc; a += blockDim.x)
-          dst[rel[a]] = cadd(dst[rel[a]], Uc[upd_index(a, b, uc, utc)]);
-      } else {
-        for (int a = b + threadIdx.x; a < uc; a += blockDim.x) {
-          T* d = ft.U + upd_index(rel[a] - s, tc - s, u, ft.ut);
-          *d = cadd(*d, Uc[upd_index(a, b, uc, utc)]);
+      for (int a0 = b + lane; a0 < uc; a0 += 4 * 32) {
+        T* dst[4];
+        T val[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int a = a0 + 32 * t;
+          dst[t] = nullptr;
+          if (a < uc) {
+            const int ra = rel[a];
+            dst[t] = tc < s ? ft.G + (int64_t)tc * ld + ra : ft.U + upd_index(ra - s, tc - s, u, ft.ut);
+            val[t] = Uc[upd_index(a, b, uc, utc)];
+          }
         }
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (dst[t]) *dst[t] = cadd(*dst[t], val[t]);
       }
     }
     __syncthreads();
