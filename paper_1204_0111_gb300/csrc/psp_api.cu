@@ -108,6 +108,28 @@ static void upload(DevBuf& d, const std::vector<U>& h) {
 }
 // Stream-ordered upload: the copy from pageable memory is staged before the call returns, and it
 // does not wait for work already queued on the stream.
+// A stream for host-to-device uploads of tables built on the host: a copy from pageable memory may
+// wait for the work already on the stream it is issued on, so uploads issued on the compute stream
+// would hold the host until the device caught up; join() makes the compute stream wait for them.
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t e = nullptr;
+  SideStream() {
+    PSP_CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    PSP_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  SideStream(const SideStream&) = delete;
+  SideStream& operator=(const SideStream&) = delete;
+  ~SideStream() {
+    if (e) cudaEventDestroy(e);
+    if (s) cudaStreamDestroy(s);
+  }
+  void join(cudaStream_t st) {
+    PSP_CK(cudaEventRecord(e, s));
+    PSP_CK(cudaStreamWaitEvent(st, e, 0));
+  }
+};
+
 template <typename U>
 static void upload_async(DevBuf& d, const std::vector<U>& h, cudaStream_t st) {
   d.alloc(std::max<size_t>(h.size() * sizeof(U), 16));
@@ -536,6 +558,8 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
   PSP_CK(cudaMemsetAsync(status, 0, 8 * sizeof(int), st));
   static const char* names[] = {"k_assemble", "k_diag_ldlt", "k_panel_right", "k_panel_left", "k_gemm", "k_copy_linv",
                                 "k_tc_gemm", "k_tc_pack", "k_scale_zd", "k_panel_rsolve"};
+  // task arrays go up on a side stream, so that the next group's planning overlaps the device's work
+  SideStream up;
   std::vector<void*> chunks;
   const Allocator* chunk_alloc = g_alloc && g_alloc->alloc ? g_alloc : nullptr;
   struct ChunkGuard {
@@ -558,9 +582,9 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
     E* d = nullptr;
     if (n > 0) {
       if (chunk_alloc) d = static_cast<E*>(dev_alloc(n * sizeof(E), chunk_alloc));
-      else PSP_CK(cudaMallocAsync(reinterpret_cast<void**>(&d), n * sizeof(E), st));
+      else PSP_CK(cudaMallocAsync(reinterpret_cast<void**>(&d), n * sizeof(E), up.s));
       chunks.push_back(d);
-      PSP_CK(cudaMemcpyAsync(d, v.data() + done, n * sizeof(E), cudaMemcpyHostToDevice, st));
+      PSP_CK(cudaMemcpyAsync(d, v.data() + done, n * sizeof(E), cudaMemcpyHostToDevice, up.s));
     }
     return d;
   };
@@ -574,6 +598,7 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
     const GemmTask<T>* GT = upload_tail(gtasks, up_g);
     const TcPackTask* PT = upload_tail(ptasks, up_p);
     const TcGemmTask* TT = upload_tail(ttasks, up_t);
+    up.join(st);   // the group's kernels after its task arrays
     up_f = fronts.size();
     up_c = ctasks.size();
     up_d = dlist.size();
@@ -1100,6 +1125,7 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
 // Solve plan: per shape and level, forward row tasks and backward column tasks.
 // ---------------------------------------------------------------------------
 static void plan_solve(psp_ctx_s* X, cudaStream_t st) {
+  SideStream side;   // the tables go up while the device still factors
   std::vector<SolveTask> tasks;
   X->splan.assign(X->shapes.size(), {});
   for (size_t si = 0; si < X->shapes.size(); ++si) {
@@ -1161,7 +1187,7 @@ static void plan_solve(psp_ctx_s* X, cudaStream_t st) {
       P.nbwdB = (int)(tasks.size() - P.bwdB_off);
     }
   }
-  upload_async(X->d_stasks, tasks, st);
+  upload_async(X->d_stasks, tasks, side.s);
 
   // per shape: tasks per front, up and down
   std::vector<int> front_base(X->shapes.size() + 1, 0), ntask_up, ntask_down, ntask_upA, ntask_downA;
@@ -1304,8 +1330,8 @@ static void plan_solve(psp_ctx_s* X, cudaStream_t st) {
     SP.hsteps = steps;
     SP.nsteps = (int)steps.size();
     SP.nqueue = (int)queue.size();
-    upload_async(SP.steps, steps, st);
-    upload_async(SP.queue, queue, st);
+    upload_async(SP.steps, steps, side.s);
+    upload_async(SP.queue, queue, side.s);
     SP.nfront_steps = nfs;
     sync_words = std::max(sync_words, (size_t)words);
   }
@@ -1321,9 +1347,10 @@ static void plan_solve(psp_ctx_s* X, cudaStream_t st) {
     p.nz = pr.nz;
     pss.push_back(p);
   }
-  upload_async(X->d_sweep_probs, pss, st);
+  upload_async(X->d_sweep_probs, pss, side.s);
   X->sweep_sync_words = sync_words;
   X->d_sweep_sync.alloc(X->sweep_sync_words * 4);
+  side.join(st);
   PSP_CK(cudaMemsetAsync(X->d_sweep_sync.p, 0, X->sweep_sync_words * 4, st));
 }
 
