@@ -565,15 +565,19 @@ static void factor_all(psp_ctx_s* X, cudaStream_t st, const std::function<void()
   struct ChunkGuard {
     std::vector<void*>& c;
     cudaStream_t s;
+    cudaStream_t up;
     const Allocator* A;
     ~ChunkGuard() {
+      // copies still in flight on the side stream (an error between an upload and its join) end
+      // before their chunks are released
+      if (!c.empty()) cudaStreamSynchronize(up);
       if (A && !c.empty()) cudaStreamSynchronize(s);   // the caller's free is not stream-ordered
       for (void* p : c) {
         if (A) dev_free(p, A);
         else cudaFreeAsync(p, s);
       }
     }
-  } chunk_guard{chunks, st, chunk_alloc};
+  } chunk_guard{chunks, st, up.s, chunk_alloc};
   // copies v[done, size) to a new device chunk (the copy from pageable memory is staged before the
   // call returns, so the vector may grow afterwards); returns the chunk and advances done
   auto upload_tail = [&](const auto& v, size_t& done) {
