@@ -350,8 +350,8 @@ psp_status psp_stats(psp_handle h, psp_kernel_stat* out, int capacity, int* coun
  * sweep (the GPU's counterpart of the paper's choice of process grids, §2.1).  On this handle it
  * times psp_apply with nrhs right-hand sides (per problem of a batch) under candidate schedules
  * and keeps the fastest: the tasks a tree level is split into (152 .. 2432), the resident CTAs per
- * SM (2, 3, 4, 6, 8), the cap on rows / columns per task (64 .. 256) and, for nrhs > 1, the
- * right-hand sides per CTA pass (1 .. 8) and the floor on rows per task (8 .. 64).  It searches one
+ * SM (2, 3, 4, 6, 8), the cap on rows / columns per task (64 .. 256), the floor on rows per task
+ * (8 .. 64) and, for nrhs > 1, the right-hand sides per CTA pass (1 .. 8).  It searches one
  * coordinate at a time, starting from the handle's current schedule, timing `reps` applications
  * (CUDA events on `stream`) per candidate after one untimed one.  Results do not change beyond
  * rounding (the schedule only regroups the same sums).  The work vectors are the handle's own; the

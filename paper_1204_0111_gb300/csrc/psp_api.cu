@@ -2672,12 +2672,11 @@ psp_status psp_tune_sweep(psp_handle X, int nrhs, int reps, void* stream, psp_sw
       if (lt != best.lt) consider({lt, best.cps, best.rg, best.mr, best.xr});
     for (int cps : {2, 3, 4, 6, 8})
       if (cps != best.cps) consider({best.lt, cps, best.rg, best.mr, best.xr});
-    if (nrhs > 1) {
+    if (nrhs > 1)
       for (int rg : {1, 2, 4, 8})
         if (rg <= nrhs && rg != best.rg) consider({best.lt, best.cps, rg, best.mr, best.xr});
-      for (int mr : {8, 16, 32, 64})
-        if (mr != best.mr) consider({best.lt, best.cps, best.rg, mr, best.xr});
-    }
+    for (int mr : {8, 16, 32, 64})
+      if (mr != best.mr) consider({best.lt, best.cps, best.rg, mr, best.xr});
   } catch (...) {
     X->stats.timing = was_timing;
     cudaEventDestroy(e0);
