@@ -115,12 +115,14 @@ def test_apply_matches_oracle(case, nrhs):
 @pytest.mark.parametrize("si", ["extended", "paper", "two"])
 @pytest.mark.parametrize("max_rows", [128, 256])
 def test_whole_front_up_tasks_match_oracle(max_rows, si):
-    # up-the-tree tasks of up to 128 or 256 rows (a whole front per task at the bottom of the tree)
+    # up-the-tree tasks of up to 128 or 256 rows (a whole front per task at the bottom of the tree);
+    # one task per level is enough (sweep_level_tasks 1), so the small case's levels keep the full
+    # width instead of halving it towards the 8-row floor
     case = CASES[2]
     c = torch.from_numpy(case.c).cuda()
     P = psp.SweepingPreconditioner(c, case.h, case.omega, case.gamma, case.depth, pad=case.pad, leaf=case.leaf,
                                    pml_C=case.C, alpha=case.alpha, faces=case.faces, sweep_max_rows=max_rows,
-                                   selective_inversion=si)
+                                   sweep_level_tasks=1, selective_inversion=si)
     r = wl.random_vector(case.N, 3, seed=33)
     out = np.zeros_like(r)
     P.apply(r, out)
