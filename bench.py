@@ -511,7 +511,8 @@ def extra_workload(name, w, precision, dev, sched=None, maxit=400, desc="", tune
         torch.cuda.empty_cache()
         sched = dict(sched or {}, sweep_level_tasks=tuning["sweep_level_tasks"],
                      sweep_ctas_per_sm=tuning["sweep_ctas_per_sm"], sweep_rhs_group=tuning["sweep_rhs_group"],
-                     sweep_min_rows=tuning["sweep_min_rows"], sweep_max_rows=tuning["sweep_max_rows"])
+                     sweep_min_rows=tuning["sweep_min_rows"], sweep_max_rows=tuning["sweep_max_rows"],
+                     sweep_claim_ahead=tuning["sweep_claim_ahead"])
     f = w.rhs()
     f_dev = torch.from_numpy(f).to(dev)
     u_dev = torch.zeros_like(f_dev)
@@ -615,7 +616,7 @@ def gpu_main(a):
         setup_tuning[prec] = ts
         sched[prec] = {"sweep_level_tasks": t["sweep_level_tasks"], "sweep_ctas_per_sm": t["sweep_ctas_per_sm"],
                        "sweep_rhs_group": t["sweep_rhs_group"], "sweep_min_rows": t["sweep_min_rows"],
-                       "sweep_max_rows": t["sweep_max_rows"],
+                       "sweep_max_rows": t["sweep_max_rows"], "sweep_claim_ahead": t["sweep_claim_ahead"],
                        "selective_inversion": ts["selective_inversion"],
                        "tc_min_dim": ts["tc_min_dim"] if prec == "c64" else 0}
     if a.no_tune and a.si != "auto":
@@ -814,7 +815,8 @@ def batch_object(dev, steps, warmup, with_e2e=False):
     tuning = B.tune_sweep(nrhs=nrhs, reps=2)     # the library's autotuner, before any timed work
     B.close()
     sched = {"sweep_level_tasks": tuning["sweep_level_tasks"], "sweep_ctas_per_sm": tuning["sweep_ctas_per_sm"],
-             "sweep_rhs_group": tuning["sweep_rhs_group"], "sweep_max_rows": tuning["sweep_max_rows"], "pml_C": pml_C}
+             "sweep_rhs_group": tuning["sweep_rhs_group"], "sweep_max_rows": tuning["sweep_max_rows"],
+             "sweep_claim_ahead": tuning["sweep_claim_ahead"], "pml_C": pml_C}
 
     def step(stats=0, problems=prs, f=f_dev, u=u_dev):
         B = psp.SweepingPreconditionerBatch(problems, precision="c64", collect_stats=stats, **sched)

@@ -157,6 +157,12 @@ typedef struct {
                            64 .. 256: a level whose fronts outnumber the CTAs takes whole fronts of up
                            to this many rows per task, gathering each front's vector once; <= 0
                            selects the default (256) */
+  int sweep_claim_ahead; /* sweep schedule: queue tasks a CTA of the persistent sweep holds besides the
+                            one it runs, 1 or 2.  2 claims the task after next while a task waits and
+                            runs, so the next one's queue entry is in shared memory when it is done;
+                            1 claims the next task only as a task starts waiting, so a task claimed by
+                            a busy CTA waits behind one task rather than two.  <= 0 selects the
+                            default (2).  The results do not depend on it */
 } psp_options;
 
 /* Per-solve report filled by psp_solve (host struct). */
@@ -368,7 +374,8 @@ typedef struct {
   double best_ms;         /* one application under the chosen schedule */
   int sweep_min_rows;     /* floor on rows / columns per task */
   int sweep_max_rows;     /* cap on rows / columns per task */
-  int reserved[2];
+  int sweep_claim_ahead;  /* tasks a CTA holds besides the one it runs */
+  int reserved[1];
 } psp_sweep_tuning;
 
 psp_status psp_tune_sweep(psp_handle h, int nrhs, int reps, void* stream, psp_sweep_tuning* out);

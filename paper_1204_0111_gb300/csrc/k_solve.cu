@@ -548,13 +548,17 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs<T> a) {
   unsigned* head = a.ctr;
   unsigned* step_done = a.ctr + kSweepStepCounters;
   const int nrg = (a.cx.nrhs + RG - 1) / RG;
-  // Thread 0 holds the index of this CTA's current task and of its next one: the one after is claimed
-  // while the current one waits and runs, and the next one's queue entry is copied into the other
-  // shared-memory slot asynchronously, so that taking a task costs no dependent global load.
+  // Thread 0 holds the index of this CTA's current task and of its next one, and the next one's queue
+  // entry is copied into the other shared-memory slot asynchronously, so that taking a task costs no
+  // dependent global load.  Claiming two ahead (claim_ahead 2), the task after the next one is claimed
+  // while the current one waits and runs, and the next one's entry is copied meanwhile; claiming one
+  // ahead, the next task is claimed as the current one starts waiting and its entry copied once the
+  // wait is over, so a CTA holds one task besides the one it runs, not two.
+  const bool two_ahead = a.claim_ahead > 1;
   int cur = 0, nxt = 0, buf = 0;
   if (threadIdx.x == 0) {
     cur = (int)atomicAdd(head, 1u);
-    nxt = (int)atomicAdd(head, 1u);
+    if (two_ahead) nxt = (int)atomicAdd(head, 1u);
     if (cur < a.nqueue) s_q[0] = a.queue[cur];
     s_cx = a.cx;   // fields common to every task; thread 0 sets the per-task ones below
   }
@@ -597,18 +601,29 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs<T> a) {
     const int dir = e.dir, R = e.R;
     int after = 0;
     if (threadIdx.x == 0) {
-      after = (int)atomicAdd(head, 1u);   // the task after the next one (its index is read at the end)
-      if (nxt < a.nqueue) {
+      if (two_ahead) {
+        after = (int)atomicAdd(head, 1u);   // the task after the next one (its index is read at the end)
+        if (nxt < a.nqueue) {
+          const char* src = reinterpret_cast<const char*>(a.queue + nxt);
+          char* dst = reinterpret_cast<char*>(&s_q[buf ^ 1]);
+          cp_async16(dst, src);
+          cp_async16(dst + 16, src + 16);
+          cp_async16(dst + 32, src + 32);
+        }
+      } else {
+        nxt = (int)atomicAdd(head, 1u);   // the next task (its index is read after the wait)
+      }
+    }
+    prefetch_task<T>(tk, dir, s_cx);
+    if (threadIdx.x == 0) {
+      const bool ok = e.wait < 0 || wait_count(a.ctr + e.wait, e.target, a.status, a.sticky);
+      if (!two_ahead && nxt < a.nqueue) {
         const char* src = reinterpret_cast<const char*>(a.queue + nxt);
         char* dst = reinterpret_cast<char*>(&s_q[buf ^ 1]);
         cp_async16(dst, src);
         cp_async16(dst + 16, src + 16);
         cp_async16(dst + 32, src + 32);
       }
-    }
-    prefetch_task<T>(tk, dir, s_cx);
-    if (threadIdx.x == 0) {
-      const bool ok = e.wait < 0 || wait_count(a.ctr + e.wait, e.target, a.status, a.sticky);
       __threadfence();
       s_ok = ok;
     }
@@ -630,7 +645,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs<T> a) {
       atomicAdd(step_done + e.step, 1u);
       cp_async_wait_all();   // the next task's entry has landed
       cur = nxt;
-      nxt = after;
+      if (two_ahead) nxt = after;
     }
     buf ^= 1;   // every thread: the next task's entry is in the other slot
   }

@@ -338,6 +338,7 @@ struct psp_ctx_s {
   int tc_min_dim = 64;
   int sweep_level_tasks = 608, sweep_ctas_per_sm = 8, sweep_rhs_group = 0, solve_rhs_group = 0, sweep_min_rows = 8;
   int sweep_max_rows = 256;
+  int sweep_claim_ahead = 2;   // tasks a sweep CTA holds besides the one it runs
   int gmres_basis = 0;   // 0 auto, 1 keep z_j, 2 V only
   int si_mode = 0;       // psp_si_mode: what the factor of each front keeps (selective inversion, §2.2)
   bool test_sweep_stall = false;
@@ -1449,6 +1450,7 @@ static void apply_core(psp_ctx_s* X, double2* u, int nrhs, T* xf, T* xb, T* upd,
     sa.factor = X->d_factor.as<T>();
     sa.queue = SP.queue.as<QueueEntry>();
     sa.nqueue = SP.nqueue;
+    sa.claim_ahead = X->sweep_claim_ahead;
     sa.nprobs = np;
     sa.probs = X->d_sweep_probs.as<ProblemSweep>();
     unsigned* sync = X->d_sweep_sync.as<unsigned>();
@@ -2194,7 +2196,7 @@ static psp_status check_options(const psp_options* opt, psp_options* o) {
       (o->aux_mode != PSP_AUX_MOVING_PML && o->aux_mode != PSP_AUX_EXACT) || !(o->alpha >= 0) || !(o->pml_C >= 0) ||
       o->gmres_basis < 0 || o->gmres_basis > 2 || o->panel_begin < 0 || o->panel_count < 0 ||
       (o->dev_alloc == nullptr) != (o->dev_free == nullptr) || o->selective_inversion < 0 || o->selective_inversion > 3 ||
-      o->c64_diag_fp64 < 0 || o->c64_diag_fp64 > 1)
+      o->c64_diag_fp64 < 0 || o->c64_diag_fp64 > 1 || o->sweep_claim_ahead > 2)
     return fail(PSP_ERR_ARG, "bad options");
   return PSP_OK;
 }
@@ -2225,6 +2227,7 @@ static void init_options(psp_ctx_s* X, const psp_options& o) {
   X->sweep_rhs_group = o.sweep_rhs_group > 0 ? o.sweep_rhs_group : 0;
   X->sweep_min_rows = o.sweep_min_rows > 0 ? o.sweep_min_rows : 8;
   X->sweep_max_rows = o.sweep_max_rows > 0 ? std::min(256, std::max(64, o.sweep_max_rows)) : 256;
+  X->sweep_claim_ahead = o.sweep_claim_ahead > 0 ? o.sweep_claim_ahead : 2;
   X->solve_rhs_group = o.solve_rhs_group > 0 ? o.solve_rhs_group : 0;
   X->gmres_basis = o.gmres_basis;
   X->si_mode = o.selective_inversion;
@@ -2632,7 +2635,7 @@ psp_status psp_tune_sweep(psp_handle X, int nrhs, int reps, void* stream, psp_sw
   cudaEvent_t e0, e1;
   PSP_CK(cudaEventCreate(&e0));
   PSP_CK(cudaEventCreate(&e1));
-  struct Sched { int lt, cps, rg, mr, xr; };
+  struct Sched { int lt, cps, rg, mr, xr, ca; };
   int timed = 0;
   auto time_one = [&](const Sched& c) {
     if (c.lt != X->sweep_level_tasks || c.mr != X->sweep_min_rows || c.xr != X->sweep_max_rows) {
@@ -2643,6 +2646,7 @@ psp_status psp_tune_sweep(psp_handle X, int nrhs, int reps, void* stream, psp_sw
     }
     X->sweep_ctas_per_sm = c.cps;
     X->sweep_rhs_group = c.rg;
+    X->sweep_claim_ahead = c.ca;
     apply_dispatch(X, u.as<double2>(), nrhs, st);
     PSP_CK(cudaEventRecord(e0, st));
     for (int r = 0; r < reps; ++r) apply_dispatch(X, u.as<double2>(), nrhs, st);
@@ -2655,7 +2659,8 @@ psp_status psp_tune_sweep(psp_handle X, int nrhs, int reps, void* stream, psp_sw
   };
   const bool was_timing = X->stats.timing;
   X->stats.timing = false;
-  Sched best{X->sweep_level_tasks, X->sweep_ctas_per_sm, X->sweep_rhs_group, X->sweep_min_rows, X->sweep_max_rows};
+  Sched best{X->sweep_level_tasks, X->sweep_ctas_per_sm, X->sweep_rhs_group, X->sweep_min_rows, X->sweep_max_rows,
+             X->sweep_claim_ahead};
   double best_ms = 0, initial_ms = 0;
   try {
     best_ms = initial_ms = time_one(best);
@@ -2667,16 +2672,18 @@ psp_status psp_tune_sweep(psp_handle X, int nrhs, int reps, void* stream, psp_sw
       }
     };
     for (int xr : {64, 128, 256})
-      if (xr != best.xr) consider({best.lt, best.cps, best.rg, best.mr, xr});
+      if (xr != best.xr) consider({best.lt, best.cps, best.rg, best.mr, xr, best.ca});
     for (int lt : {152, 304, 608, 1216, 2432})
-      if (lt != best.lt) consider({lt, best.cps, best.rg, best.mr, best.xr});
+      if (lt != best.lt) consider({lt, best.cps, best.rg, best.mr, best.xr, best.ca});
     for (int cps : {2, 3, 4, 6, 8})
-      if (cps != best.cps) consider({best.lt, cps, best.rg, best.mr, best.xr});
+      if (cps != best.cps) consider({best.lt, cps, best.rg, best.mr, best.xr, best.ca});
     if (nrhs > 1)
       for (int rg : {1, 2, 4, 8})
-        if (rg <= nrhs && rg != best.rg) consider({best.lt, best.cps, rg, best.mr, best.xr});
+        if (rg <= nrhs && rg != best.rg) consider({best.lt, best.cps, rg, best.mr, best.xr, best.ca});
     for (int mr : {8, 16, 32, 64})
-      if (mr != best.mr) consider({best.lt, best.cps, best.rg, mr, best.xr});
+      if (mr != best.mr) consider({best.lt, best.cps, best.rg, mr, best.xr, best.ca});
+    for (int ca : {1, 2})
+      if (ca != best.ca) consider({best.lt, best.cps, best.rg, best.mr, best.xr, ca});
   } catch (...) {
     X->stats.timing = was_timing;
     cudaEventDestroy(e0);
@@ -2694,6 +2701,7 @@ psp_status psp_tune_sweep(psp_handle X, int nrhs, int reps, void* stream, psp_sw
   }
   X->sweep_ctas_per_sm = best.cps;
   X->sweep_rhs_group = best.rg;
+  X->sweep_claim_ahead = best.ca;
   if (out) {
     std::memset(out, 0, sizeof(*out));
     out->sweep_level_tasks = best.lt;
@@ -2701,6 +2709,7 @@ psp_status psp_tune_sweep(psp_handle X, int nrhs, int reps, void* stream, psp_sw
     out->sweep_rhs_group = best.rg;
     out->sweep_min_rows = best.mr;
     out->sweep_max_rows = best.xr;
+    out->sweep_claim_ahead = best.ca;
     out->candidates = timed;
     out->initial_ms = initial_ms;
     out->best_ms = best_ms;

@@ -313,6 +313,7 @@ struct SweepArgs {
   int nprobs;
   const ProblemSweep* probs;    // per problem; cx's vectors and work vectors are offset per problem
   int chunk;                    // vector entries a task stages in shared memory at a time (set by launch_sweep)
+  int claim_ahead;              // 2: a CTA holds the two tasks after the one it runs; 1: the next one only
 };
 // returns 0 on success, -1 when a cooperative launch is not possible, else a cudaError_t; smax / ldmax:
 // the widest front's s and s + u

@@ -41,7 +41,7 @@ class Options(ctypes.Structure):
                 ("factor_every_panel", ctypes.c_int), ("panel_begin", ctypes.c_int), ("panel_count", ctypes.c_int),
                 ("dev_alloc", ctypes.c_void_p), ("dev_free", ctypes.c_void_p), ("alloc_ctx", ctypes.c_void_p),
                 ("selective_inversion", ctypes.c_int), ("c64_diag_fp64", ctypes.c_int),
-                ("sweep_max_rows", ctypes.c_int)]
+                ("sweep_max_rows", ctypes.c_int), ("sweep_claim_ahead", ctypes.c_int)]
 
 
 # psp_options.dev_alloc / dev_free callback types
@@ -68,7 +68,7 @@ class SweepTuning(ctypes.Structure):
     _fields_ = [("sweep_level_tasks", ctypes.c_int), ("sweep_ctas_per_sm", ctypes.c_int),
                 ("sweep_rhs_group", ctypes.c_int), ("candidates", ctypes.c_int), ("initial_ms", ctypes.c_double),
                 ("best_ms", ctypes.c_double), ("sweep_min_rows", ctypes.c_int), ("sweep_max_rows", ctypes.c_int),
-                ("reserved", ctypes.c_int * 2)]
+                ("sweep_claim_ahead", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -188,7 +188,7 @@ class SweepingPreconditioner:
                  tc_min_dim=0, sweep_level_tasks=0, sweep_ctas_per_sm=0, setup_temp_mb=0, sweep_rhs_group=0,
                  solve_rhs_group=0, test_sweep_stall=0, gmres_basis="auto", factor_every_panel=False,
                  panels=None, allocator=None, selective_inversion="extended", sweep_min_rows=0,
-                 diag_fp64=False, sweep_max_rows=0):
+                 diag_fp64=False, sweep_max_rows=0, sweep_claim_ahead=0):
         nz, ny, nx = c.shape
         self.nx, self.ny, self.nz = nx, ny, nz
         self.N = nx * ny * nz
@@ -200,6 +200,7 @@ class SweepingPreconditioner:
         o.sweep_min_rows = int(sweep_min_rows)
         o.c64_diag_fp64 = 1 if diag_fp64 else 0
         o.sweep_max_rows = int(sweep_max_rows)
+        o.sweep_claim_ahead = int(sweep_claim_ahead)
         o.gmres_basis = {"auto": 0, "z": 1, "v": 2}[gmres_basis]
         o.factor_every_panel = 1 if factor_every_panel else 0
         if panels is not None:                   # (first, count): one block of a multi-GPU sweep
@@ -345,7 +346,8 @@ class SweepingPreconditionerBatch(SweepingPreconditioner):
     def __init__(self, problems, pad=None, leaf=64, pml_C=4.0, alpha=2 * math.pi, precision="c128", faces=63,
                  mode="moving", stream=None, collect_stats=0, tensor_cores=True, tc_min_dim=0, sweep_level_tasks=0,
                  sweep_ctas_per_sm=0, setup_temp_mb=0, sweep_rhs_group=0, solve_rhs_group=0,
-                 selective_inversion="extended", factor_every_panel=False, allocator=None, sweep_max_rows=0):
+                 selective_inversion="extended", factor_every_panel=False, allocator=None, sweep_max_rows=0,
+                 sweep_claim_ahead=0):
         n = len(problems)
         grids = (Grid * n)()
         cs = (_P * n)()
@@ -373,6 +375,7 @@ class SweepingPreconditionerBatch(SweepingPreconditioner):
         o.selective_inversion = SI_MODES[selective_inversion]
         o.factor_every_panel = 1 if factor_every_panel else 0
         o.sweep_max_rows = int(sweep_max_rows)
+        o.sweep_claim_ahead = int(sweep_claim_ahead)
         if allocator is not None:
             self._alloc_cbs = _allocator_callbacks(*allocator)
             o.dev_alloc = ctypes.cast(self._alloc_cbs[0], ctypes.c_void_p)

@@ -49,6 +49,10 @@ def test_bad_arguments_are_rejected_before_any_device_call(L):
     o.precision = 7
     st = L.psp_setup(ctypes.byref(g), ctypes.cast(c, ctypes.c_void_p), 1.0, 2, 2, ctypes.byref(o), None, ctypes.byref(h))
     assert st == 1
+    L.psp_default_options(ctypes.byref(o))
+    o.sweep_claim_ahead = 3
+    st = L.psp_setup(ctypes.byref(g), ctypes.cast(c, ctypes.c_void_p), 1.0, 2, 2, ctypes.byref(o), None, ctypes.byref(h))
+    assert st == 1 and b"options" in L.psp_last_error()
     assert L.psp_apply(None, None, None, 1, None) == 1
     assert L.psp_destroy(None) == 0
 

@@ -37,10 +37,11 @@ def oracle_for(case: Case, mode="moving"):
     return _oracles[key]
 
 
-def gpu_for(case: Case, precision="c128", mode="moving"):
+def gpu_for(case: Case, precision="c128", mode="moving", **kw):
     c = torch.from_numpy(case.c).cuda()
     return psp.SweepingPreconditioner(c, case.h, case.omega, case.gamma, case.depth, pad=case.pad, leaf=case.leaf,
-                                      pml_C=case.C, alpha=case.alpha, precision=precision, faces=case.faces, mode=mode)
+                                      pml_C=case.C, alpha=case.alpha, precision=precision, faces=case.faces, mode=mode,
+                                      **kw)
 
 
 def rel(a, b):
@@ -276,6 +277,25 @@ def test_tensor_core_fronts_complex64(case):
     assert (st.get("k_tc_gemm", {}).get("launches", 0) > 0) == big
 
 
+@pytest.mark.parametrize("precision", ["c128", "c64"])
+@pytest.mark.parametrize("si", ["extended", "paper"])
+def test_claiming_one_task_ahead_gives_the_same_bits(si, precision):
+    # a sweep CTA holding one queue task besides the one it runs, instead of two, changes which CTA
+    # runs what and when, not the arithmetic: the same bits, for one and for several right-hand sides
+    case = CASES[2]
+    for nrhs in (1, 3):
+        r = wl.random_vector(case.N, nrhs, seed=45)
+        outs = []
+        for ca in (2, 1):
+            P = gpu_for(case, selective_inversion=si, precision=precision, sweep_claim_ahead=ca)
+            out = np.zeros_like(r)
+            P.apply(r, out)
+            P.close()
+            outs.append(out)
+        assert np.array_equal(outs[0], outs[1])
+        assert rel(outs[1], oracle_for(case).apply(r)) < (1e-10 if precision == "c128" else 1e-4)
+
+
 def test_sweep_autotuner_keeps_results():
     case = CASES[2]
     P = gpu_for(case)
@@ -283,7 +303,7 @@ def test_sweep_autotuner_keeps_results():
     t = P.tune_sweep(nrhs=2, reps=1)
     assert t["sweep_level_tasks"] in (152, 304, 608, 1216, 2432)
     assert t["sweep_ctas_per_sm"] in (2, 3, 4, 6, 8) and t["sweep_rhs_group"] in (0, 1, 2)
-    assert t["sweep_max_rows"] in (64, 128, 256)
+    assert t["sweep_max_rows"] in (64, 128, 256) and t["sweep_claim_ahead"] in (1, 2)
     assert t["candidates"] >= 10 and 0 < t["best_ms"] <= t["initial_ms"]
     r = wl.random_vector(case.N, 2, seed=44)
     out = np.zeros_like(r)
