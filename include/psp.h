@@ -357,7 +357,8 @@ psp_status psp_stats(psp_handle h, psp_kernel_stat* out, int capacity, int* coun
  * times psp_apply with nrhs right-hand sides (per problem of a batch) under candidate schedules
  * and keeps the fastest: the tasks a tree level is split into (152 .. 2432), the resident CTAs per
  * SM (2, 3, 4, 6, 8), the cap on rows / columns per task (64 .. 256), the floor on rows per task
- * (8 .. 64) and, for nrhs > 1, the right-hand sides per CTA pass (1 .. 8).  It searches one
+ * (8 .. 64), the queue tasks a CTA holds ahead (1, 2) and, for nrhs > 1, the right-hand sides per
+ * CTA pass (1 .. 8).  It searches one
  * coordinate at a time, starting from the handle's current schedule, timing `reps` applications
  * (CUDA events on `stream`) per candidate after one untimed one.  Results do not change beyond
  * rounding (the schedule only regroups the same sums).  The work vectors are the handle's own; the
