@@ -458,8 +458,8 @@ static int pick_rg(int nrhs, size_t per_rhs_bytes) {
 // (the chains of a batch of independent problems are interleaved in the queue and run side by
 // side), so every front does, through its descendants.  A down-the-tree task waits for its parent
 // (the root: for its own up-the-tree tasks).  A task only waits on tasks earlier in the queue.  A
-// CTA claims its tasks in queue order, one ahead of the task it runs; the earliest unfinished task
-// is therefore the one some CTA runs (a CTA holding it only as its next task would be running an
+// CTA claims its tasks in queue order, one or two ahead of the task it runs; the earliest unfinished
+// task is therefore the one some CTA runs (a CTA holding it only as a later task would be running an
 // earlier unfinished one), every task it waits for has finished, and since every CTA of a
 // cooperative launch is resident, the sweep progresses.  Each wait is bounded anyway: a CTA that
 // gives up sets status[2] and stops; the others then give up at their next wait.
