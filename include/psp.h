@@ -161,8 +161,9 @@ typedef struct {
                             one it runs, 1 or 2.  2 claims the task after next while a task waits and
                             runs, so the next one's queue entry is in shared memory when it is done;
                             1 claims the next task only as a task starts waiting, so a task claimed by
-                            a busy CTA waits behind one task rather than two.  <= 0 selects the
-                            default (2).  The results do not depend on it */
+                            a busy CTA waits behind one task rather than two (measured faster on
+                            most workloads).  <= 0 selects the default (1).  The results do not
+                            depend on it */
 } psp_options;
 
 /* Per-solve report filled by psp_solve (host struct). */

@@ -338,7 +338,7 @@ struct psp_ctx_s {
   int tc_min_dim = 64;
   int sweep_level_tasks = 608, sweep_ctas_per_sm = 8, sweep_rhs_group = 0, solve_rhs_group = 0, sweep_min_rows = 8;
   int sweep_max_rows = 256;
-  int sweep_claim_ahead = 2;   // tasks a sweep CTA holds besides the one it runs
+  int sweep_claim_ahead = 1;   // tasks a sweep CTA holds besides the one it runs
   int gmres_basis = 0;   // 0 auto, 1 keep z_j, 2 V only
   int si_mode = 0;       // psp_si_mode: what the factor of each front keeps (selective inversion, §2.2)
   bool test_sweep_stall = false;
@@ -2227,7 +2227,7 @@ static void init_options(psp_ctx_s* X, const psp_options& o) {
   X->sweep_rhs_group = o.sweep_rhs_group > 0 ? o.sweep_rhs_group : 0;
   X->sweep_min_rows = o.sweep_min_rows > 0 ? o.sweep_min_rows : 8;
   X->sweep_max_rows = o.sweep_max_rows > 0 ? std::min(256, std::max(64, o.sweep_max_rows)) : 256;
-  X->sweep_claim_ahead = o.sweep_claim_ahead > 0 ? o.sweep_claim_ahead : 2;
+  X->sweep_claim_ahead = o.sweep_claim_ahead > 0 ? o.sweep_claim_ahead : 1;
   X->solve_rhs_group = o.solve_rhs_group > 0 ? o.solve_rhs_group : 0;
   X->gmres_basis = o.gmres_basis;
   X->si_mode = o.selective_inversion;
